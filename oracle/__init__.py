@@ -1,0 +1,129 @@
+"""CPU oracle for canonical connected-components labels.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline of ``bench.py`` may import this package; the library path must not.
+It shares no code with the CUDA implementation.
+
+Canonical labels (the definition every implementation is checked against):
+background pixels get 0; every pixel of a connected component gets
+1 + the smallest raster position ``x + y*W`` found in that component
+(pixel model of Sec. 3; root = element whose label equals its own address,
+Sec. 3.1.1; links always point from the larger to the smaller label,
+Sec. 3.1.3).  Any nonzero input byte is foreground.
+
+Three independent routes to that result:
+
+* ``label_two_pass`` -- raster two-pass union-find, plain C (``ccl_oracle.c``).
+* ``label_bfs``      -- breadth-first flood fill in raster order, plain C.
+* ``label_closure``  -- pure Python: repeated min-propagation over the
+  adjacency until nothing changes.  Slow; for images of a few hundred pixels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ccl_oracle.c")
+_LIB = os.path.join(_HERE, "libccl_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``ccl_oracle.c`` into ``libccl_oracle.so`` beside it with gcc."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            for name in ("ccl_oracle_two_pass", "ccl_oracle_bfs"):
+                fn = getattr(lib, name)
+                fn.restype = ctypes.c_int
+                fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+def _call(name: str, img: np.ndarray, conn: int) -> np.ndarray:
+    img = np.asarray(img)
+    if img.ndim != 2 or img.dtype != np.uint8:
+        raise ValueError("image must be a 2D uint8 array")
+    if conn not in (4, 8):
+        raise ValueError("connectivity must be 4 or 8")
+    H, W = img.shape
+    if img.strides[1] != 1 or (H > 1 and img.strides[0] < W):
+        img = np.ascontiguousarray(img)
+    # numpy may report any stride for a dimension of extent 1
+    pitch = img.strides[0] if H > 1 else W
+    out = np.empty((H, W), dtype=np.int32)
+    if H == 0 or W == 0:
+        return out
+    rc = getattr(_load(), name)(img.ctypes.data, H, W, pitch, conn, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"{name} failed with status {rc}")
+    return out
+
+
+def label_two_pass(img: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels by raster two-pass union-find (C)."""
+    return _call("ccl_oracle_two_pass", img, conn)
+
+
+def label_bfs(img: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels by raster-order breadth-first flood fill (C)."""
+    return _call("ccl_oracle_bfs", img, conn)
+
+
+def label(img: np.ndarray, conn: int) -> np.ndarray:
+    """The oracle's answer: the two-pass union-find labels."""
+    return label_two_pass(img, conn)
+
+
+def label_closure(img: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels by min-propagation to a fixed point (pure Python).
+
+    Every foreground pixel starts with 1 + its own raster position; each sweep
+    replaces a pixel's value by the minimum over itself and its foreground
+    neighbours.  At the fixed point every pixel holds the minimum of its
+    component.  Quadratic in the worst case: small images only.
+    """
+    img = np.asarray(img)
+    H, W = img.shape
+    fg = [[bool(img[y, x]) for x in range(W)] for y in range(H)]
+    lab = [[(y * W + x + 1) if fg[y][x] else 0 for x in range(W)] for y in range(H)]
+    if conn == 4:
+        nbrs = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+    elif conn == 8:
+        nbrs = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+    else:
+        raise ValueError("connectivity must be 4 or 8")
+    changed = True
+    while changed:
+        changed = False
+        for y in range(H):
+            for x in range(W):
+                if not fg[y][x]:
+                    continue
+                best = lab[y][x]
+                for dx, dy in nbrs:
+                    nx, ny = x + dx, y + dy
+                    if 0 <= nx < W and 0 <= ny < H and fg[ny][nx] and lab[ny][nx] < best:
+                        best = lab[ny][nx]
+                if best != lab[y][x]:
+                    lab[y][x] = best
+                    changed = True
+    return np.array(lab, dtype=np.int32).reshape(H, W)
