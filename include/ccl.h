@@ -1,0 +1,135 @@
+/*
+ * ccl.h -- C ABI of the GB300 block-based connected-components labeller.
+ *
+ * Problem (Sec. 1 and the first paragraph of Sec. 3): given a 2D binary image
+ * I(x,y) of H rows and W columns, give every connected foreground region one
+ * ID.  A pixel's raster position is P(x,y) = x + y*W; its provisional label
+ * is its own position and the root of an equivalence list is the element whose
+ * label equals its own address (Sec. 3.1.1), with links always from the
+ * larger label to the smaller (Sec. 3.1.3, Sec. 3.2).  The root is therefore
+ * the smallest position of its component, and this library writes the
+ * canonical labels
+ *
+ *     labels[y*W + x] = 0                                   if I(x,y) == 0
+ *     labels[y*W + x] = 1 + min{ x' + y'*W : (x',y') in C }  if (x,y) in C
+ *
+ * for every connected component C.  The +1 frees 0 for the background.  Any
+ * nonzero input byte is foreground.  Connectivity is 4 (the connectivity the
+ * paper evaluates, Sec. 4.3) or 8.
+ *
+ * The method (Sec. 3): (1) each tile is labelled locally in on-chip memory by
+ * coarse labelling -- row connection, column connection, unification of the
+ * label-equivalence lists -- followed by a refinement that merges separated
+ * sub-regions and an ID conversion to global positions (Kernel 1, Sec.
+ * 3.1.1-3.1.4); (2) tiles are merged by analysing only the pixels on tile
+ * boundaries (Kernel 2, Sec. 3.2, Eq. 1-2); (3) a root-find flattens the
+ * global label map (Sec. 3.3).
+ *
+ * Conventions shared by every entry point
+ *   - Memory: `img` is read-only, row stride `pitch` bytes (pitch >= W).
+ *     `labels` is dense int32 with row stride W.  The two must not overlap.
+ *     Device pointers unless the name says host.  The caller owns them.
+ *   - Streams: `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.  Device entry points are asynchronous and ordered on
+ *     `stream`; argument errors are reported synchronously and nothing is
+ *     enqueued.  A device-side error (an iteration cap reached inside a
+ *     union-find loop) is recorded in a per-device error word and reported by
+ *     ccl_get_device_status().
+ *   - Sizes: H, W >= 0; an image with H == 0 or W == 0 is a no-op that returns
+ *     CCL_OK.  H*W must not exceed 2^31 - 2 (CCL_ERR_UNSUPPORTED otherwise),
+ *     so that 1 + position fits an int32.
+ *   - Threads: entry points may be called from several host threads; calls
+ *     that share a stream are ordered by that stream.
+ */
+#ifndef CCL_H
+#define CCL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCL_OK = 0,
+    CCL_ERR_INVALID_ARG = 1,
+    CCL_ERR_UNSUPPORTED = 2,
+    CCL_ERR_OUT_OF_MEMORY = 3,
+    CCL_ERR_CUDA = 4,
+    CCL_ERR_DEVICE_TIMEOUT = 5,
+    CCL_ERR_BUSY = 6,
+    CCL_ERR_NOT_FOUND = 7
+} ccl_status;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *ccl_status_string(int status);
+
+/* Library ABI version: major * 10000 + minor * 100 + patch. */
+int ccl_version(void);
+
+/*
+ * Label one image (Sec. 3, all three steps).
+ *   img          device, u8 [H][pitch]; nonzero = foreground.
+ *   H, W         rows and columns.
+ *   pitch        input row stride in bytes, >= W.
+ *   connectivity 4 or 8.
+ *   labels       device, int32 [H][W] (row stride W), written in full.
+ *   stream       cudaStream_t.
+ * Uses a library-owned scratch buffer per (device, stream), grown on demand
+ * (the growth is a cudaMalloc; call once outside stream capture before
+ * capturing).  Returns CCL_ERR_INVALID_ARG for NULL pointers, negative sizes,
+ * pitch < W, connectivity not in {4,8} or overlapping img/labels;
+ * CCL_ERR_UNSUPPORTED when H*W > 2^31 - 2; CCL_ERR_OUT_OF_MEMORY when the
+ * scratch cannot grow; CCL_ERR_CUDA when a launch fails.
+ */
+ccl_status ccl_label(const uint8_t *img, int H, int W, size_t pitch, int connectivity,
+                     int32_t *labels, void *stream);
+
+/*
+ * Scratch bytes that ccl_label_ws() needs for an H x W image (independent of
+ * the connectivity, which is accepted for symmetry).  Writes *bytes.
+ */
+ccl_status ccl_workspace_size(int H, int W, int connectivity, size_t *bytes);
+
+/*
+ * ccl_label() with caller-owned scratch: `workspace` is a device buffer of at
+ * least ccl_workspace_size() bytes, 256-byte aligned, used only by the work
+ * enqueued by this call (no other call may use it until that work is done).
+ * Returns CCL_ERR_INVALID_ARG when it is NULL, misaligned or too small.
+ */
+ccl_status ccl_label_ws(const uint8_t *img, int H, int W, size_t pitch, int connectivity,
+                        int32_t *labels, void *workspace, size_t workspace_bytes,
+                        void *stream);
+
+/*
+ * Label an image held in HOST memory: copies it to library-owned device
+ * buffers on `stream`, labels it, copies the labels back to `host_labels`
+ * (int32 [H][W]) and waits for the stream before returning, so the labels
+ * are ready on return.  Page-locked host buffers give the fastest copies.
+ * Errors as ccl_label(), plus a device error found by the wait.
+ */
+ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch,
+                          int connectivity, int32_t *host_labels, void *stream);
+
+/*
+ * Waits for `stream`, then reports and clears the current device's error
+ * word: CCL_ERR_DEVICE_TIMEOUT when a union-find loop reached its iteration
+ * cap since the last check (its outputs are then not valid), CCL_ERR_CUDA when
+ * the wait itself failed, CCL_OK otherwise.
+ */
+ccl_status ccl_get_device_status(void *stream);
+
+/*
+ * Test hook for failure detection: caps every find/union loop in the kernels
+ * at `cap` iterations (cap <= 0 restores the default, which no valid input
+ * can reach).  A low cap makes the loops give up, set the device error word
+ * and return, so nothing spins.  Affects launches made after the call.
+ */
+void ccl_debug_set_iteration_cap(int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCL_H */

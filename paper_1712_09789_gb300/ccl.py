@@ -1,0 +1,184 @@
+"""Thin Python binding of the C ABI in ``include/ccl.h``.
+
+Argument marshalling only: every function hands tensors' device pointers,
+sizes and the current CUDA stream to ``libccl.so`` and raises ``CclError``
+on a non-OK status.  The library must have been built (``build()`` in
+``__graft_entry__`` or ``python -m paper_1712_09789_gb300.build``); there is
+no fallback, and importing a missing library fails loudly.
+
+Tensors: images are 2D ``uint8`` CUDA tensors whose rows are contiguous
+(``stride(1) == 1``; the row stride ``stride(0)`` is passed as the pitch);
+labels are 2D ``int32`` CUDA tensors, contiguous.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libccl.so")
+_lock = threading.Lock()
+_lib = None
+
+CCL_OK = 0
+CCL_ERR_INVALID_ARG = 1
+CCL_ERR_UNSUPPORTED = 2
+CCL_ERR_OUT_OF_MEMORY = 3
+CCL_ERR_CUDA = 4
+CCL_ERR_DEVICE_TIMEOUT = 5
+CCL_ERR_BUSY = 6
+CCL_ERR_NOT_FOUND = 7
+
+
+class CclError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {ccl_status_string(status)} ({status})")
+
+
+_c = ctypes
+_SIGS = {
+    "ccl_status_string": (_c.c_char_p, [_c.c_int]),
+    "ccl_version": (_c.c_int, []),
+    "ccl_label": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
+                             _c.c_void_p]),
+    "ccl_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "ccl_label_ws": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
+                                _c.c_void_p, _c.c_size_t, _c.c_void_p]),
+    "ccl_label_host": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
+                                  _c.c_void_p, _c.c_void_p]),
+    "ccl_get_device_status": (_c.c_int, [_c.c_void_p]),
+    "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
+}
+
+
+def load() -> ctypes.CDLL:
+    """Load ``libccl.so`` and declare its signatures (once)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"{LIB_PATH} is missing: build the CUDA library first "
+                    "(python -m paper_1712_09789_gb300.build)")
+            lib = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, where: str):
+    if st != CCL_OK:
+        raise CclError(st, where)
+
+
+def ccl_status_string(status: int) -> str:
+    return load().ccl_status_string(status).decode()
+
+
+def ccl_version() -> int:
+    return load().ccl_version()
+
+
+def _stream_ptr(stream, device) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _image_args(img):
+    import torch
+
+    if not isinstance(img, torch.Tensor) or img.dtype != torch.uint8 or img.dim() != 2:
+        raise ValueError("image must be a 2D torch.uint8 tensor")
+    if not img.is_cuda:
+        raise ValueError("image must be a CUDA tensor")
+    H, W = img.shape
+    if W > 0 and H > 1 and img.stride(1) != 1:
+        raise ValueError("image rows must be contiguous (stride(1) == 1)")
+    pitch = img.stride(0) if H > 1 else W
+    return H, W, pitch
+
+
+def _labels_for(img, labels):
+    import torch
+
+    H, W = img.shape
+    if labels is None:
+        return torch.empty((H, W), dtype=torch.int32, device=img.device)
+    if labels.dtype != torch.int32 or tuple(labels.shape) != (H, W) or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous int32 tensor of the image's shape")
+    if labels.device != img.device:
+        raise ValueError("labels must be on the image's device")
+    return labels
+
+
+def ccl_label(img, connectivity: int = 8, labels=None, stream=None):
+    """Canonical labels of a device image (``ccl_label``).  Returns ``labels``."""
+    H, W, pitch = _image_args(img)
+    labels = _labels_for(img, labels)
+    st = load().ccl_label(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+                          _stream_ptr(stream, img.device))
+    _check(st, "ccl_label")
+    return labels
+
+
+def ccl_workspace_size(H: int, W: int, connectivity: int = 8) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().ccl_workspace_size(H, W, connectivity, ctypes.byref(out)), "ccl_workspace_size")
+    return out.value
+
+
+def ccl_label_ws(img, workspace, connectivity: int = 8, labels=None, stream=None):
+    """``ccl_label`` with a caller-owned scratch tensor (``ccl_label_ws``)."""
+    H, W, pitch = _image_args(img)
+    labels = _labels_for(img, labels)
+    nbytes = workspace.numel() * workspace.element_size()
+    st = load().ccl_label_ws(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+                             workspace.data_ptr(), nbytes, _stream_ptr(stream, img.device))
+    _check(st, "ccl_label_ws")
+    return labels
+
+
+def ccl_label_host(img: np.ndarray, connectivity: int = 8, labels: np.ndarray | None = None,
+                   stream=None) -> np.ndarray:
+    """Labels of a host image; copies in, labels, copies out and waits
+    (``ccl_label_host``).  ``img`` is a 2D uint8 array with contiguous rows."""
+    if not isinstance(img, np.ndarray) or img.dtype != np.uint8 or img.ndim != 2:
+        raise ValueError("image must be a 2D numpy uint8 array")
+    H, W = img.shape
+    if W > 0 and H > 1 and img.strides[1] != 1:
+        raise ValueError("image rows must be contiguous")
+    pitch = img.strides[0] if H > 1 else W
+    if labels is None:
+        labels = np.empty((H, W), np.int32)
+    elif labels.dtype != np.int32 or labels.shape != (H, W) or not labels.flags.c_contiguous:
+        raise ValueError("labels must be a contiguous int32 array of the image's shape")
+    import torch
+
+    st = load().ccl_label_host(img.ctypes.data, H, W, pitch, connectivity, labels.ctypes.data,
+                               _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device())))
+    _check(st, "ccl_label_host")
+    return labels
+
+
+def ccl_get_device_status(stream=None) -> int:
+    """Waits for the stream and returns (and clears) the device status code."""
+    import torch
+
+    return load().ccl_get_device_status(
+        _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device())))
+
+
+def ccl_debug_set_iteration_cap(cap: int) -> None:
+    load().ccl_debug_set_iteration_cap(cap)

@@ -1,0 +1,190 @@
+// ccl_api.cu -- the C ABI declared in include/ccl.h: argument checks,
+// library-owned scratch per (device, stream), host-buffer entry point and the
+// device error word.
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ccl.h"
+#include "ccl_internal.h"
+
+namespace {
+
+std::mutex g_mu;
+int g_cap = 0;  // iteration cap for new launches; 0 = default
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+// scratch, and the host entry point's staging buffers, per (device, stream)
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_scratch;
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_img;
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_lab;
+
+ccl_status grow(DevBuf &b, size_t need) {
+    if (b.bytes >= need) return CCL_OK;
+    if (b.ptr) {
+        cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+    }
+    // grow geometrically so that a sequence of larger images reallocates rarely
+    size_t want = need + need / 4;
+    if (cudaMalloc(&b.ptr, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&b.ptr, need) != cudaSuccess) {
+            cudaGetLastError();
+            return CCL_ERR_OUT_OF_MEMORY;
+        }
+        want = need;
+    }
+    b.bytes = want;
+    return CCL_OK;
+}
+
+ccl_status check_image_args(const void *img, int H, int W, size_t pitch, int conn, const void *labels) {
+    if (H < 0 || W < 0) return CCL_ERR_INVALID_ARG;
+    if (conn != 4 && conn != 8) return CCL_ERR_INVALID_ARG;
+    if (H == 0 || W == 0) return CCL_OK;
+    if (!img || !labels) return CCL_ERR_INVALID_ARG;
+    if (pitch < (size_t)W) return CCL_ERR_INVALID_ARG;
+    if ((long long)H * (long long)W > 2147483646LL) return CCL_ERR_UNSUPPORTED;
+    // the input span and the output span must not overlap
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(img);
+    const uintptr_t i1 = i0 + (size_t)(H - 1) * pitch + (size_t)W;
+    const uintptr_t o0 = reinterpret_cast<uintptr_t>(labels);
+    const uintptr_t o1 = o0 + (size_t)H * (size_t)W * sizeof(int32_t);
+    if (i0 < o1 && o0 < i1) return CCL_ERR_INVALID_ARG;
+    return CCL_OK;
+}
+
+int current_cap() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_cap;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ccl_status_string(int status) {
+    switch (status) {
+        case CCL_OK: return "CCL_OK";
+        case CCL_ERR_INVALID_ARG: return "CCL_ERR_INVALID_ARG";
+        case CCL_ERR_UNSUPPORTED: return "CCL_ERR_UNSUPPORTED";
+        case CCL_ERR_OUT_OF_MEMORY: return "CCL_ERR_OUT_OF_MEMORY";
+        case CCL_ERR_CUDA: return "CCL_ERR_CUDA";
+        case CCL_ERR_DEVICE_TIMEOUT: return "CCL_ERR_DEVICE_TIMEOUT";
+        case CCL_ERR_BUSY: return "CCL_ERR_BUSY";
+        case CCL_ERR_NOT_FOUND: return "CCL_ERR_NOT_FOUND";
+        default: return "CCL_ERR_UNKNOWN";
+    }
+}
+
+int ccl_version(void) { return 100; }
+
+void ccl_debug_set_iteration_cap(int cap) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_cap = cap > 0 ? cap : 0;
+}
+
+ccl_status ccl_workspace_size(int H, int W, int connectivity, size_t *bytes) {
+    if (!bytes || H < 0 || W < 0 || (connectivity != 4 && connectivity != 8)) return CCL_ERR_INVALID_ARG;
+    if ((long long)H * (long long)W > 2147483646LL) return CCL_ERR_UNSUPPORTED;
+    *bytes = (H == 0 || W == 0) ? 0 : ccl::workspace_bytes(H, W);
+    return CCL_OK;
+}
+
+ccl_status ccl_label_ws(const uint8_t *img, int H, int W, size_t pitch, int connectivity, int32_t *labels,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    ccl_status st = check_image_args(img, H, W, pitch, connectivity, labels);
+    if (st != CCL_OK || H == 0 || W == 0) return st;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+        workspace_bytes < ccl::workspace_bytes(H, W))
+        return CCL_ERR_INVALID_ARG;
+    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, workspace,
+                          static_cast<cudaStream_t>(stream), current_cap()) != 0)
+        return CCL_ERR_CUDA;
+    return CCL_OK;
+}
+
+ccl_status ccl_label(const uint8_t *img, int H, int W, size_t pitch, int connectivity, int32_t *labels,
+                     void *stream) {
+    ccl_status st = check_image_args(img, H, W, pitch, connectivity, labels);
+    if (st != CCL_OK || H == 0 || W == 0) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t need = ccl::workspace_bytes(H, W);
+    void *ws = nullptr;
+    int cap = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DevBuf &b = g_scratch[{dev, s}];
+        if (b.bytes < need) {
+            // the old buffer may still be in use by earlier work on this stream
+            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+            st = grow(b, need);
+            if (st != CCL_OK) return st;
+        }
+        ws = b.ptr;
+        cap = g_cap;
+    }
+    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, ws, s, cap) != 0) return CCL_ERR_CUDA;
+    return CCL_OK;
+}
+
+ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,
+                          int32_t *host_labels, void *stream) {
+    ccl_status st = check_image_args(host_img, H, W, pitch, connectivity, host_labels);
+    if (st != CCL_OK || H == 0 || W == 0) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t dpitch = ((size_t)W + 15) & ~(size_t)15;
+    const size_t img_bytes = dpitch * (size_t)H;
+    const size_t lab_bytes = (size_t)H * (size_t)W * sizeof(int32_t);
+    const size_t need = ccl::workspace_bytes(H, W);
+    void *ws, *dimg, *dlab;
+    int cap;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DevBuf &b = g_scratch[{dev, s}];
+        DevBuf &bi = g_host_img[{dev, s}];
+        DevBuf &bl = g_host_lab[{dev, s}];
+        if (b.bytes < need || bi.bytes < img_bytes || bl.bytes < lab_bytes) {
+            if (cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+            if ((st = grow(b, need)) != CCL_OK) return st;
+            if ((st = grow(bi, img_bytes)) != CCL_OK) return st;
+            if ((st = grow(bl, lab_bytes)) != CCL_OK) return st;
+        }
+        ws = b.ptr;
+        dimg = bi.ptr;
+        dlab = bl.ptr;
+        cap = g_cap;
+    }
+    if (cudaMemcpy2DAsync(dimg, dpitch, host_img, pitch, (size_t)W, (size_t)H, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return CCL_ERR_CUDA;
+    if (ccl::launch_label(static_cast<const uint8_t *>(dimg), H, W, dpitch, connectivity,
+                          static_cast<int32_t *>(dlab), ws, s, cap) != 0)
+        return CCL_ERR_CUDA;
+    if (cudaMemcpyAsync(host_labels, dlab, lab_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CCL_ERR_CUDA;
+    return ccl_get_device_status(stream);
+}
+
+ccl_status ccl_get_device_status(void *stream) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CCL_ERR_CUDA;
+    int v = 0;
+    if (ccl::read_and_clear_device_error(&v) != 0) return CCL_ERR_CUDA;
+    return v ? CCL_ERR_DEVICE_TIMEOUT : CCL_OK;
+}
+
+}  // extern "C"

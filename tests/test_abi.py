@@ -1,0 +1,92 @@
+"""The C-ABI library loads, exports every symbol its header declares, and
+applies its host-side argument checks without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1712_09789_gb300 import build as ccl_build
+from paper_1712_09789_gb300 import ccl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))
+           if f.endswith(".h")]
+
+
+def declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("ccl_") and not name.endswith("_t"):
+                names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ccl_build.build()
+    return ccl.load()
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for must in ("ccl_label", "ccl_label_ws", "ccl_workspace_size", "ccl_label_host",
+                 "ccl_get_device_status", "ccl_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    raw = ctypes.CDLL(ccl.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_status_strings(lib):
+    assert ccl.ccl_status_string(0) == "CCL_OK"
+    assert ccl.ccl_status_string(5) == "CCL_ERR_DEVICE_TIMEOUT"
+    assert ccl.ccl_status_string(999) == "CCL_ERR_UNKNOWN"
+    assert ccl.ccl_version() >= 100
+
+
+def test_workspace_size_host_logic(lib):
+    assert ccl.ccl_workspace_size(0, 10) == 0
+    a = ccl.ccl_workspace_size(32, 128)
+    b = ccl.ccl_workspace_size(33, 129)  # four tiles instead of one
+    assert a > 0 and b > a
+    assert ccl.ccl_workspace_size(8192, 8192) < 64 * 1024 * 1024
+    with pytest.raises(ccl.CclError):
+        ccl.ccl_workspace_size(-1, 5)
+    with pytest.raises(ccl.CclError) as e:
+        ccl.ccl_workspace_size(65536, 32768)  # H*W = 2^31 > 2^31 - 2
+    assert e.value.status == ccl.CCL_ERR_UNSUPPORTED
+
+
+def test_argument_checks_before_any_device_work(lib):
+    f = lib.ccl_label
+    dummy_in, dummy_out = 0x10000, 0x90000000
+    # connectivity
+    assert f(dummy_in, 4, 4, 4, 6, dummy_out, None) == ccl.CCL_ERR_INVALID_ARG
+    # negative sizes
+    assert f(dummy_in, -1, 4, 4, 8, dummy_out, None) == ccl.CCL_ERR_INVALID_ARG
+    # pitch < W
+    assert f(dummy_in, 4, 8, 4, 8, dummy_out, None) == ccl.CCL_ERR_INVALID_ARG
+    # NULL pointers
+    assert f(None, 4, 4, 4, 8, dummy_out, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(dummy_in, 4, 4, 4, 8, None, None) == ccl.CCL_ERR_INVALID_ARG
+    # too many pixels for int32 labels
+    assert f(dummy_in, 65536, 32768, 65536, 8, dummy_out, None) == ccl.CCL_ERR_UNSUPPORTED
+    # overlapping input and output
+    assert f(dummy_in, 16, 16, 16, 8, dummy_in + 64, None) == ccl.CCL_ERR_INVALID_ARG
+    # empty images are a no-op
+    assert f(None, 0, 16, 16, 8, None, None) == ccl.CCL_OK
+    assert f(None, 16, 0, 16, 4, None, None) == ccl.CCL_OK
+    # caller-owned scratch must be present, aligned and large enough
+    g = lib.ccl_label_ws
+    assert g(dummy_in, 32, 32, 32, 8, dummy_out, None, 1 << 20, None) == ccl.CCL_ERR_INVALID_ARG
+    assert g(dummy_in, 32, 32, 32, 8, dummy_out, 0x20000 + 8, 1 << 20, None) == ccl.CCL_ERR_INVALID_ARG
+    assert g(dummy_in, 32, 32, 32, 8, dummy_out, 0x20000, 16, None) == ccl.CCL_ERR_INVALID_ARG
