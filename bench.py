@@ -1,0 +1,431 @@
+#!/usr/bin/env python3
+"""Benchmark of the block-based CCL hot path on GB300.
+
+Default workload (one "step"): the 4096x4096 single-image set -- i.i.d.
+Bernoulli foreground at densities 0.1..0.9 and granular noise (g = 4, 16) at
+0.5, seeds 0..2 (33 images) -- each labelled with 4- and 8-connectivity
+through ``ccl_label`` (66 labelings, 1.107 Gpixel per step).  Inputs are
+resident in HBM when the timed region starts; 33 distinct inputs and 66
+distinct outputs (4.98 GB) cycle through every step, so nothing of one step
+is still in the 129 MB L2 when the same image comes back.
+
+The JSON line carries, besides the contract keys:
+  roofline      the dominant kernel's algorithmic bytes per launch divided by
+                its mean CUDA-event duration over the timed region, against
+                the measured HBM copy bandwidth;
+  cpu_baseline  the CPU oracle timed on a bounded sample of the same work;
+  e2e           the same metric through ``ccl_label_host`` (host buffers,
+                copies inside the timed region);
+  clocks        SM clocks and throttle reasons sampled during the timed region;
+  extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
+                between repetitions) with its per-kernel breakdown.
+
+``--impl reference`` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gpixel/s & % HBM roofline, plain vs batched persistent; serving p50/p99 ms"
+UNIT = "Gpixel/s"
+BYTES_PER_PIXEL = 5          # 1 B image read + 4 B label written
+KERNEL_BYTES_PER_PIXEL = {   # algorithmic bytes of each kernel per image pixel
+    "k_local_border": 1,     # reads the image once
+    "k_block_merge": 0,      # border records only
+    "k_flatten": 0,
+    "k_relabel": 5,          # reads the image, writes every label
+}
+SIDE = 4096
+CONNS = (4, 8)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured", float(p.get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 6800.0, "fallback", 2070.0
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1712_09789_gb300", "csrc")
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when there is none or the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"^csrc_digest:\s*([0-9a-f]+)", text, re.M)
+    m_b = re.search(r"^dram_bytes_per_launch_4096:\s*([0-9.eE+]+)", text, re.M)
+    if not m_sha or not m_b or m_sha.group(1) != csrc_digest():
+        return None
+    return float(m_b.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50", "-i", str(self.gpu_index), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def noise_4096_images():
+    from paper_1712_09789_gb300 import synth
+
+    return list(synth.noise_4096_set(SIDE))
+
+
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    """The reference arm: the CPU oracle on the host, one bounded sample of the
+    step's work per step."""
+    rank, world, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    from paper_1712_09789_gb300 import synth
+
+    oracle.build()
+    imgs = [img for _, img in synth.noise_4096_set(SIDE, seeds=(0,))]
+    # calibrate: seconds per row of a 4096-wide image
+    t0 = time.perf_counter()
+    oracle.label(np.ascontiguousarray(imgs[4][:256]), 8)
+    per_row = (time.perf_counter() - t0) / 256
+    budget = 90.0
+    rows = int(max(8, min(SIDE, budget / max(1, args.steps + args.warmup) / per_row)))
+    work = [(img, c) for c in CONNS for img in imgs]
+
+    def step(i):
+        img, conn = work[i % len(work)]
+        oracle.label(np.ascontiguousarray(img[:rows]), conn)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    px = rows * SIDE * args.steps
+    value = px / dt / 1e9
+    sample = (f"{rows}-row x 4096 strips of the 4096x4096 noise set (seed 0), cycling densities, "
+              f"granularities and both connectivities, one strip per step")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "4096x4096 uint8 noise set (configs: density sweep + granular), "
+                               "CPU oracle two-pass union-find", "rows_per_step": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1712_09789_gb300 import build as lib_build
+    from paper_1712_09789_gb300 import ccl
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        lib_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    ccl.load()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    named = noise_4096_images()
+    host = [img for _, img in named]
+    dev = [torch.from_numpy(img).cuda() for img in host]
+    work = [(i, c) for c in CONNS for i in range(len(dev))]
+    outs = [torch.empty((SIDE, SIDE), dtype=torch.int32, device="cuda") for _ in work]
+    px_step = len(work) * SIDE * SIDE
+
+    def step():
+        for k, (i, c) in enumerate(work):
+            ccl.ccl_label(dev[i], c, labels=outs[k])
+
+    for _ in range(args.warmup):
+        step()
+    status = ccl.ccl_get_device_status()
+    if status != ccl.CCL_OK:
+        raise RuntimeError(f"device status after warm-up: {ccl.ccl_status_string(status)}")
+
+    # -- timed region: device time with CUDA events, per-kernel events on the
+    # launching stream (the current stream, which ccl_label uses)
+    cvd = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(cvd[local].strip() if local < len(cvd) else str(local))
+    ccl.ccl_debug_kernel_timing(True)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ktimes = ccl.ccl_debug_kernel_times()
+    ccl.ccl_debug_kernel_timing(False)
+    status = ccl.ccl_get_device_status()
+    if status != ccl.CCL_OK:
+        raise RuntimeError(f"device status after timed region: {ccl.ccl_status_string(status)}")
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    value = world * px_step * args.steps / (ms / 1e3) / 1e9
+
+    hbm_gbs, peak_kind, _ = load_peaks()
+    total_kernel_ms = sum(v[0] for v in ktimes.values()) or 1.0
+    dominant = max(ktimes, key=lambda k: ktimes[k][0])
+    dom_ms, dom_n = ktimes[dominant]
+    dom_avg_s = dom_ms / max(1, dom_n) / 1e3
+    algo_bytes = KERNEL_BYTES_PER_PIXEL[dominant] * SIDE * SIDE
+    achieved = algo_bytes / dom_avg_s / 1e9
+    traffic = recorded_traffic(dominant)
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_gbs,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
+                "mean_launch_us": dom_avg_s * 1e6}
+    kernels = {k: {"launches": n, "mean_us": (t / n * 1e3) if n else None,
+                   "share": t / total_kernel_ms} for k, (t, n) in ktimes.items()}
+    path_frac = value * 1e9 / world * BYTES_PER_PIXEL / (hbm_gbs * 1e9)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {
+            "workload": "4096x4096 uint8 noise set: Bernoulli p=0.1..0.9 and granular g=4,16 at p=0.5, "
+                        "seeds 0..2 (33 images), each with 4- and 8-connectivity (66 labelings/step), "
+                        "plain ccl_label path",
+            "images": len(dev), "H": SIDE, "W": SIDE, "connectivity": list(CONNS),
+            "pixels_per_step": px_step,
+            "l2": "inputs larger than L2: 33 inputs (554 MB) and 66 outputs (4.4 GB) cycle every step",
+        },
+        "hbm_roofline_frac_path": path_frac,
+        "roofline": roofline,
+        "kernels": kernels,
+        "gpu_launches": int(sum(n for _, n in ktimes.values())),
+        "clocks": clocks,
+    }
+
+    # -- extra: the 8192x8192 Bernoulli(0.5) 8-connectivity image
+    if rank == 0 and not args.no_extra:
+        line["extra"] = bench_8192(torch, ccl, hbm_gbs)
+
+    # -- e2e through host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        line["e2e"] = bench_e2e(torch, ccl, host, work, args, world, max_over_ranks)
+
+    # -- CPU oracle on a bounded sample, rank 0 at N = 1 only
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = bench_cpu(host, work, outs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def bench_8192(torch, ccl, hbm_gbs):
+    from paper_1712_09789_gb300 import synth
+
+    N = 8192
+    img = torch.from_numpy(synth.bernoulli(N, N, 0.5, 0)).cuda()
+    out = torch.empty((N, N), dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ccl.ccl_label(img, 8, labels=out)
+    reps = 30
+    times = []
+    ccl.ccl_debug_kernel_timing(True)
+    for _ in range(reps):
+        flush.fill_(1)  # evict the previous repetition's data from L2
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ccl.ccl_label(img, 8, labels=out)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    kt = ccl.ccl_debug_kernel_times()
+    ccl.ccl_debug_kernel_timing(False)
+    med = statistics.median(times)
+    gpx = N * N / (med / 1e3) / 1e9
+    return {"workload": "8192x8192 Bernoulli p=0.5 seed 0, 8-connectivity, L2 flushed between reps",
+            "median_us": med * 1e3, "min_us": min(times) * 1e3, "mean_us": statistics.mean(times) * 1e3,
+            "stdev_us": statistics.pstdev(times) * 1e3,
+            "gpixel_s": gpx, "hbm_roofline_frac": gpx * 1e9 * BYTES_PER_PIXEL / (hbm_gbs * 1e9),
+            "kernels_mean_us": {k: (t / n * 1e3 if n else None) for k, (t, n) in kt.items()}}
+
+
+def bench_e2e(torch, ccl, host, work, args, world, max_over_ranks):
+    import numpy as np
+
+    pinned = [torch.from_numpy(h).pin_memory() for h in host]
+    pin_np = [p.numpy() for p in pinned]
+    out = torch.empty((SIDE, SIDE), dtype=torch.int32).pin_memory().numpy()
+    steps = max(1, min(3, args.steps))
+
+    def step():
+        for i, c in work:
+            ccl.ccl_label_host(pin_np[i], c, labels=out)
+
+    step()  # warm-up: grows the library's staging buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    dt = max_over_ranks(time.perf_counter() - t0)
+    px = len(work) * SIDE * SIDE
+    return {"value": world * px * steps / dt / 1e9, "unit": UNIT,
+            "h2d_bytes_per_step": len(work) * SIDE * SIDE,
+            "d2h_bytes_per_step": len(work) * SIDE * SIDE * 4,
+            "steps": steps, "api": "ccl_label_host (pinned host buffers, synchronous per image)"}
+
+
+def bench_cpu(host, work, outs):
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    budget = 15.0
+    done, px, checked = 0, 0, 0
+    t_total = 0.0
+    for k, (i, c) in enumerate(work):
+        t0 = time.perf_counter()
+        want = oracle.label(host[i], c)
+        t_total += time.perf_counter() - t0
+        px += host[i].size
+        done += 1
+        if np.array_equal(outs[k].cpu().numpy(), want):
+            checked += 1
+        if t_total >= budget:
+            break
+    return {"value": px / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {done} of the step's 66 labelings (4096x4096 each), single thread",
+            "parity_bit_exact": f"{checked}/{done}"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

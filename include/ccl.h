@@ -128,6 +128,23 @@ ccl_status ccl_get_device_status(void *stream);
  */
 void ccl_debug_set_iteration_cap(int cap);
 
+/*
+ * Benchmark hook.  While enabled, every call records CUDA events on its own
+ * stream around each of its kernels (kind 0: tile-local labelling, 1: block
+ * merge, 2: root flatten, 3: relabel) and their durations accumulate per
+ * kind.  Enabling or disabling waits for pending events and clears the sums.
+ */
+void ccl_debug_kernel_timing(int enable);
+
+/*
+ * Waits for the recorded events and writes up to n per-kind sums in
+ * milliseconds and launch counts.  Returns the number of kernel kinds.
+ */
+int ccl_debug_kernel_times(double *ms_sum, long long *counts, int n);
+
+/* Kernel name of a kind (static string; "" when out of range). */
+const char *ccl_debug_kernel_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

@@ -52,6 +52,9 @@ _SIGS = {
                                   _c.c_void_p, _c.c_void_p]),
     "ccl_get_device_status": (_c.c_int, [_c.c_void_p]),
     "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
+    "ccl_debug_kernel_timing": (None, [_c.c_int]),
+    "ccl_debug_kernel_times": (_c.c_int, [_c.POINTER(_c.c_double), _c.POINTER(_c.c_longlong), _c.c_int]),
+    "ccl_debug_kernel_name": (_c.c_char_p, [_c.c_int]),
 }
 
 
@@ -182,3 +185,17 @@ def ccl_get_device_status(stream=None) -> int:
 
 def ccl_debug_set_iteration_cap(cap: int) -> None:
     load().ccl_debug_set_iteration_cap(cap)
+
+
+def ccl_debug_kernel_timing(enable: bool) -> None:
+    load().ccl_debug_kernel_timing(1 if enable else 0)
+
+
+def ccl_debug_kernel_times() -> dict:
+    """Per-kernel ``{name: (total_ms, launches)}`` since timing was enabled."""
+    lib = load()
+    n = lib.ccl_debug_kernel_times(None, None, 0)
+    ms = (ctypes.c_double * n)()
+    cnt = (ctypes.c_longlong * n)()
+    lib.ccl_debug_kernel_times(ms, cnt, n)
+    return {lib.ccl_debug_kernel_name(k).decode(): (ms[k], cnt[k]) for k in range(n)}

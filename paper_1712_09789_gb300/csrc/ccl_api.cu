@@ -180,6 +180,15 @@ ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch, i
     return ccl_get_device_status(stream);
 }
 
+void ccl_debug_kernel_timing(int enable) { ccl::timing_enable(enable != 0); }
+
+int ccl_debug_kernel_times(double *ms_sum, long long *counts, int n) {
+    if (!ms_sum || !counts || n < 0) return ccl::kKernelKinds;
+    return ccl::timing_read(ms_sum, counts, n);
+}
+
+const char *ccl_debug_kernel_name(int kind) { return ccl::kernel_kind_name(kind); }
+
 ccl_status ccl_get_device_status(void *stream) {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CCL_ERR_CUDA;
     int v = 0;

@@ -19,4 +19,11 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
 
+// Benchmark timing of the kernels enqueued by launch_label().
+constexpr int kKindLocal = 0, kKindMerge = 1, kKindFlatten = 2, kKindRelabel = 3;
+constexpr int kKernelKinds = 4;
+void timing_enable(bool on);
+int timing_read(double *ms, long long *count, int n);
+const char *kernel_kind_name(int k);
+
 }  // namespace ccl

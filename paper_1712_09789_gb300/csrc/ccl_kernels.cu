@@ -20,6 +20,10 @@
 // (often an L2 hit) and 4 B label write in k_relabel, plus the border records
 // (2 B per border pixel) and union-find entries (8 B per border component).
 #include <cstdint>
+#include <deque>
+#include <mutex>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "ccl_internal.h"
@@ -298,6 +302,102 @@ static Scratch carve(void *ws, int H, int W) {
     return s;
 }
 
+// ---------------------------------------------------------------------------
+// Per-kernel timing for benchmarks: when on, an event is recorded on the
+// launching stream before the first kernel of a call and after each kernel;
+// consecutive events bracket one kernel.  Completed events are folded into
+// per-kind sums and returned to a pool, so long runs hold few events.
+
+namespace {
+
+struct TimingRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+struct TimingState {
+    std::mutex mu;
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::deque<TimingRec> pending;
+    double ms[kKernelKinds] = {};
+    long long count[kKernelKinds] = {};
+} g_timing;
+
+cudaEvent_t timing_event() {
+    if (!g_timing.pool.empty()) {
+        cudaEvent_t e = g_timing.pool.back();
+        g_timing.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void timing_fold(bool wait) {
+    while (!g_timing.pending.empty()) {
+        TimingRec r = g_timing.pending.front();
+        if (wait) {
+            cudaEventSynchronize(r.b);
+        } else if (cudaEventQuery(r.b) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_timing.ms[r.kind] += ms;
+            g_timing.count[r.kind] += 1;
+        } else {
+            cudaGetLastError();
+        }
+        g_timing.pending.pop_front();
+        // r.b opens the next record of the same call, so only r.a is free
+        // now; the last record of a call frees its closing event as well.
+        g_timing.pool.push_back(r.a);
+        if (r.kind == kKernelKinds - 1) g_timing.pool.push_back(r.b);
+    }
+}
+
+// Records an event on `s` and, when `kind` >= 0, closes a record for the
+// kernel launched since `prev`.  Returns the new event (nullptr when off).
+cudaEvent_t timing_mark(cudaStream_t s, cudaEvent_t prev, int kind) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    if (!g_timing.on) return nullptr;
+    timing_fold(false);
+    cudaEvent_t e = timing_event();
+    cudaEventRecord(e, s);
+    if (kind >= 0 && prev) g_timing.pending.push_back({kind, prev, e});
+    return e;
+}
+
+}  // namespace
+
+void timing_enable(bool on) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    timing_fold(true);
+    g_timing.on = on;
+    for (int k = 0; k < kKernelKinds; ++k) {
+        g_timing.ms[k] = 0.0;
+        g_timing.count[k] = 0;
+    }
+}
+
+int timing_read(double *ms, long long *count, int n) {
+    std::lock_guard<std::mutex> lk(g_timing.mu);
+    timing_fold(true);
+    for (int k = 0; k < n && k < kKernelKinds; ++k) {
+        ms[k] = g_timing.ms[k];
+        count[k] = g_timing.count[k];
+    }
+    return kKernelKinds;
+}
+
+const char *kernel_kind_name(int k) {
+    static const char *names[kKernelKinds] = {"k_local_border", "k_block_merge", "k_flatten", "k_relabel"};
+    return (k >= 0 && k < kKernelKinds) ? names[k] : "";
+}
+
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap) {
     ImageArgs a;
@@ -317,16 +417,25 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
     const long long slots = (long long)nt * kSlots + 16;
     const int local_cap = cap > 0 ? cap : 2 * kNodes;
     const int global_cap = cap > 0 ? cap : (int)(slots < (1LL << 30) ? slots : (1LL << 30));
+    cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
         k_local_border<true><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<true><<<nt, kThreads, 0, stream>>>(s, a.ntx, a.nty, global_cap);
+        ev = timing_mark(stream, ev, kKindMerge);
         k_flatten<<<nt, kThreads, 0, stream>>>(s, global_cap);
+        ev = timing_mark(stream, ev, kKindFlatten);
         k_relabel<true><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        ev = timing_mark(stream, ev, kKindRelabel);
     } else {
         k_local_border<false><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<false><<<nt, kThreads, 0, stream>>>(s, a.ntx, a.nty, global_cap);
+        ev = timing_mark(stream, ev, kKindMerge);
         k_flatten<<<nt, kThreads, 0, stream>>>(s, global_cap);
+        ev = timing_mark(stream, ev, kKindFlatten);
         k_relabel<false><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        ev = timing_mark(stream, ev, kKindRelabel);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
