@@ -113,6 +113,30 @@ ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch,
                           int connectivity, int32_t *host_labels, void *stream);
 
 /*
+ * ccl_label() for callers that may not allocate device memory while they run
+ * -- e.g. a program that gave all of the GPU's memory to its own pool at
+ * start-up, or a latency-critical loop that must not call cudaMalloc/cudaFree
+ * because those can block and synchronise the whole device.  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ *
+ * The caller still passes img and labels (same meaning as ccl_label()).  The
+ * scratch is a fixed array of ccl_noalloc_max_workspace_bytes() bytes
+ * (16 MiB) that every GPU loading the library reserves until the process
+ * exits; this call allocates nothing.  Images whose ccl_workspace_size()
+ * exceeds that limit (for example more than 4096 x 8192 pixels) are rejected
+ * with CCL_ERR_UNSUPPORTED and nothing is enqueued.  The first call on a device
+ * looks up the array's device address, so make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race on it and must be serialised by
+ * the caller.  Leftover contents from earlier calls are never read.
+ */
+ccl_status ccl_label_noalloc(const uint8_t *img, int H, int W, size_t pitch, int connectivity,
+                             int32_t *labels, void *stream);
+
+/* Size in bytes of the fixed scratch array used by ccl_label_noalloc(). */
+size_t ccl_noalloc_max_workspace_bytes(void);
+
+/*
  * Waits for `stream`, then reports and clears the current device's error
  * word: CCL_ERR_DEVICE_TIMEOUT when a union-find loop reached its iteration
  * cap since the last check (its outputs are then not valid), CCL_ERR_CUDA when

@@ -51,6 +51,9 @@ _SIGS = {
     "ccl_label_host": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
                                   _c.c_void_p, _c.c_void_p]),
     "ccl_get_device_status": (_c.c_int, [_c.c_void_p]),
+    "ccl_label_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
+                                     _c.c_void_p]),
+    "ccl_noalloc_max_workspace_bytes": (_c.c_size_t, []),
     "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
     "ccl_debug_kernel_timing": (None, [_c.c_int]),
     "ccl_debug_kernel_times": (_c.c_int, [_c.POINTER(_c.c_double), _c.POINTER(_c.c_longlong), _c.c_int]),
@@ -134,6 +137,23 @@ def ccl_label(img, connectivity: int = 8, labels=None, stream=None):
                           _stream_ptr(stream, img.device))
     _check(st, "ccl_label")
     return labels
+
+
+def ccl_label_noalloc(img, connectivity: int = 8, labels=None, stream=None):
+    """``ccl_label`` without any device allocation (``ccl_label_noalloc``):
+    the scratch is the library's fixed per-device array, so this suits callers
+    that may not allocate while running.  ``labels`` should be preallocated by
+    such callers; overlapping calls race on the shared scratch."""
+    H, W, pitch = _image_args(img)
+    labels = _labels_for(img, labels)
+    st = load().ccl_label_noalloc(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+                                  _stream_ptr(stream, img.device))
+    _check(st, "ccl_label_noalloc")
+    return labels
+
+
+def ccl_noalloc_max_workspace_bytes() -> int:
+    return load().ccl_noalloc_max_workspace_bytes()
 
 
 def ccl_workspace_size(H: int, W: int, connectivity: int = 8) -> int:

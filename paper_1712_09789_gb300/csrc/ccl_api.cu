@@ -71,6 +71,16 @@ int current_cap() {
 
 }  // namespace
 
+namespace ccl {
+
+ccl_status check_image_args_api(const void *img, int H, int W, size_t pitch, int conn, const void *labels) {
+    return check_image_args(img, H, W, pitch, conn, labels);
+}
+
+int iteration_cap_api() { return current_cap(); }
+
+}  // namespace ccl
+
 extern "C" {
 
 const char *ccl_status_string(int status) {

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/ccl.h"
+
 namespace ccl {
 
 // Scratch bytes needed by launch_label() for an H x W image.
@@ -18,6 +20,11 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
 
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
+
+// Argument checks and iteration cap of the C ABI, for entry points that live
+// in other translation units (same rules as ccl_label()).
+ccl_status check_image_args_api(const void *img, int H, int W, size_t pitch, int conn, const void *labels);
+int iteration_cap_api();
 
 // Benchmark timing of the kernels enqueued by launch_label().
 constexpr int kKindLocal = 0, kKindMerge = 1, kKindFlatten = 2, kKindRelabel = 3;
