@@ -42,11 +42,11 @@ if ROOT not in sys.path:
 METRIC = "Gpixel/s & % HBM roofline, plain vs batched persistent; serving p50/p99 ms"
 UNIT = "Gpixel/s"
 BYTES_PER_PIXEL = 5          # 1 B image read + 4 B label written
-KERNEL_BYTES_PER_PIXEL = {   # algorithmic bytes of each kernel per image pixel
-    "k_local_border": 1,     # reads the image once
-    "k_block_merge": 0,      # border records only
-    "k_flatten": 0,
-    "k_relabel": 5,          # reads the image, writes every label
+KERNEL_BYTES_PER_PIXEL = {   # the path's algorithmic bytes each kernel moves, per pixel
+    "k_block_local": 1,      # reads the image once
+    "k_block_merge": 0,      # block border records only
+    "k_flatten": 0,          # border slots only
+    "k_block_write": 4,      # writes every label once
 }
 SIDE = 4096
 CONNS = (4, 8)

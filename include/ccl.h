@@ -121,7 +121,7 @@ ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch,
  *
  * The caller still passes img and labels (same meaning as ccl_label()).  The
  * scratch is a fixed array of ccl_noalloc_max_workspace_bytes() bytes
- * (16 MiB) that every GPU loading the library reserves until the process
+ * (64 MiB) that every GPU loading the library reserves until the process
  * exits; this call allocates nothing.  Images whose ccl_workspace_size()
  * exceeds that limit (for example more than 4096 x 8192 pixels) are rejected
  * with CCL_ERR_UNSUPPORTED and nothing is enqueued.  The first call on a device

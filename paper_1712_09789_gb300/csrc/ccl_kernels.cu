@@ -1,24 +1,26 @@
 // ccl_kernels.cu -- the three steps of the block-based labeller as sm_103a
 // kernels, and the launcher that enqueues them on a stream.
 //
-//   k_local_border  step 1, Kernel 1 (Sec. 3.1): tile-local coarse labelling
-//                   and refinement in shared memory; writes only what the
-//                   block merge needs -- the tile's border record (which
-//                   border-component every border pixel belongs to) and one
-//                   union-find entry per border-touching component.
-//   k_block_merge   step 2, Kernel 2 (Sec. 3.2): only pixel pairs that
-//                   straddle a tile edge are examined; matching foreground
-//                   pairs merge their components in the global union-find.
-//   k_flatten       step 3, first half (Sec. 3.3): root-find for every
-//                   border component, so each entry names its final root.
-//   k_relabel       step 3, second half: recomputes the tile-local labelling
-//                   from the image (instead of storing it), looks up the
-//                   final key of each border component and writes
-//                   1 + key for every foreground pixel, 0 for background.
+//   k_block_local   step 1, Kernel 1 (Sec. 3.1) on 512 x 64 blocks: every
+//                   thread labels its 32 x 8 lane tile by coarse labelling
+//                   (row connection by bit operations; column connection to
+//                   the first run above; unification through the list) and
+//                   refinement (merging the further runs above); the lane
+//                   tiles of the block are then merged along their seams.
+//                   Writes the block's row masks, one value per run (block key
+//                   of its root, or its border slot), the border record of
+//                   the block and one global union-find entry per border
+//                   component.
+//   k_block_merge   step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
+//                   pairs that straddle a block edge are examined.
+//   k_flatten       step 3, first half (Sec. 3.3): root-find for every border
+//                   slot.
+//   k_block_write   step 3, second half: expands the per-run values over the
+//                   row masks and writes every label once.
 //
-// HBM traffic per pixel: 1 B image read in k_local_border, 1 B image read
-// (often an L2 hit) and 4 B label write in k_relabel, plus the border records
-// (2 B per border pixel) and union-find entries (8 B per border component).
+// HBM traffic per pixel: 1 B image read, 4 B label write, plus the row masks
+// (1/8 B written, 1/8 B read) and the per-run values (1 B label and 2 B value
+// per run, written and read once), most of which stay in L2.
 #include <cstdint>
 #include <deque>
 #include <mutex>
@@ -26,8 +28,8 @@
 
 #include <cuda_runtime.h>
 
+#include "ccl_block.cuh"
 #include "ccl_internal.h"
-#include "ccl_tile.cuh"
 
 namespace ccl {
 
@@ -38,141 +40,531 @@ struct ImageArgs {
     int32_t *labels;
     size_t pitch;
     int H, W;
-    int ntx, nty;
+    int nbx, nby;
     bool vec_ok;       // img and pitch 16-byte aligned
     bool out_vec_ok;   // labels 16-byte aligned and W % 4 == 0
 };
 
+// Per-block scratch regions (all sized for capacity; only used parts are
+// touched).
 struct Scratch {
-    uint16_t *edges;   // [ntiles][kEdge]
-    uint64_t *P;       // [ntiles][kSlots]
-    int32_t *nslots;   // [ntiles]
+    uint32_t *masks;   // [blocks][128 lane tiles][8 rows]
+    uint4 *lstream;    // [blocks][kLChunks][128]: run labels, 16 per chunk
+    uint4 *vstream;    // [blocks][kVChunks][128]: run values, 8 per chunk
+    uint16_t *edges;   // [blocks][kEdge]
+    uint64_t *P;       // [blocks][kSlots]
+    int32_t *nslots;   // [blocks]
 };
-
-__device__ __forceinline__ void clear_tile_state(TileSmem &sm) {
-    for (int i = threadIdx.x; i < kNodes / 32; i += kThreads) sm.border[i] = 0u;
-    if (threadIdx.x == 0) sm.err = 0;
-}
 
 __device__ __forceinline__ void report(int err) {
     if (err) atomicOr(&g_device_error, err);
 }
 
 // ---------------------------------------------------------------------------
+struct LocalSmem {
+    uint16_t par[kLabCap * kThreads];            // list entries, see ccl_block.cuh
+    uint8_t lab[3][kLW][kLabPitch];              // run-start labels: row 0, then two alternating rows
+    uint8_t lcol[kLH][kLabPitch];                // label of the run holding column 0, per row
+    uint8_t rcol[kLH][kLabPitch];                // label of the run holding column 31, per row
+    uint32_t mask[kLH][kThreads];                // row masks
+    uint32_t border[kLabCap * kThreads / 32];    // bit per id: root touching the block border
+    uint32_t prefix[kLabCap * kThreads / 32];
+    uint32_t warp_tot[kThreads / 32];
+    int nslots;
+    int err;
+};
+
+__device__ __forceinline__ int lab_buf(int r) { return r == 0 ? 0 : 1 + ((r - 1) & 1); }
+
+// Border record entry of a run value: its slot, or background when the value
+// is not a border slot (only possible after an iteration cap was hit).
+__device__ __forceinline__ uint16_t border_slot(uint16_t v) {
+    return (v & kBorderFlag) ? (uint16_t)(v & 0x3FFF) : kBg;
+}
+
+// 16 one-byte labels collected low byte first in a 128-bit shift register.
+struct ByteQueue {
+    uint64_t lo = 0, hi = 0;
+    __device__ __forceinline__ void push(uint32_t b) {
+        lo = (lo >> 8) | (hi << 56);
+        hi = (hi >> 8) | ((uint64_t)b << 56);
+    }
+    __device__ __forceinline__ uint4 bits() const {
+        return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
+    }
+};
+
+// 8 two-byte values collected low half first in a 128-bit shift register.
+struct HalfQueue {
+    uint32_t q0 = 0, q1 = 0, q2 = 0, q3 = 0;
+    __device__ __forceinline__ void push(uint32_t v) {
+        q0 = __funnelshift_r(q0, q1, 16);
+        q1 = __funnelshift_r(q1, q2, 16);
+        q2 = __funnelshift_r(q2, q3, 16);
+        q3 = (q3 >> 16) | (v << 16);
+    }
+    __device__ __forceinline__ uint4 bits() const { return make_uint4(q0, q1, q2, q3); }
+};
+
 template <bool kConn8>
-__global__ void __launch_bounds__(kThreads) k_local_border(ImageArgs a, Scratch s, int cap) {
-    __shared__ TileSmem sm;
-    const int t = blockIdx.x;
-    const int tx = t % a.ntx, ty = t / a.ntx;
-    const int x0 = tx * kTileW, y0 = ty * kTileH;
-    clear_tile_state(sm);
+__global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratch s, int cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    LocalSmem &sm = *reinterpret_cast<LocalSmem *>(smem_raw);
+    const int b = blockIdx.x;
+    const int bx = b % a.nbx, by = b / a.nbx;
+    const int x0 = bx * kBW, y0 = by * kBH;
+    const int t = threadIdx.x;
+    const int tx = t & (kBLX - 1), ty = t >> 4;
+    const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
+    int err = 0;
 
-    uint32_t m, S;
-    label_tile<kConn8>(sm, a.img, a.H, a.W, a.pitch, a.vec_ok, x0, y0, cap, m, S);
-    number_border_roots(sm);
+    for (int i = t; i < kLabCap * kThreads / 32; i += kThreads) sm.border[i] = 0u;
+    if (t == 0) sm.err = 0;
 
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint16_t *E = s.edges + (size_t)t * kEdge;
-    // border record: slot of the pixel's component, or kBg
+    // -- initialization: the lane tile's 8 rows as masks (all loads in flight
+    // at once; pixels outside the image are background)
+    uint32_t mrow[kLH];
+    if (a.vec_ok && xl + kLW <= a.W && yl + kLH <= a.H) {
+        uint4 raw[2 * kLH];
+        const uint8_t *p = a.img + (size_t)yl * a.pitch + xl;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int rr = k ? kTileH - 1 : 0;
-        const uint32_t mm = sm.rowm[w][rr];
-        uint16_t v = kBg;
-        if ((mm >> lane) & 1u) {
-            const int a0 = hibit(sm.runs[w][rr] & upto(lane));
-            v = (uint16_t)border_slot(sm, sm.parent[swz(rr * kTileW + kSubW * w + a0)]);
+        for (int r = 0; r < kLH; ++r) {
+            raw[2 * r] = ldg_nc16(p + (size_t)r * a.pitch);
+            raw[2 * r + 1] = ldg_nc16(p + (size_t)r * a.pitch + 16);
         }
-        E[(k ? kEdgeBottom : kEdgeTop) + kSubW * w + lane] = v;
+#pragma unroll
+        for (int r = 0; r < kLH; ++r) mrow[r] = nz16(raw[2 * r]) | (nz16(raw[2 * r + 1]) << 16);
+    } else {
+#pragma unroll
+        for (int r = 0; r < kLH; ++r) {
+            uint32_t m = 0;
+            const int y = yl + r;
+            if (y < a.H && xl < a.W) {
+                const uint8_t *p = a.img + (size_t)y * a.pitch + xl;
+                const int n = a.W - xl < kLW ? a.W - xl : kLW;
+                for (int i = 0; i < n; ++i) m |= (uint32_t)(__ldg(p + i) != 0) << i;
+            }
+            mrow[r] = m;
+        }
     }
-    if (w == 0) {
-        const uint16_t v = (m & 1u) ? (uint16_t)border_slot(sm, sm.parent[swz(lane * kTileW)]) : kBg;
-        E[kEdgeLeft + lane] = v;
+#pragma unroll
+    for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
+
+    // -- coarse labelling and refinement, row by row.  Every loop below runs
+    // the same number of rounds on all 32 lanes of a warp (the maximum any
+    // lane needs), so the 32 lane tiles advance in lockstep.
+    volatile uint16_t *vpar = sm.par;
+    uint32_t prevM = 0, prevS = 0;
+    int nlab = 0, nrun = 0;
+    ByteQueue lq;
+    uint4 *lout = s.lstream + (size_t)b * kLChunks * kThreads + t;
+#pragma unroll 1
+    for (int r = 0; r < kLH; ++r) {
+        const uint32_t m = sm.mask[r][t];
+        uint32_t S = m & ~(m << 1);                 // run starts
+        uint32_t E = m & ~(m >> 1);                 // run ends
+        uint8_t *cur = &sm.lab[lab_buf(r)][0][t];
+        const uint8_t *prev = &sm.lab[lab_buf(r > 0 ? r - 1 : 0)][0][t];
+        uint8_t lc = 0xFF, rc = 0xFF;
+        const int nmax = __reduce_max_sync(kFull, __popc(S));
+        for (int k = 0; k < nmax; ++k) {
+            const bool act = S != 0u;
+            const int a0 = act ? lobit(S) : 0;
+            const int a1 = act ? lobit(E) : 0;
+            S &= S - 1u;
+            E &= E - 1u;
+            const uint32_t P = act ? (prevM & touch_range<kConn8>(run_bits(a0, a1))) : 0u;
+            const bool linked = P != 0u;
+            const int u0 = linked ? lobit(P) : 0;
+            // column connection: the first run above that the run touches
+            int L = 0;
+            if (linked) L = prev[hibit(prevS & upto(u0)) * kLabPitch];
+            // unification: walk to the list's root (own lists only), halving
+            bool pend = linked;
+            for (int i = 0; __any_sync(kFull, pend); ++i) {
+                if (pend) {
+                    const uint16_t e = vpar[L * kThreads + t];
+                    if (e & kRoot) {
+                        pend = false;
+                    } else {
+                        const int p = e & (kLabCap - 1);
+                        const uint16_t g = vpar[p * kThreads + t];
+                        if (g & kRoot) {
+                            L = p;
+                            pend = false;
+                        } else {
+                            vpar[L * kThreads + t] = g;
+                            L = g & (kLabCap - 1);
+                        }
+                    }
+                }
+                if (i >= cap) {
+                    if (pend) err |= kErrLocalCap;
+                    break;
+                }
+            }
+            // no foreground above: a new list whose root is this run
+            if (act && !linked) {
+                L = nlab++;
+                vpar[L * kThreads + t] = (uint16_t)(kRoot | (r * kLW + a0));
+            }
+            // refinement: every further run above joins the same list; the
+            // larger label is hung under the smaller
+            uint32_t Q = linked ? (prevS & P & ~upto(u0)) : 0u;
+            for (int i = 0; __any_sync(kFull, Q != 0u); ++i) {
+                const bool hq = Q != 0u;
+                int L2 = 0;
+                if (hq) {
+                    L2 = prev[lobit(Q) * kLabPitch];
+                    Q &= Q - 1u;
+                }
+                bool pend2 = hq;
+                for (int j = 0; __any_sync(kFull, pend2); ++j) {
+                    if (pend2) {
+                        const uint16_t e = vpar[L2 * kThreads + t];
+                        if (e & kRoot) pend2 = false;
+                        else L2 = e & (kLabCap - 1);
+                    }
+                    if (j >= cap) {
+                        if (pend2) err |= kErrLocalCap;
+                        break;
+                    }
+                }
+                if (hq && L2 != L) {
+                    const int lo = L2 < L ? L2 : L, hi = L2 < L ? L : L2;
+                    vpar[hi * kThreads + t] = (uint16_t)lo;
+                    L = lo;
+                }
+                if (i >= cap) break;
+            }
+            if (act) {
+                cur[a0 * kLabPitch] = (uint8_t)L;
+                if (a0 == 0) lc = (uint8_t)L;
+                if (a1 == kLW - 1) rc = (uint8_t)L;
+                lq.push((uint32_t)L);
+                ++nrun;
+                if ((nrun & 15) == 0) lout[(size_t)((nrun >> 4) - 1) * kThreads] = lq.bits();
+            }
+        }
+        sm.lcol[r][t] = lc;
+        sm.rcol[r][t] = rc;
+        prevM = m;
+        prevS = m & ~(m << 1);
+        __syncwarp();
     }
-    if (w == kWarps - 1) {
-        uint16_t v = kBg;
-        if (m >> 31) v = (uint16_t)border_slot(sm, sm.parent[swz(lane * kTileW + kSubW * w + hibit(S))]);
-        E[kEdgeRight + lane] = v;
+    if (nrun & 15) {
+        for (int k = nrun & 15; k < 16; ++k) lq.push(0);
+        lout[(size_t)(nrun >> 4) * kThreads] = lq.bits();
     }
-    // one union-find entry per border component: a root keyed by its
+    // own parent links become block-wide ids: the thread index joins the label
+    const int nlab_max = __reduce_max_sync(kFull, nlab);
+    for (int L = 0; L < nlab_max; ++L) {
+        if (L < nlab) {
+            const uint16_t e = vpar[L * kThreads + t];
+            if (!(e & kRoot)) vpar[L * kThreads + t] = (uint16_t)((t << 7) | (e & (kLabCap - 1)));
+        }
+    }
+    __syncthreads();
+
+    // -- block merge of the lane tiles along their seams (Kernel 2's boundary
+    // analysis applied inside the block, on the shared lists)
+    const uint32_t m0 = mrow[0];
+    {
+        const bool hasl = tx > 0;
+        const int tl = hasl ? t - 1 : t;
+#pragma unroll
+        for (int r = 0; r < kLH; ++r) {
+            const bool me_fg = hasl && (mrow[r] & 1u);
+            const int me = (t << 7) | sm.lcol[r][t];
+            // a pair repeating the row above's pair (both columns continue
+            // vertically) adds nothing
+            const bool up_me = r > 0 && (mrow[r > 0 ? r - 1 : 0] & 1u);
+            const bool dn_me = r + 1 < kLH && (mrow[r + 1 < kLH ? r + 1 : r] & 1u);
+            const bool up_l = r > 0 && (sm.mask[r > 0 ? r - 1 : 0][tl] >> 31);
+            const bool dn_l = r + 1 < kLH && (sm.mask[r + 1 < kLH ? r + 1 : r][tl] >> 31);
+            const bool at_l = sm.mask[r][tl] >> 31;
+            union_block_sync(sm.par, me_fg && at_l && !(up_me && up_l), me, (tl << 7) | sm.rcol[r][tl], cap, err);
+            if (kConn8) {
+                union_block_sync(sm.par, me_fg && up_l && !up_me, me,
+                                 (tl << 7) | sm.rcol[r > 0 ? r - 1 : 0][tl], cap, err);
+                union_block_sync(sm.par, me_fg && dn_l && !dn_me, me,
+                                 (tl << 7) | sm.rcol[r + 1 < kLH ? r + 1 : r][tl], cap, err);
+            }
+        }
+    }
+    {
+        const bool hasu = ty > 0;
+        const int tu = hasu ? t - kBLX : t;
+        const uint32_t mU = hasu ? sm.mask[kLH - 1][tu] : 0u;
+        const uint32_t SU = mU & ~(mU << 1);
+        const uint8_t *top = &sm.lab[0][0][t];
+        const uint8_t *bot = &sm.lab[lab_buf(kLH - 1)][0][tu];
+        uint32_t S = hasu ? (m0 & ~(m0 << 1)) : 0u;
+        uint32_t E = m0 & ~(m0 >> 1);
+        const int nmax = __reduce_max_sync(kFull, __popc(S));
+        for (int k = 0; k < nmax; ++k) {
+            const bool act = S != 0u;
+            const int a0 = act ? lobit(S) : 0;
+            const int a1 = act ? lobit(E) : 0;
+            S &= S - 1u;
+            E &= E - 1u;
+            const uint32_t P = act ? (mU & touch_range<kConn8>(run_bits(a0, a1))) : 0u;
+            const int me = (t << 7) | top[a0 * kLabPitch];
+            const int u0 = P ? lobit(P) : 0;
+            union_block_sync(sm.par, P != 0u, me, (tu << 7) | bot[hibit((SU & upto(u0)) | 1u) * kLabPitch], cap,
+                             err);
+            uint32_t Q = P ? (SU & P & ~upto(u0)) : 0u;
+            while (__any_sync(kFull, Q != 0u)) {
+                const bool hq = Q != 0u;
+                const int q = hq ? lobit(Q) : 0;
+                Q &= Q - 1u;
+                union_block_sync(sm.par, hq, me, (tu << 7) | bot[q * kLabPitch], cap, err);
+            }
+        }
+        if (kConn8) {
+            // corners: the lane tiles up-left and up-right
+            const bool ul = hasu && tx > 0 && (m0 & 1u);
+            const int tul = ul ? tu - 1 : t;
+            const uint32_t mUL = ul ? sm.mask[kLH - 1][tul] : 0u;
+            const uint32_t SUL = mUL & ~(mUL << 1);
+            union_block_sync(sm.par, ul && (mUL >> 31), (t << 7) | top[0],
+                             (tul << 7) | sm.lab[lab_buf(kLH - 1)][hibit(SUL | 1u)][tul], cap, err);
+            const bool ur = hasu && tx + 1 < kBLX && (m0 >> 31);
+            const int tur = ur ? tu + 1 : t;
+            const uint32_t S0 = m0 & ~(m0 << 1);
+            union_block_sync(sm.par, ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | top[hibit(S0 | 1u) * kLabPitch],
+                             (tur << 7) | sm.lab[lab_buf(kLH - 1)][0][tur], cap, err);
+        }
+    }
+    __syncthreads();
+
+    // -- compress: every own list entry points straight at its root (the
+    // finds only read, so every store here is a final root)
+    for (int L = 0; L < nlab_max; ++L) {
+        if (L < nlab) {
+            const int id = (t << 7) | L;
+            const int root = find_root_ro(vpar, id, cap, err);
+            if (root != id) vpar[L * kThreads + t] = (uint16_t)root;
+        }
+    }
+    __syncthreads();
+
+    // -- roots that own a pixel of the block border
+    auto root_of = [&](int id) -> int {
+        const uint16_t e = vpar[par_index(id)];
+        return (e & kRoot) ? id : (int)e;
+    };
+    auto mark = [&](int id) {
+        const int root = root_of(id);
+        atomicOr(&sm.border[root >> 5], 1u << (root & 31));
+    };
+    if (ty == 0)
+        for (uint32_t S = m0 & ~(m0 << 1); S; S &= S - 1) mark((t << 7) | sm.lab[0][lobit(S)][t]);
+    if (ty == kBLY - 1) {
+        const uint32_t m7 = mrow[kLH - 1];
+        for (uint32_t S = m7 & ~(m7 << 1); S; S &= S - 1)
+            mark((t << 7) | sm.lab[lab_buf(kLH - 1)][lobit(S)][t]);
+    }
+    if (tx == 0) {
+#pragma unroll
+        for (int r = 0; r < kLH; ++r)
+            if (mrow[r] & 1u) mark((t << 7) | sm.lcol[r][t]);
+    }
+    if (tx == kBLX - 1) {
+#pragma unroll
+        for (int r = 0; r < kLH; ++r)
+            if (mrow[r] >> 31) mark((t << 7) | sm.rcol[r][t]);
+    }
+    __syncthreads();
+    {
+        // exclusive popcount prefix over 512 words: 4 per thread, then a scan
+        uint32_t c[4], sum = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { c[k] = __popc(sm.border[4 * t + k]); sum += c[k]; }
+        const int lane = t & 31, w = t >> 5;
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) sm.warp_tot[w] = incl;
+        __syncthreads();
+        uint32_t base = 0;
+        for (int i = 0; i < w; ++i) base += sm.warp_tot[i];
+        uint32_t run = base + incl - sum;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { sm.prefix[4 * t + k] = run; run += c[k]; }
+        // at most kSlots border components exist; more marks only after an
+        // iteration cap was hit, and the surplus slots are dropped
+        if (t == kThreads - 1) {
+            sm.nslots = (int)(base + incl) < kSlots ? (int)(base + incl) : kSlots;
+            if ((int)(base + incl) > kSlots) sm.err |= kErrLocalCap;
+        }
+    }
+    __syncthreads();
+    auto slot_of = [&](int root) -> int {
+        return (int)(sm.prefix[root >> 5] + __popc(sm.border[root >> 5] & ((1u << (root & 31)) - 1u)));
+    };
+
+    // -- one global union-find entry per border component, keyed by its
     // minimum global raster position (ID conversion, Sec. 3.1.4)
     {
-        const int word = threadIdx.x;  // kNodes / 32 == kThreads
-        uint32_t bits = sm.border[word];
-        int slot = (int)sm.prefix[word];
-        const uint32_t base = (uint32_t)t * kSlots;
-        for (; bits; bits &= bits - 1, ++slot) {
-            const int node = word * 32 + __ffs(bits) - 1;
-            s.P[base + slot] = pack_slot(node_key(node, x0, y0, a.W), base + (uint32_t)slot);
+        const uint32_t sbase = (uint32_t)b * kSlots;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int word = 4 * t + k;
+            uint32_t bits = sm.border[word];
+            uint32_t slot = sm.prefix[word];
+            for (; bits && slot < (uint32_t)kSlots; bits &= bits - 1, ++slot) {
+                const int root = word * 32 + lobit(bits);
+                const int key = root_key(root, vpar[par_index(root)]);
+                const uint32_t g = (uint32_t)(y0 + (key >> kBWLog2)) * (uint32_t)a.W +
+                                   (uint32_t)(x0 + (key & (kBW - 1)));
+                s.P[sbase + slot] = pack_slot(g, sbase + slot);
+            }
         }
     }
-    if (threadIdx.x == 0) {
-        s.nslots[t] = sm.nslots;
+    __syncthreads();
+    // -- each own root entry becomes the value its runs carry from now on
+    for (int L = 0; L < nlab_max; ++L) {
+        if (L < nlab) {
+            const int id = (t << 7) | L;
+            const uint16_t e = vpar[L * kThreads + t];
+            if (e & kRoot) {
+                const bool border = (sm.border[id >> 5] >> (id & 31)) & 1u;
+                vpar[L * kThreads + t] = border ? (uint16_t)(kRootBorder | slot_of(id))
+                                                : (uint16_t)(kRoot | root_key(id, e));
+            }
+        }
+    }
+    __syncthreads();
+
+    // -- border record of the block: the slot of every border pixel
+    uint16_t *Eb = s.edges + (size_t)b * kEdge;
+    if (ty == 0 || ty == kBLY - 1) {
+        const int rr = ty == 0 ? 0 : kLH - 1;
+        const uint32_t m = mrow[rr];
+        const uint32_t S = m & ~(m << 1);
+        const uint8_t *lb = &sm.lab[lab_buf(rr)][0][t];
+        uint16_t *dst = Eb + (ty == 0 ? kEdgeTop : kEdgeBottom) + kLW * tx;
+#pragma unroll 4
+        for (int c = 0; c < kLW; ++c) {
+            uint16_t v = kBg;
+            if ((m >> c) & 1u) v = border_slot(run_value(vpar, (t << 7) | lb[hibit(S & upto(c)) * kLabPitch]));
+            dst[c] = v;
+        }
+    }
+    if (tx == 0 || tx == kBLX - 1) {
+        uint16_t *dst = Eb + (tx == 0 ? kEdgeLeft : kEdgeRight) + kLH * ty;
+#pragma unroll
+        for (int r = 0; r < kLH; ++r) {
+            const bool fg = tx == 0 ? (mrow[r] & 1u) : (mrow[r] >> 31);
+            const int L = tx == 0 ? sm.lcol[r][t] : sm.rcol[r][t];
+            dst[r] = fg ? border_slot(run_value(vpar, (t << 7) | L)) : kBg;
+        }
+    }
+    // -- per-run values: block key of the root, or kBorderFlag | slot
+    {
+        const uint4 *lin = s.lstream + (size_t)b * kLChunks * kThreads + t;
+        uint4 *vout = s.vstream + (size_t)b * kVChunks * kThreads + t;
+        HalfQueue vq;
+        const int nrun_max = __reduce_max_sync(kFull, nrun);
+        for (int k = 0; k < nrun_max; k += 16) {
+            uint4 c = make_uint4(0, 0, 0, 0);
+            if (k < nrun) c = lin[(size_t)(k >> 4) * kThreads];
+            const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (k + j < nrun) {
+                    const int L = (w4[j >> 2] >> (8 * (j & 3))) & 0xFF;
+                    vq.push(run_value(vpar, (t << 7) | L));
+                    if (((k + j + 1) & 7) == 0) vout[(size_t)((k + j) >> 3) * kThreads] = vq.bits();
+                }
+            }
+        }
+        if (nrun & 7) {
+            for (int k = nrun & 7; k < 8; ++k) vq.push(0);
+            vout[(size_t)(nrun >> 3) * kThreads] = vq.bits();
+        }
+    }
+    // -- row masks for the write-out pass
+    {
+        uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * kThreads + t) * kLH);
+        mo[0] = make_uint4(mrow[0], mrow[1], mrow[2], mrow[3]);
+        mo[1] = make_uint4(mrow[4], mrow[5], mrow[6], mrow[7]);
+    }
+    if (err) atomicOr(&sm.err, err);
+    __syncthreads();
+    if (t == 0) {
+        s.nslots[b] = sm.nslots;
         report(sm.err);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Each tile examines the pixel pairs across its top edge, its left edge and
+// Each block examines the pixel pairs across its top edge, its left edge and
 // (8-connectivity) its two upper corners; the right, bottom and lower corners
-// belong to the neighbouring tiles.  Thread j takes top-edge column j and,
-// for j < kTileH, left-edge row j.  A pair that repeats the pair of the
-// neighbouring thread is skipped.
+// belong to the neighbouring blocks.  A pair that repeats the pair of the
+// neighbouring pixel is skipped.
 template <bool kConn8>
-__global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int ntx, int nty, int cap) {
-    const int t = blockIdx.x;
-    const int tx = t % ntx, ty = t / ntx;
-    const int j = threadIdx.x;
-    const uint16_t *E = s.edges + (size_t)t * kEdge;
-    const uint32_t base = (uint32_t)t * kSlots;
+__global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int nbx, int nby, int cap) {
+    const int b = blockIdx.x;
+    const int bx = b % nbx, by = b / nbx;
+    const uint16_t *E = s.edges + (size_t)b * kEdge;
+    const uint32_t base = (uint32_t)b * kSlots;
+    const uint32_t bound = (uint32_t)nbx * (uint32_t)nby * kSlots;
     int err = 0;
+    // every slot named by a border record is below its block's slot count;
+    // checking it keeps the finds inside initialised entries whatever happened
+    const auto valid = [&](int blk, uint16_t v) { return v != kBg && (int)v < s.nslots[blk]; };
 
-    if (ty > 0) {
-        const int tu = t - ntx;
-        const uint16_t *Eu = s.edges + (size_t)tu * kEdge;
-        const uint32_t ubase = (uint32_t)tu * kSlots;
-        const uint16_t a = E[kEdgeTop + j];
-        if (a != kBg) {
+    if (by > 0) {
+        const int bu = b - nbx;
+        const uint16_t *Eu = s.edges + (size_t)bu * kEdge;
+        const uint32_t ubase = (uint32_t)bu * kSlots;
+        for (int j = threadIdx.x; j < kBW; j += kThreads) {
+            const uint16_t a = E[kEdgeTop + j];
+            if (!valid(b, a)) continue;
             const uint16_t aL = j > 0 ? E[kEdgeTop + j - 1] : kBg;
-            const uint16_t aR = j + 1 < kTileW ? E[kEdgeTop + j + 1] : kBg;
-            const uint16_t b = Eu[kEdgeBottom + j];
-            const uint16_t bL = j > 0 ? Eu[kEdgeBottom + j - 1] : kBg;
-            if (b != kBg && !(aL == a && bL == b)) union_global(s.P, base + a, ubase + b, cap, err);
+            const uint16_t aR = j + 1 < kBW ? E[kEdgeTop + j + 1] : kBg;
+            const uint16_t c = Eu[kEdgeBottom + j];
+            const uint16_t cL = j > 0 ? Eu[kEdgeBottom + j - 1] : kBg;
+            if (valid(bu, c) && !(aL == a && cL == c)) union_global(s.P, base + a, ubase + c, cap, err, bound);
             if (kConn8) {
-                // up-left: same pair as the left neighbour's vertical pair when aL == a
                 if (j > 0) {
-                    if (bL != kBg && aL != a) union_global(s.P, base + a, ubase + bL, cap, err);
-                } else if (tx > 0) {
-                    const uint16_t c = s.edges[(size_t)(tu - 1) * kEdge + kEdgeBottom + kTileW - 1];
-                    if (c != kBg) union_global(s.P, base + a, (uint32_t)(tu - 1) * kSlots + c, cap, err);
+                    if (valid(bu, cL) && aL != a) union_global(s.P, base + a, ubase + cL, cap, err, bound);
+                } else if (bx > 0) {
+                    const uint16_t d = s.edges[(size_t)(bu - 1) * kEdge + kEdgeBottom + kBW - 1];
+                    if (valid(bu - 1, d)) union_global(s.P, base + a, (uint32_t)(bu - 1) * kSlots + d, cap, err, bound);
                 }
-                // up-right: same pair as the right neighbour's vertical pair when aR == a
-                if (j + 1 < kTileW) {
-                    const uint16_t bR = Eu[kEdgeBottom + j + 1];
-                    if (bR != kBg && aR != a) union_global(s.P, base + a, ubase + bR, cap, err);
-                } else if (tx + 1 < ntx) {
-                    const uint16_t c = s.edges[(size_t)(tu + 1) * kEdge + kEdgeBottom + 0];
-                    if (c != kBg) union_global(s.P, base + a, (uint32_t)(tu + 1) * kSlots + c, cap, err);
+                if (j + 1 < kBW) {
+                    const uint16_t cR = Eu[kEdgeBottom + j + 1];
+                    if (valid(bu, cR) && aR != a) union_global(s.P, base + a, ubase + cR, cap, err, bound);
+                } else if (bx + 1 < nbx) {
+                    const uint16_t d = s.edges[(size_t)(bu + 1) * kEdge + kEdgeBottom + 0];
+                    if (valid(bu + 1, d)) union_global(s.P, base + a, (uint32_t)(bu + 1) * kSlots + d, cap, err, bound);
                 }
             }
         }
     }
-    if (tx > 0 && j < kTileH) {
-        const int tl = t - 1;
-        const uint16_t *El = s.edges + (size_t)tl * kEdge;
-        const uint32_t lbase = (uint32_t)tl * kSlots;
-        const uint16_t a = E[kEdgeLeft + j];
-        if (a != kBg) {
+    if (bx > 0) {
+        const int bl = b - 1;
+        const uint16_t *El = s.edges + (size_t)bl * kEdge;
+        const uint32_t lbase = (uint32_t)bl * kSlots;
+        for (int j = threadIdx.x; j < kBH; j += kThreads) {
+            const uint16_t a = E[kEdgeLeft + j];
+            if (!valid(b, a)) continue;
             const uint16_t aU = j > 0 ? E[kEdgeLeft + j - 1] : kBg;
-            const uint16_t aD = j + 1 < kTileH ? E[kEdgeLeft + j + 1] : kBg;
-            const uint16_t b = El[kEdgeRight + j];
-            const uint16_t bU = j > 0 ? El[kEdgeRight + j - 1] : kBg;
-            if (b != kBg && !(aU == a && bU == b)) union_global(s.P, base + a, lbase + b, cap, err);
+            const uint16_t aD = j + 1 < kBH ? E[kEdgeLeft + j + 1] : kBg;
+            const uint16_t c = El[kEdgeRight + j];
+            const uint16_t cU = j > 0 ? El[kEdgeRight + j - 1] : kBg;
+            if (valid(bl, c) && !(aU == a && cU == c)) union_global(s.P, base + a, lbase + c, cap, err, bound);
             if (kConn8) {
-                if (j > 0 && bU != kBg && aU != a) union_global(s.P, base + a, lbase + bU, cap, err);
-                if (j + 1 < kTileH) {
-                    const uint16_t bD = El[kEdgeRight + j + 1];
-                    if (bD != kBg && aD != a) union_global(s.P, base + a, lbase + bD, cap, err);
+                if (j > 0 && valid(bl, cU) && aU != a) union_global(s.P, base + a, lbase + cU, cap, err, bound);
+                if (j + 1 < kBH) {
+                    const uint16_t cD = El[kEdgeRight + j + 1];
+                    if (valid(bl, cD) && aD != a) union_global(s.P, base + a, lbase + cD, cap, err, bound);
                 }
             }
         }
@@ -181,94 +573,101 @@ __global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int ntx, in
 }
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_flatten(Scratch s, int cap) {
-    const int t = blockIdx.x;
-    const int n = s.nslots[t];
+__global__ void __launch_bounds__(kThreads) k_flatten(Scratch s, int cap, uint32_t bound) {
+    const int b = blockIdx.x;
+    const int n = s.nslots[b];
     int err = 0;
     for (int k = threadIdx.x; k < n; k += kThreads) {
-        const uint32_t slot = (uint32_t)t * kSlots + (uint32_t)k;
+        const uint32_t slot = (uint32_t)b * kSlots + (uint32_t)k;
         uint32_t key;
-        const uint32_t root = find_global(s.P, slot, key, cap, err);
+        const uint32_t root = find_global_ro(s.P, slot, key, cap, err, bound);
         if (root != slot && !err) ((volatile uint64_t *)s.P)[slot] = pack_slot(key, root);
     }
     report(err);
 }
 
 // ---------------------------------------------------------------------------
-struct RelabelSmem {
-    TileSmem tile;
+struct WriteSmem {
     int slot_label[kSlots];
-    int4 stage[kTileH * kTileW / 4];   // output tile, 16-byte chunks swizzled by row
+    int stage[kBLY][kBW];   // one row of every lane tile row; 16-byte chunks swizzled
 };
 
-__device__ __forceinline__ int stage_chunk(int row, int q) { return row * (kTileW / 4) + (q ^ (row & 7)); }
+// Chunk q of a staging row holds columns 4q..4q+3; lane tile tx owns chunks
+// 8tx..8tx+7, stored at q ^ (tx & 7) so that lanes writing the same column of
+// different lane tiles hit different banks.
+__device__ __forceinline__ int stage_index(int col) {
+    const int q = col >> 2;
+    return ((q ^ ((q >> 3) & 7)) << 2) | (col & 3);
+}
 
-template <bool kConn8>
-__global__ void __launch_bounds__(kThreads) k_relabel(ImageArgs a, Scratch s, int cap) {
-    __shared__ RelabelSmem smr;
-    TileSmem &sm = smr.tile;
-    const int t = blockIdx.x;
-    const int tx = t % a.ntx, ty = t / a.ntx;
-    const int x0 = tx * kTileW, y0 = ty * kTileH;
-    clear_tile_state(sm);
+__global__ void __launch_bounds__(kThreads, 4) k_block_write(ImageArgs a, Scratch s) {
+    __shared__ WriteSmem sm;
+    const int b = blockIdx.x;
+    const int bx = b % a.nbx, by = b / a.nbx;
+    const int x0 = bx * kBW, y0 = by * kBH;
+    const int t = threadIdx.x;
+    const int tx = t & (kBLX - 1), ty = t >> 4;
 
-    uint32_t m, S;
-    label_tile<kConn8>(sm, a.img, a.H, a.W, a.pitch, a.vec_ok, x0, y0, cap, m, S);
-    number_border_roots(sm);
+    const int ns = s.nslots[b];
+    for (int k = t; k < ns; k += kThreads)
+        sm.slot_label[k] = (int)(uint32_t)(s.P[(size_t)b * kSlots + k] >> 32) + 1;
 
-    // final label of each border component
-    for (int k = threadIdx.x; k < sm.nslots; k += kThreads) {
-        const uint64_t v = s.P[(size_t)t * kSlots + k];
-        smr.slot_label[k] = (int)(uint32_t)(v >> 32) + 1;
-    }
+    const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * kThreads + t) * kLH);
+    const uint4 mA = mi[0], mB = mi[1];
+    const uint32_t mrow[kLH] = {mA.x, mA.y, mA.z, mA.w, mB.x, mB.y, mB.z, mB.w};
+    const uint4 *vin = s.vstream + (size_t)b * kVChunks * kThreads + t;
+    uint4 vq = make_uint4(0, 0, 0, 0);
+    int vi = 8, vc = 0;
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int r = lane;
-    const int rowbase = r * kTileW + kSubW * w;
-    // every run start: root -> final label (in place; each lane touches only
-    // the entries of its own row)
-    for (uint32_t u = S; u; u &= u - 1) {
-        const int n = rowbase + __ffs(u) - 1;
-        const int root = sm.parent[swz(n)];
-        const int lab = is_border_root(sm, root) ? smr.slot_label[border_slot(sm, root)]
-                                                  : (int)node_key(root, x0, y0, a.W) + 1;
-        sm.parent[swz(n)] = lab;
-    }
-    // expand run labels over the row into the staging tile
-    {
-        int cur = 0;
+    int *row = sm.stage[ty];
 #pragma unroll
-        for (int k = 0; k < kSubW / 4; ++k) {
-            int v[4];
+    for (int r = 0; r < kLH; ++r) {
+        const uint32_t m = mrow[r];
+        // background over this lane tile's row, then the runs
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int c = 4 * k + j;
-                if ((S >> c) & 1u) cur = sm.parent[swz(rowbase + c)];
-                v[j] = ((m >> c) & 1u) ? cur : 0;
+        for (int k = 0; k < kLW / 4; ++k)
+            reinterpret_cast<int4 *>(row)[stage_index(kLW * tx + 4 * k) >> 2] = make_int4(0, 0, 0, 0);
+        uint32_t S = m & ~(m << 1);
+        uint32_t E = m & ~(m >> 1);
+        while (S) {
+            const int a0 = lobit(S), a1 = lobit(E);
+            S &= S - 1;
+            E &= E - 1;
+            if (vi == 8) {
+                vq = vin[(size_t)(vc++) * kThreads];
+                vi = 0;
             }
-            smr.stage[stage_chunk(r, (kSubW / 4) * w + k)] = make_int4(v[0], v[1], v[2], v[3]);
+            const uint32_t w = vi < 2 ? vq.x : vi < 4 ? vq.y : vi < 6 ? vq.z : vq.w;
+            const uint32_t v = (w >> ((vi & 1) * 16)) & 0xFFFFu;
+            ++vi;
+            const uint32_t slot = v & 0x7FFFu;
+            const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
+                                               : (int)((uint32_t)(y0 + (int)(v >> kBWLog2)) * (uint32_t)a.W +
+                                                       (uint32_t)(x0 + (int)(v & (kBW - 1)))) + 1;
+            for (int c = a0; c <= a1; ++c) row[stage_index(kLW * tx + c)] = lab;
         }
-    }
-    __syncthreads();
-
-    // coalesced write-out: a warp stores one 512-byte tile row per step
-    for (int row = w; row < kTileH; row += kWarps) {
-        const int y = y0 + row;
-        if (y >= a.H) break;
-        const int4 v = smr.stage[stage_chunk(row, lane)];
-        const int x = x0 + 4 * lane;
-        int32_t *dst = a.labels + (size_t)y * a.W + x;
-        if (a.out_vec_ok && x + 4 <= a.W) {
-            __stcs(reinterpret_cast<int4 *>(dst), v);
-        } else {
-            if (x + 0 < a.W) __stcs(dst + 0, v.x);
-            if (x + 1 < a.W) __stcs(dst + 1, v.y);
-            if (x + 2 < a.W) __stcs(dst + 2, v.z);
-            if (x + 3 < a.W) __stcs(dst + 3, v.w);
+        __syncthreads();
+        // coalesced write-out: image rows y0 + 8*ry + r, 128 chunks of 4 pixels
+#pragma unroll
+        for (int ry = 0; ry < kBLY; ++ry) {
+            const int y = y0 + kLH * ry + r;
+            const int x = x0 + 4 * t;
+            if (y < a.H && x < a.W) {
+                const int4 v = reinterpret_cast<const int4 *>(sm.stage[ry])[stage_index(4 * t) >> 2];
+                int32_t *dst = a.labels + (size_t)y * a.W + x;
+                if (a.out_vec_ok && x + 4 <= a.W) {
+                    __stcs(reinterpret_cast<int4 *>(dst), v);
+                } else {
+                    __stcs(dst, v.x);
+                    if (x + 1 < a.W) __stcs(dst + 1, v.y);
+                    if (x + 2 < a.W) __stcs(dst + 2, v.z);
+                    if (x + 3 < a.W) __stcs(dst + 3, v.w);
+                }
+            }
         }
+        __syncthreads();
     }
-    if (threadIdx.x == 0) report(sm.err);
 }
 
 }  // namespace ccl
@@ -278,27 +677,45 @@ __global__ void __launch_bounds__(kThreads) k_relabel(ImageArgs a, Scratch s, in
 
 namespace ccl {
 
-size_t workspace_bytes(int H, int W) {
-    const size_t ntx = ((size_t)W + kTileW - 1) / kTileW;
-    const size_t nty = ((size_t)H + kTileH - 1) / kTileH;
-    const size_t nt = ntx * nty;
-    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
-    return up(nt * kEdge * sizeof(uint16_t)) + up(nt * kSlots * sizeof(uint64_t)) +
-           up(nt * sizeof(int32_t));
+namespace {
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t masks, lstream, vstream, edges, P, nslots, total;
+};
+
+Layout layout_for(size_t nb) {
+    Layout l;
+    size_t off = 0;
+    l.masks = off;   off += up256(nb * kThreads * kLH * sizeof(uint32_t));
+    l.lstream = off; off += up256(nb * kLChunks * kThreads * sizeof(uint4));
+    l.vstream = off; off += up256(nb * kVChunks * kThreads * sizeof(uint4));
+    l.edges = off;   off += up256(nb * kEdge * sizeof(uint16_t));
+    l.P = off;       off += up256(nb * kSlots * sizeof(uint64_t));
+    l.nslots = off;  off += up256(nb * sizeof(int32_t));
+    l.total = off;
+    return l;
 }
 
+size_t blocks_for(int H, int W) {
+    return (((size_t)W + kBW - 1) / kBW) * (((size_t)H + kBH - 1) / kBH);
+}
+
+}  // namespace
+
+size_t workspace_bytes(int H, int W) { return layout_for(blocks_for(H, W)).total; }
+
 static Scratch carve(void *ws, int H, int W) {
-    const size_t ntx = ((size_t)W + kTileW - 1) / kTileW;
-    const size_t nty = ((size_t)H + kTileH - 1) / kTileH;
-    const size_t nt = ntx * nty;
-    auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    const Layout l = layout_for(blocks_for(H, W));
     char *p = static_cast<char *>(ws);
     Scratch s;
-    s.edges = reinterpret_cast<uint16_t *>(p);
-    p += up(nt * kEdge * sizeof(uint16_t));
-    s.P = reinterpret_cast<uint64_t *>(p);
-    p += up(nt * kSlots * sizeof(uint64_t));
-    s.nslots = reinterpret_cast<int32_t *>(p);
+    s.masks = reinterpret_cast<uint32_t *>(p + l.masks);
+    s.lstream = reinterpret_cast<uint4 *>(p + l.lstream);
+    s.vstream = reinterpret_cast<uint4 *>(p + l.vstream);
+    s.edges = reinterpret_cast<uint16_t *>(p + l.edges);
+    s.P = reinterpret_cast<uint64_t *>(p + l.P);
+    s.nslots = reinterpret_cast<int32_t *>(p + l.nslots);
     return s;
 }
 
@@ -394,8 +811,27 @@ int timing_read(double *ms, long long *count, int n) {
 }
 
 const char *kernel_kind_name(int k) {
-    static const char *names[kKernelKinds] = {"k_local_border", "k_block_merge", "k_flatten", "k_relabel"};
+    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_flatten", "k_block_write"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
+}
+
+// The block-local kernel needs more than the 48 KB of shared memory a launch
+// gets without opting in; the opt-in is per device.
+bool kernel_attributes_set() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return true;
+    const int bytes = (int)sizeof(LocalSmem);
+    if (cudaFuncSetAttribute(k_block_local<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_block_local<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+            cudaSuccess)
+        return false;
+    done[dev] = true;
+    return true;
 }
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
@@ -406,37 +842,34 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
     a.pitch = pitch;
     a.H = H;
     a.W = W;
-    a.ntx = (W + kTileW - 1) / kTileW;
-    a.nty = (H + kTileH - 1) / kTileH;
+    a.nbx = (W + kBW - 1) / kBW;
+    a.nby = (H + kBH - 1) / kBH;
     a.vec_ok = ((reinterpret_cast<uintptr_t>(img) | pitch) & 15) == 0;
     a.out_vec_ok = (reinterpret_cast<uintptr_t>(labels) & 15) == 0 && (W & 3) == 0;
     const Scratch s = carve(ws, H, W);
-    const unsigned nt = (unsigned)a.ntx * (unsigned)a.nty;
+    const unsigned nb = (unsigned)a.nbx * (unsigned)a.nby;
     // Default caps: a find walks a strictly decreasing chain, so it cannot
-    // take more steps than there are nodes (slots); no valid input reaches them.
-    const long long slots = (long long)nt * kSlots + 16;
-    const int local_cap = cap > 0 ? cap : 2 * kNodes;
+    // take more steps than there are list entries (slots); no valid input
+    // reaches them.
+    const long long slots = (long long)nb * kSlots + 16;
+    const int local_cap = cap > 0 ? cap : kLabCap * kThreads + 16;
     const int global_cap = cap > 0 ? cap : (int)(slots < (1LL << 30) ? slots : (1LL << 30));
+    if (!kernel_attributes_set()) return -1;
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_local_border<true><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        k_block_local<true><<<nb, kThreads, sizeof(LocalSmem), stream>>>(a, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<true><<<nt, kThreads, 0, stream>>>(s, a.ntx, a.nty, global_cap);
-        ev = timing_mark(stream, ev, kKindMerge);
-        k_flatten<<<nt, kThreads, 0, stream>>>(s, global_cap);
-        ev = timing_mark(stream, ev, kKindFlatten);
-        k_relabel<true><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
-        ev = timing_mark(stream, ev, kKindRelabel);
+        k_block_merge<true><<<nb, kThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
     } else {
-        k_local_border<false><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
+        k_block_local<false><<<nb, kThreads, sizeof(LocalSmem), stream>>>(a, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<false><<<nt, kThreads, 0, stream>>>(s, a.ntx, a.nty, global_cap);
-        ev = timing_mark(stream, ev, kKindMerge);
-        k_flatten<<<nt, kThreads, 0, stream>>>(s, global_cap);
-        ev = timing_mark(stream, ev, kKindFlatten);
-        k_relabel<false><<<nt, kThreads, 0, stream>>>(a, s, local_cap);
-        ev = timing_mark(stream, ev, kKindRelabel);
+        k_block_merge<false><<<nb, kThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
     }
+    ev = timing_mark(stream, ev, kKindMerge);
+    k_flatten<<<nb, kThreads, 0, stream>>>(s, global_cap, nb * (uint32_t)kSlots);
+    ev = timing_mark(stream, ev, kKindFlatten);
+    k_block_write<<<nb, kThreads, 0, stream>>>(a, s);
+    ev = timing_mark(stream, ev, kKindRelabel);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

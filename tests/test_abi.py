@@ -55,10 +55,11 @@ def test_status_strings(lib):
 
 def test_workspace_size_host_logic(lib):
     assert ccl.ccl_workspace_size(0, 10) == 0
-    a = ccl.ccl_workspace_size(32, 128)
-    b = ccl.ccl_workspace_size(33, 129)  # four tiles instead of one
-    assert a > 0 and b > a
-    assert ccl.ccl_workspace_size(8192, 8192) < 64 * 1024 * 1024
+    a = ccl.ccl_workspace_size(64, 512)
+    b = ccl.ccl_workspace_size(65, 513)  # four 512x64 blocks instead of one
+    assert a > 0 and b > 3 * a
+    # scratch stays below 2 bytes of address space per pixel
+    assert ccl.ccl_workspace_size(8192, 8192) < 2 * 8192 * 8192
     with pytest.raises(ccl.CclError):
         ccl.ccl_workspace_size(-1, 5)
     with pytest.raises(ccl.CclError) as e:

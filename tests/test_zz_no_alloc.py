@@ -20,7 +20,7 @@ def test_noalloc_declared_and_exported_without_gpu():
     ccl_build.build()
     lib = ccl.load()
     assert hasattr(lib, "ccl_label_noalloc")
-    assert ccl.ccl_noalloc_max_workspace_bytes() == 16 << 20
+    assert ccl.ccl_noalloc_max_workspace_bytes() == 64 << 20
     # arguments are checked before any device work
     assert lib.ccl_label_noalloc(0x1000, 4, 4, 4, 6, 0x900000, None) == ccl.CCL_ERR_INVALID_ARG
     # too large for the fixed scratch: rejected, nothing enqueued
@@ -35,7 +35,7 @@ def test_noalloc_matches_ccl_label_on_two_calls_in_a_row():
     ccl_build.build()
     cases = [(synth.bernoulli(1000, 1537, 0.5, 11), 8),
              (synth.smoothed(4096, 4096, 8.0, 0.5, 12), 4)]
-    # the larger image fills most of the 16 MiB scratch
+    # the larger image fills about half of the 64 MiB scratch
     assert ccl.ccl_workspace_size(4096, 4096) <= ccl.ccl_noalloc_max_workspace_bytes()
     imgs = [torch.from_numpy(img).cuda() for img, _ in cases]
     outs = [torch.full(img.shape, -7, dtype=torch.int32, device="cuda") for img in imgs]
