@@ -47,7 +47,7 @@ constexpr uint16_t kBg = 0xFFFF;
 constexpr uint16_t kBorderFlag = 0x8000;  // per-run value: border slot, else block key
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr int kLabPitch = 132;          // bytes per column row of the label buffers
-constexpr int kLChunks = kRunCap / 16;  // 16 one-byte labels per 16-byte chunk
+constexpr int kLWords = kRunCap / 4;    // 4 one-byte labels per 32-bit word
 constexpr int kVChunks = kRunCap / 8;   // 8 two-byte values per 16-byte chunk
 
 constexpr int kErrLocalCap = 1;
@@ -93,7 +93,10 @@ __device__ __forceinline__ uint32_t touch_range(uint32_t rm) {
 // ---------------------------------------------------------------------------
 // Shared-memory label-equivalence lists of one block.
 
-__device__ __forceinline__ int par_index(int id) { return (id & (kLabCap - 1)) * kThreads + (id >> 7); }
+// (masked on both fields, so no entry value can address outside the table)
+__device__ __forceinline__ int par_index(int id) {
+    return (id & (kLabCap - 1)) * kThreads + ((id >> 7) & (kThreads - 1));
+}
 
 // Block raster key (row * 512 + column) of a root, from its id and entry.
 __device__ __forceinline__ int root_key(int id, uint16_t entry) {

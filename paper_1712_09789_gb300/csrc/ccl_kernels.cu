@@ -49,7 +49,7 @@ struct ImageArgs {
 // touched).
 struct Scratch {
     uint32_t *masks;   // [blocks][128 lane tiles][8 rows]
-    uint4 *lstream;    // [blocks][kLChunks][128]: run labels, 16 per chunk
+    uint32_t *lstream; // [blocks][kLWords][128]: run labels, 4 per word
     uint4 *vstream;    // [blocks][kVChunks][128]: run values, 8 per chunk
     uint16_t *edges;   // [blocks][kEdge]
     uint64_t *P;       // [blocks][kSlots]
@@ -67,8 +67,13 @@ struct LocalSmem {
     uint8_t lcol[kLH][kLabPitch];                // label of the run holding column 0, per row
     uint8_t rcol[kLH][kLabPitch];                // label of the run holding column 31, per row
     uint32_t mask[kLH][kThreads];                // row masks
-    uint32_t border[kLabCap * kThreads / 32];    // bit per id: root touching the block border
-    uint32_t prefix[kLabCap * kThreads / 32];
+    union {
+        uint16_t qpair[16][kThreads];            // further contacts of the current row (scan)
+        struct {
+            uint32_t border[kLabCap * kThreads / 32];  // bit per id: root touching the block border
+            uint32_t prefix[kLabCap * kThreads / 32];
+        };
+    };
     uint32_t warp_tot[kThreads / 32];
     int nslots;
     int err;
@@ -81,18 +86,6 @@ __device__ __forceinline__ int lab_buf(int r) { return r == 0 ? 0 : 1 + ((r - 1)
 __device__ __forceinline__ uint16_t border_slot(uint16_t v) {
     return (v & kBorderFlag) ? (uint16_t)(v & 0x3FFF) : kBg;
 }
-
-// 16 one-byte labels collected low byte first in a 128-bit shift register.
-struct ByteQueue {
-    uint64_t lo = 0, hi = 0;
-    __device__ __forceinline__ void push(uint32_t b) {
-        lo = (lo >> 8) | (hi << 56);
-        hi = (hi >> 8) | ((uint64_t)b << 56);
-    }
-    __device__ __forceinline__ uint4 bits() const {
-        return make_uint4((uint32_t)lo, (uint32_t)(lo >> 32), (uint32_t)hi, (uint32_t)(hi >> 32));
-    }
-};
 
 // 8 two-byte values collected low half first in a 128-bit shift register.
 struct HalfQueue {
@@ -118,7 +111,6 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
     const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
     int err = 0;
 
-    for (int i = t; i < kLabCap * kThreads / 32; i += kThreads) sm.border[i] = 0u;
     if (t == 0) sm.err = 0;
 
     // -- initialization: the lane tile's 8 rows as masks (all loads in flight
@@ -153,11 +145,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
     // -- coarse labelling and refinement, row by row.  Every loop below runs
     // the same number of rounds on all 32 lanes of a warp (the maximum any
     // lane needs), so the 32 lane tiles advance in lockstep.
+    //
+    // Coarse labelling: a run with foreground above takes the label value of
+    // the first run above it (row connection by bit operations, column
+    // connection to that run); labels therefore travel down unchanged and
+    // no list is walked here.  A run without foreground above opens a new
+    // list.  Refinement: every further run above that a run touches is
+    // queued and the queued pairs of the row are merged after the row, the
+    // larger root hung under the smaller.
     volatile uint16_t *vpar = sm.par;
     uint32_t prevM = 0, prevS = 0;
     int nlab = 0, nrun = 0;
-    ByteQueue lq;
-    uint4 *lout = s.lstream + (size_t)b * kLChunks * kThreads + t;
+    uint32_t lacc = 0;                              // 4 run labels, first in the low byte
+    uint32_t *lout = s.lstream + (size_t)b * kLWords * kThreads + t;
 #pragma unroll 1
     for (int r = 0; r < kLH; ++r) {
         const uint32_t m = sm.mask[r][t];
@@ -165,106 +165,107 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
         uint32_t E = m & ~(m >> 1);                 // run ends
         uint8_t *cur = &sm.lab[lab_buf(r)][0][t];
         const uint8_t *prev = &sm.lab[lab_buf(r > 0 ? r - 1 : 0)][0][t];
-        uint8_t lc = 0xFF, rc = 0xFF;
+        int nq = 0;
         const int nmax = __reduce_max_sync(kFull, __popc(S));
         for (int k = 0; k < nmax; ++k) {
             const bool act = S != 0u;
-            const int a0 = act ? lobit(S) : 0;
-            const int a1 = act ? lobit(E) : 0;
+            // an exhausted lane sees a dummy run at bit 31 and stores nothing
+            const int a0 = lobit(S | 0x80000000u);
+            const int a1 = lobit(E | 0x80000000u);
             S &= S - 1u;
             E &= E - 1u;
-            const uint32_t P = act ? (prevM & touch_range<kConn8>(run_bits(a0, a1))) : 0u;
-            const bool linked = P != 0u;
-            const int u0 = linked ? lobit(P) : 0;
-            // column connection: the first run above that the run touches
-            int L = 0;
-            if (linked) L = prev[hibit(prevS & upto(u0)) * kLabPitch];
-            // unification: walk to the list's root (own lists only), halving
-            bool pend = linked;
-            for (int i = 0; __any_sync(kFull, pend); ++i) {
-                if (pend) {
-                    const uint16_t e = vpar[L * kThreads + t];
-                    if (e & kRoot) {
-                        pend = false;
-                    } else {
-                        const int p = e & (kLabCap - 1);
-                        const uint16_t g = vpar[p * kThreads + t];
-                        if (g & kRoot) {
-                            L = p;
-                            pend = false;
-                        } else {
-                            vpar[L * kThreads + t] = g;
-                            L = g & (kLabCap - 1);
-                        }
-                    }
-                }
-                if (i >= cap) {
-                    if (pend) err |= kErrLocalCap;
-                    break;
-                }
+            const uint32_t P = prevM & touch_range<kConn8>(run_bits(a0, a1)) & (0u - (uint32_t)act);
+            const int u0 = P ? lobit(P) : 0;
+            int L = nlab;
+            if (P) L = prev[hibit(prevS & upto(u0)) * kLabPitch];
+            else if (act) {
+                vpar[nlab * kThreads + t] = (uint16_t)(kRoot | (r * kLW + a0));
+                ++nlab;
             }
-            // no foreground above: a new list whose root is this run
-            if (act && !linked) {
-                L = nlab++;
-                vpar[L * kThreads + t] = (uint16_t)(kRoot | (r * kLW + a0));
-            }
-            // refinement: every further run above joins the same list; the
-            // larger label is hung under the smaller
-            uint32_t Q = linked ? (prevS & P & ~upto(u0)) : 0u;
-            for (int i = 0; __any_sync(kFull, Q != 0u); ++i) {
-                const bool hq = Q != 0u;
-                int L2 = 0;
-                if (hq) {
-                    L2 = prev[lobit(Q) * kLabPitch];
+            uint32_t Q = P ? (prevS & P & ~upto(u0)) : 0u;
+            while (__any_sync(kFull, Q != 0u)) {
+                if (Q) {
+                    sm.qpair[nq][t] = (uint16_t)(L | (prev[lobit(Q) * kLabPitch] << 8));
+                    ++nq;
                     Q &= Q - 1u;
                 }
-                bool pend2 = hq;
-                for (int j = 0; __any_sync(kFull, pend2); ++j) {
-                    if (pend2) {
-                        const uint16_t e = vpar[L2 * kThreads + t];
-                        if (e & kRoot) pend2 = false;
-                        else L2 = e & (kLabCap - 1);
-                    }
-                    if (j >= cap) {
-                        if (pend2) err |= kErrLocalCap;
-                        break;
-                    }
-                }
-                if (hq && L2 != L) {
-                    const int lo = L2 < L ? L2 : L, hi = L2 < L ? L : L2;
-                    vpar[hi * kThreads + t] = (uint16_t)lo;
-                    L = lo;
-                }
-                if (i >= cap) break;
             }
             if (act) {
                 cur[a0 * kLabPitch] = (uint8_t)L;
-                if (a0 == 0) lc = (uint8_t)L;
-                if (a1 == kLW - 1) rc = (uint8_t)L;
-                lq.push((uint32_t)L);
+                lacc = (lacc >> 8) | ((uint32_t)L << 24);
                 ++nrun;
-                if ((nrun & 15) == 0) lout[(size_t)((nrun >> 4) - 1) * kThreads] = lq.bits();
+                if ((nrun & 3) == 0) lout[(size_t)((nrun >> 2) - 1) * kThreads] = lacc;
             }
         }
-        sm.lcol[r][t] = lc;
-        sm.rcol[r][t] = rc;
+        sm.lcol[r][t] = (m & 1u) ? cur[0] : (uint8_t)0xFF;
+        sm.rcol[r][t] = (m >> 31) ? cur[hibit(m & ~(m << 1)) * kLabPitch] : (uint8_t)0xFF;
         prevM = m;
         prevS = m & ~(m << 1);
+        // refinement of the row: merge the queued pairs (own lists only)
+        const int nqmax = __reduce_max_sync(kFull, nq);
+        for (int j = 0; j < nqmax; ++j) {
+            const bool hq = j < nq;
+            const uint16_t pr = hq ? sm.qpair[j][t] : (uint16_t)0;
+            int A = pr & 0xFF, B = pr >> 8;
+            bool pa = hq, pb = hq;
+            for (int i = 0; __any_sync(kFull, pa || pb); ++i) {
+                // root-finds with path halving (own lists, no other writer)
+                if (pa) {
+                    const uint16_t e = vpar[A * kThreads + t];
+                    if (e & kRoot) {
+                        pa = false;
+                    } else {
+                        const int p = e & (kLabCap - 1);
+                        const uint16_t g = vpar[p * kThreads + t];
+                        if (g & kRoot) { A = p; pa = false; }
+                        else { vpar[A * kThreads + t] = g; A = g & (kLabCap - 1); }
+                    }
+                }
+                if (pb) {
+                    const uint16_t e = vpar[B * kThreads + t];
+                    if (e & kRoot) {
+                        pb = false;
+                    } else {
+                        const int p = e & (kLabCap - 1);
+                        const uint16_t g = vpar[p * kThreads + t];
+                        if (g & kRoot) { B = p; pb = false; }
+                        else { vpar[B * kThreads + t] = g; B = g & (kLabCap - 1); }
+                    }
+                }
+                if (i >= cap) {
+                    if (pa || pb) err |= kErrLocalCap;
+                    break;
+                }
+            }
+            if (hq && A != B) {
+                const int lo = A < B ? A : B, hi = A < B ? B : A;
+                vpar[hi * kThreads + t] = (uint16_t)lo;
+            }
+        }
         __syncwarp();
     }
-    if (nrun & 15) {
-        for (int k = nrun & 15; k < 16; ++k) lq.push(0);
-        lout[(size_t)(nrun >> 4) * kThreads] = lq.bits();
-    }
-    // own parent links become block-wide ids: the thread index joins the label
+    if (nrun & 3) lout[(size_t)(nrun >> 2) * kThreads] = lacc >> (8 * (4 - (nrun & 3)));
+    // compress the own lists (labels are still lane-local here, so no other
+    // lane reads them) and turn parent links into block-wide ids: the thread
+    // index joins the label
     const int nlab_max = __reduce_max_sync(kFull, nlab);
     for (int L = 0; L < nlab_max; ++L) {
         if (L < nlab) {
-            const uint16_t e = vpar[L * kThreads + t];
-            if (!(e & kRoot)) vpar[L * kThreads + t] = (uint16_t)((t << 7) | (e & (kLabCap - 1)));
+            // entries already converted by earlier rounds carry this thread's
+            // index in their high bits; the low bits are the lane-local label
+            int x = L;
+            uint16_t e = vpar[x * kThreads + t];
+            for (int i = 0; !(e & kRoot) && i < cap; ++i) {
+                x = e & (kLabCap - 1);
+                e = vpar[x * kThreads + t];
+            }
+            if (x != L) vpar[L * kThreads + t] = (uint16_t)((t << 7) | x);
         }
     }
     __syncthreads();
+
+    // the refinement queue is dead now; its space holds the border bitmap
+    for (int i = t; i < kLabCap * kThreads / 32; i += kThreads) sm.border[i] = 0u;
 
     // -- block merge of the lane tiles along their seams (Kernel 2's boundary
     // analysis applied inside the block, on the shared lists)
@@ -439,6 +440,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
         }
     }
     __syncthreads();
+    // ... and so does every own non-root entry (it points straight at a root,
+    // whose value is final), making a run's value a single lookup
+    for (int L = 0; L < nlab_max; ++L) {
+        if (L < nlab) {
+            const uint16_t e = vpar[L * kThreads + t];
+            if (e < kRootBorder) vpar[L * kThreads + t] = vpar[par_index(e)];
+        }
+    }
 
     // -- border record of the block: the slot of every border pixel
     uint16_t *Eb = s.edges + (size_t)b * kEdge;
@@ -466,19 +475,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
     }
     // -- per-run values: block key of the root, or kBorderFlag | slot
     {
-        const uint4 *lin = s.lstream + (size_t)b * kLChunks * kThreads + t;
+        const uint32_t *lin = s.lstream + (size_t)b * kLWords * kThreads + t;
         uint4 *vout = s.vstream + (size_t)b * kVChunks * kThreads + t;
         HalfQueue vq;
         const int nrun_max = __reduce_max_sync(kFull, nrun);
-        for (int k = 0; k < nrun_max; k += 16) {
-            uint4 c = make_uint4(0, 0, 0, 0);
-            if (k < nrun) c = lin[(size_t)(k >> 4) * kThreads];
-            const uint32_t w4[4] = {c.x, c.y, c.z, c.w};
+        for (int k = 0; k < nrun_max; k += 4) {
+            const uint32_t w = k < nrun ? lin[(size_t)(k >> 2) * kThreads] : 0u;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 4; ++j) {
                 if (k + j < nrun) {
-                    const int L = (w4[j >> 2] >> (8 * (j & 3))) & 0xFF;
-                    vq.push(run_value(vpar, (t << 7) | L));
+                    vq.push(run_value(vpar, (t << 7) | ((w >> (8 * j)) & 0xFF)));
                     if (((k + j + 1) & 7) == 0) vout[(size_t)((k + j) >> 3) * kThreads] = vq.bits();
                 }
             }
@@ -507,8 +513,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_local(ImageArgs a, Scratc
 // (8-connectivity) its two upper corners; the right, bottom and lower corners
 // belong to the neighbouring blocks.  A pair that repeats the pair of the
 // neighbouring pixel is skipped.
+constexpr int kMergeThreads = kBW;  // one thread per top-edge column
+
 template <bool kConn8>
-__global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int nbx, int nby, int cap) {
+__global__ void __launch_bounds__(kMergeThreads) k_block_merge(Scratch s, int nbx, int nby, int cap) {
     const int b = blockIdx.x;
     const int bx = b % nbx, by = b / nbx;
     const uint16_t *E = s.edges + (size_t)b * kEdge;
@@ -523,7 +531,7 @@ __global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int nbx, in
         const int bu = b - nbx;
         const uint16_t *Eu = s.edges + (size_t)bu * kEdge;
         const uint32_t ubase = (uint32_t)bu * kSlots;
-        for (int j = threadIdx.x; j < kBW; j += kThreads) {
+        for (int j = threadIdx.x; j < kBW; j += kMergeThreads) {
             const uint16_t a = E[kEdgeTop + j];
             if (!valid(b, a)) continue;
             const uint16_t aL = j > 0 ? E[kEdgeTop + j - 1] : kBg;
@@ -552,7 +560,7 @@ __global__ void __launch_bounds__(kThreads) k_block_merge(Scratch s, int nbx, in
         const int bl = b - 1;
         const uint16_t *El = s.edges + (size_t)bl * kEdge;
         const uint32_t lbase = (uint32_t)bl * kSlots;
-        for (int j = threadIdx.x; j < kBH; j += kThreads) {
+        for (int j = threadIdx.x; j < kBH; j += kMergeThreads) {
             const uint16_t a = E[kEdgeLeft + j];
             if (!valid(b, a)) continue;
             const uint16_t aU = j > 0 ? E[kEdgeLeft + j - 1] : kBg;
@@ -689,7 +697,7 @@ Layout layout_for(size_t nb) {
     Layout l;
     size_t off = 0;
     l.masks = off;   off += up256(nb * kThreads * kLH * sizeof(uint32_t));
-    l.lstream = off; off += up256(nb * kLChunks * kThreads * sizeof(uint4));
+    l.lstream = off; off += up256(nb * kLWords * kThreads * sizeof(uint32_t));
     l.vstream = off; off += up256(nb * kVChunks * kThreads * sizeof(uint4));
     l.edges = off;   off += up256(nb * kEdge * sizeof(uint16_t));
     l.P = off;       off += up256(nb * kSlots * sizeof(uint64_t));
@@ -711,7 +719,7 @@ static Scratch carve(void *ws, int H, int W) {
     char *p = static_cast<char *>(ws);
     Scratch s;
     s.masks = reinterpret_cast<uint32_t *>(p + l.masks);
-    s.lstream = reinterpret_cast<uint4 *>(p + l.lstream);
+    s.lstream = reinterpret_cast<uint32_t *>(p + l.lstream);
     s.vstream = reinterpret_cast<uint4 *>(p + l.vstream);
     s.edges = reinterpret_cast<uint16_t *>(p + l.edges);
     s.P = reinterpret_cast<uint64_t *>(p + l.P);
@@ -859,11 +867,11 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
     if (conn == 8) {
         k_block_local<true><<<nb, kThreads, sizeof(LocalSmem), stream>>>(a, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<true><<<nb, kThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
+        k_block_merge<true><<<nb, kMergeThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
     } else {
         k_block_local<false><<<nb, kThreads, sizeof(LocalSmem), stream>>>(a, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<false><<<nb, kThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
+        k_block_merge<false><<<nb, kMergeThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
     }
     ev = timing_mark(stream, ev, kKindMerge);
     k_flatten<<<nb, kThreads, 0, stream>>>(s, global_cap, nb * (uint32_t)kSlots);
