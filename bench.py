@@ -45,7 +45,6 @@ BYTES_PER_PIXEL = 5          # 1 B image read + 4 B label written
 KERNEL_BYTES_PER_PIXEL = {   # the path's algorithmic bytes each kernel moves, per pixel
     "k_block_local": 1,      # reads the image once
     "k_block_merge": 0,      # block border records only
-    "k_flatten": 0,          # border slots only
     "k_block_write": 4,      # writes every label once
 }
 SIDE = 4096

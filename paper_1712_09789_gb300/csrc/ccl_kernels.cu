@@ -13,10 +13,9 @@
 //                   component.
 //   k_block_merge   step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
 //                   pairs that straddle a block edge are examined.
-//   k_flatten       step 3, first half (Sec. 3.3): root-find for every border
-//                   slot.
-//   k_block_write   step 3, second half: expands the per-run values over the
-//                   row masks and writes every label once.
+//   k_block_write   step 3 (Sec. 3.3): root-find for the block's border slots
+//                   in the merged union-find, then expands the per-run values
+//                   over the row masks and writes every label once.
 //
 // HBM traffic per pixel: 1 B image read, 4 B label write, plus the row masks
 // (1/8 B written, 1/8 B read) and the per-run values (1 B label and 2 B value
@@ -580,35 +579,18 @@ __global__ void __launch_bounds__(kMergeThreads) k_block_merge(Scratch s, int nb
     report(err);
 }
 
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_flatten(Scratch s, int cap, uint32_t bound) {
-    const int b = blockIdx.x;
-    const int n = s.nslots[b];
-    int err = 0;
-    for (int k = threadIdx.x; k < n; k += kThreads) {
-        const uint32_t slot = (uint32_t)b * kSlots + (uint32_t)k;
-        uint32_t key;
-        const uint32_t root = find_global_ro(s.P, slot, key, cap, err, bound);
-        if (root != slot && !err) ((volatile uint64_t *)s.P)[slot] = pack_slot(key, root);
-    }
-    report(err);
-}
-
-// ---------------------------------------------------------------------------
 struct WriteSmem {
     int slot_label[kSlots];
-    int stage[kBLY][kBW];   // one row of every lane tile row; 16-byte chunks swizzled
+    int runlab[kBLY][kBW];          // label of every run at its start column, one row of all lane tiles
+    uint32_t mask[kLH][kThreads];   // row masks of the block
 };
 
-// Chunk q of a staging row holds columns 4q..4q+3; lane tile tx owns chunks
-// 8tx..8tx+7, stored at q ^ (tx & 7) so that lanes writing the same column of
-// different lane tiles hit different banks.
-__device__ __forceinline__ int stage_index(int col) {
-    const int q = col >> 2;
-    return ((q ^ ((q >> 3) & 7)) << 2) | (col & 3);
-}
+// Position of (lane tile tx, column c) in a runlab row: the column is XORed
+// with tx so that the four lane tiles read by one warp of the copy-out spread
+// over the banks.
+__device__ __forceinline__ int runlab_index(int tx, int c) { return kLW * tx + (c ^ ((tx & 3) << 3)); }
 
-__global__ void __launch_bounds__(kThreads, 4) k_block_write(ImageArgs a, Scratch s) {
+__global__ void __launch_bounds__(kThreads, 4) k_block_write(ImageArgs a, Scratch s, int cap, uint32_t bound) {
     __shared__ WriteSmem sm;
     const int b = blockIdx.x;
     const int bx = b % a.nbx, by = b / a.nbx;
@@ -616,61 +598,88 @@ __global__ void __launch_bounds__(kThreads, 4) k_block_write(ImageArgs a, Scratc
     const int t = threadIdx.x;
     const int tx = t & (kBLX - 1), ty = t >> 4;
 
+    // final label of each border slot: root-find in the merged union-find
+    // (read-only; every union is complete when this kernel starts)
     const int ns = s.nslots[b];
-    for (int k = t; k < ns; k += kThreads)
-        sm.slot_label[k] = (int)(uint32_t)(s.P[(size_t)b * kSlots + k] >> 32) + 1;
+    int err = 0;
+    for (int k = t; k < ns; k += kThreads) {
+        uint32_t key;
+        find_global_ro(s.P, (uint32_t)b * kSlots + (uint32_t)k, key, cap, err, bound);
+        sm.slot_label[k] = (int)key + 1;
+    }
+    report(err);
 
     const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * kThreads + t) * kLH);
     const uint4 mA = mi[0], mB = mi[1];
     const uint32_t mrow[kLH] = {mA.x, mA.y, mA.z, mA.w, mB.x, mB.y, mB.z, mB.w};
+#pragma unroll
+    for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
+    // per-run values, 8 per chunk; the next chunk is always already in flight
     const uint4 *vin = s.vstream + (size_t)b * kVChunks * kThreads + t;
-    uint4 vq = make_uint4(0, 0, 0, 0);
-    int vi = 8, vc = 0;
+    int nrun = 0;
+#pragma unroll
+    for (int r = 0; r < kLH; ++r) nrun += __popc(mrow[r] & ~(mrow[r] << 1));
+    const int nchunks = (nrun + 7) >> 3;
+    uint4 vq = nchunks > 0 ? vin[0] : make_uint4(0, 0, 0, 0);
+    uint4 vnext = nchunks > 1 ? vin[kThreads] : make_uint4(0, 0, 0, 0);
+    int vi = 0, vc = 2;
     __syncthreads();
 
-    int *row = sm.stage[ty];
+    // copy-out geometry: thread t covers 4 pixels of every staged row
+    const int q = t;                       // 4-pixel chunk of a 512-pixel row
+    const int ctx = q >> 3;                // its lane tile
+    const int c0 = (q & 7) * 4;            // its first column inside the lane tile
+    const int x = x0 + 4 * q;
+
 #pragma unroll
     for (int r = 0; r < kLH; ++r) {
+        // each lane tile: one label per run of its row r, at the run start
         const uint32_t m = mrow[r];
-        // background over this lane tile's row, then the runs
-#pragma unroll
-        for (int k = 0; k < kLW / 4; ++k)
-            reinterpret_cast<int4 *>(row)[stage_index(kLW * tx + 4 * k) >> 2] = make_int4(0, 0, 0, 0);
         uint32_t S = m & ~(m << 1);
-        uint32_t E = m & ~(m >> 1);
-        while (S) {
-            const int a0 = lobit(S), a1 = lobit(E);
-            S &= S - 1;
-            E &= E - 1;
-            if (vi == 8) {
-                vq = vin[(size_t)(vc++) * kThreads];
-                vi = 0;
+        const int nmax = __reduce_max_sync(kFull, __popc(S));
+        for (int k = 0; k < nmax; ++k) {
+            if (S) {
+                const int a0 = lobit(S);
+                S &= S - 1u;
+                if (vi == 8) {
+                    vq = vnext;
+                    if (vc < nchunks) vnext = vin[(size_t)vc * kThreads];
+                    ++vc;
+                    vi = 0;
+                }
+                const uint32_t w = vi < 2 ? vq.x : vi < 4 ? vq.y : vi < 6 ? vq.z : vq.w;
+                const uint32_t v = (w >> ((vi & 1) * 16)) & 0xFFFFu;
+                ++vi;
+                const uint32_t slot = v & 0x7FFFu;
+                const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
+                                                   : (int)((uint32_t)(y0 + (int)(v >> kBWLog2)) * (uint32_t)a.W +
+                                                           (uint32_t)(x0 + (int)(v & (kBW - 1)))) + 1;
+                sm.runlab[ty][runlab_index(tx, a0)] = lab;
             }
-            const uint32_t w = vi < 2 ? vq.x : vi < 4 ? vq.y : vi < 6 ? vq.z : vq.w;
-            const uint32_t v = (w >> ((vi & 1) * 16)) & 0xFFFFu;
-            ++vi;
-            const uint32_t slot = v & 0x7FFFu;
-            const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
-                                               : (int)((uint32_t)(y0 + (int)(v >> kBWLog2)) * (uint32_t)a.W +
-                                                       (uint32_t)(x0 + (int)(v & (kBW - 1)))) + 1;
-            for (int c = a0; c <= a1; ++c) row[stage_index(kLW * tx + c)] = lab;
         }
         __syncthreads();
-        // coalesced write-out: image rows y0 + 8*ry + r, 128 chunks of 4 pixels
+        // coalesced write-out of image rows y0 + 8*ry + r: every pixel takes
+        // the label stored at the start of its run
 #pragma unroll
         for (int ry = 0; ry < kBLY; ++ry) {
             const int y = y0 + kLH * ry + r;
-            const int x = x0 + 4 * t;
             if (y < a.H && x < a.W) {
-                const int4 v = reinterpret_cast<const int4 *>(sm.stage[ry])[stage_index(4 * t) >> 2];
+                const uint32_t mm = sm.mask[r][ry * kBLX + ctx];
+                const uint32_t SS = mm & ~(mm << 1);
+                int v[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + j;
+                    v[j] = ((mm >> c) & 1u) ? sm.runlab[ry][runlab_index(ctx, hibit(SS & upto(c)))] : 0;
+                }
                 int32_t *dst = a.labels + (size_t)y * a.W + x;
                 if (a.out_vec_ok && x + 4 <= a.W) {
-                    __stcs(reinterpret_cast<int4 *>(dst), v);
+                    __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
                 } else {
-                    __stcs(dst, v.x);
-                    if (x + 1 < a.W) __stcs(dst + 1, v.y);
-                    if (x + 2 < a.W) __stcs(dst + 2, v.z);
-                    if (x + 3 < a.W) __stcs(dst + 3, v.w);
+                    __stcs(dst, v[0]);
+                    if (x + 1 < a.W) __stcs(dst + 1, v[1]);
+                    if (x + 2 < a.W) __stcs(dst + 2, v[2]);
+                    if (x + 3 < a.W) __stcs(dst + 3, v[3]);
                 }
             }
         }
@@ -819,7 +828,7 @@ int timing_read(double *ms, long long *count, int n) {
 }
 
 const char *kernel_kind_name(int k) {
-    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_flatten", "k_block_write"};
+    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
 }
 
@@ -874,9 +883,7 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
         k_block_merge<false><<<nb, kMergeThreads, 0, stream>>>(s, a.nbx, a.nby, global_cap);
     }
     ev = timing_mark(stream, ev, kKindMerge);
-    k_flatten<<<nb, kThreads, 0, stream>>>(s, global_cap, nb * (uint32_t)kSlots);
-    ev = timing_mark(stream, ev, kKindFlatten);
-    k_block_write<<<nb, kThreads, 0, stream>>>(a, s);
+    k_block_write<<<nb, kThreads, 0, stream>>>(a, s, global_cap, nb * (uint32_t)kSlots);
     ev = timing_mark(stream, ev, kKindRelabel);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
