@@ -113,6 +113,55 @@ ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch,
                           int connectivity, int32_t *host_labels, void *stream);
 
 /*
+ * One image of a batch (device pointers; same rules as ccl_label()).
+ */
+typedef struct {
+    const uint8_t *img;   /* u8 [H][pitch], nonzero = foreground */
+    int32_t *labels;      /* int32 [H][W], row stride W */
+    int H;
+    int W;
+    size_t pitch;         /* input row stride in bytes, >= W */
+} ccl_image;
+
+/*
+ * Label n images of any sizes with one launch sequence (Sec. 3, all three
+ * steps, for every image): persistent kernels take the blocks of all images
+ * from a device work queue, and the sequence is replayed as a CUDA graph
+ * held per (device, stream, connectivity, block shape).  `images` is a host
+ * array of n entries; every entry is checked as in ccl_label() and an invalid
+ * entry fails the whole call with nothing enqueued.  Entries with H or W = 0
+ * are skipped.  Outputs of different entries must not overlap each other or
+ * any input.  The block shape is $CCL_TILE if set (a ccl_tile_name()), else
+ * the one tuned for this GPU, connectivity and mean image area; when none is
+ * tuned yet the call runs ccl_autotune_batched() first, which labels the
+ * batch several times (same result) and remembers the choice.  The library
+ * owns per-stream device scratch and page-locked staging, grown on demand
+ * (growth allocates; make one call outside stream capture first).
+ * Asynchronous on `stream`.
+ */
+ccl_status ccl_label_batched(const ccl_image *images, int n, int connectivity, void *stream);
+
+/* ccl_label_batched() with an explicit block shape (0 .. ccl_tile_count()-1). */
+ccl_status ccl_label_batched_tile(const ccl_image *images, int n, int connectivity, int tile,
+                                  void *stream);
+
+/*
+ * Times every block shape on this batch (the batch is labelled each time),
+ * keeps the fastest for the batch's size class -- in memory and appended to
+ * $CCL_AUTOTUNE_CACHE or ~/.cache/ccl_gb300/autotune.txt -- and writes it to
+ * *tile (may be NULL).  Waits for `stream`.
+ */
+ccl_status ccl_autotune_batched(const ccl_image *images, int n, int connectivity, void *stream,
+                                int *tile);
+
+/* Block shape ccl_label_batched() would use for this batch; -1 if untuned. */
+ccl_status ccl_batched_tile(const ccl_image *images, int n, int connectivity, int *tile);
+
+/* Number of block shapes, and the name of one ("512x64": width x height). */
+int ccl_tile_count(void);
+const char *ccl_tile_name(int tile);
+
+/*
  * ccl_label() for callers that may not allocate device memory while they run
  * -- e.g. a program that gave all of the GPU's memory to its own pool at
  * start-up, or a latency-critical loop that must not call cudaMalloc/cudaFree

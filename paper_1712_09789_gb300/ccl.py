@@ -40,6 +40,14 @@ class CclError(RuntimeError):
 
 
 _c = ctypes
+
+
+class CclImage(ctypes.Structure):
+    """``ccl_image``: one entry of a batch."""
+    _fields_ = [("img", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("pitch", ctypes.c_size_t)]
+
+
 _SIGS = {
     "ccl_status_string": (_c.c_char_p, [_c.c_int]),
     "ccl_version": (_c.c_int, []),
@@ -54,6 +62,13 @@ _SIGS = {
     "ccl_label_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
                                      _c.c_void_p]),
     "ccl_noalloc_max_workspace_bytes": (_c.c_size_t, []),
+    "ccl_label_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p]),
+    "ccl_label_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_int, _c.c_void_p]),
+    "ccl_autotune_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p,
+                                        _c.POINTER(_c.c_int)]),
+    "ccl_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.POINTER(_c.c_int)]),
+    "ccl_tile_count": (_c.c_int, []),
+    "ccl_tile_name": (_c.c_char_p, [_c.c_int]),
     "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
     "ccl_debug_kernel_timing": (None, [_c.c_int]),
     "ccl_debug_kernel_times": (_c.c_int, [_c.POINTER(_c.c_double), _c.POINTER(_c.c_longlong), _c.c_int]),
@@ -219,3 +234,51 @@ def ccl_debug_kernel_times() -> dict:
     cnt = (ctypes.c_longlong * n)()
     lib.ccl_debug_kernel_times(ms, cnt, n)
     return {lib.ccl_debug_kernel_name(k).decode(): (ms[k], cnt[k]) for k in range(n)}
+
+
+def _batch_array(pairs):
+    """ctypes array of CclImage from (image, labels) tensor pairs."""
+    arr = (CclImage * max(1, len(pairs)))()
+    for i, (img, lab) in enumerate(pairs):
+        H, W, pitch = _image_args(img)
+        _labels_for(img, lab)
+        arr[i] = CclImage(img.data_ptr(), lab.data_ptr(), H, W, pitch)
+    return arr
+
+
+def ccl_label_batched(pairs, connectivity: int = 8, stream=None, tile: int | None = None):
+    """Label a batch of ``(image, labels)`` CUDA tensor pairs in one launch
+    sequence (``ccl_label_batched``; ``ccl_label_batched_tile`` when ``tile``
+    is given).  Returns the labels tensors."""
+    import torch
+
+    dev = pairs[0][0].device if pairs else torch.device("cuda", torch.cuda.current_device())
+    arr = _batch_array(pairs)
+    sp = _stream_ptr(stream, dev)
+    if tile is None:
+        st = load().ccl_label_batched(arr, len(pairs), connectivity, sp)
+    else:
+        st = load().ccl_label_batched_tile(arr, len(pairs), connectivity, tile, sp)
+    _check(st, "ccl_label_batched")
+    return [lab for _, lab in pairs]
+
+
+def ccl_autotune_batched(pairs, connectivity: int = 8, stream=None) -> int:
+    """Time every block shape on the batch, remember and return the fastest."""
+    arr = _batch_array(pairs)
+    out = ctypes.c_int(-1)
+    _check(load().ccl_autotune_batched(arr, len(pairs), connectivity, _stream_ptr(stream, pairs[0][0].device),
+                                       ctypes.byref(out)), "ccl_autotune_batched")
+    return out.value
+
+
+def ccl_batched_tile(pairs, connectivity: int = 8) -> int:
+    arr = _batch_array(pairs)
+    out = ctypes.c_int(-1)
+    _check(load().ccl_batched_tile(arr, len(pairs), connectivity, ctypes.byref(out)), "ccl_batched_tile")
+    return out.value
+
+
+def ccl_tile_names() -> list:
+    lib = load()
+    return [lib.ccl_tile_name(i).decode() for i in range(lib.ccl_tile_count())]

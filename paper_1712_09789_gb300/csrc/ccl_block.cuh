@@ -1,12 +1,13 @@
 // ccl_block.cuh -- device building blocks of the block-based labeller.
 //
-// Geometry.  A CTA of 128 threads owns a 512 x 64 pixel block.  Thread t owns
-// one lane tile of 32 columns x 8 rows (tx = t % 16, ty = t / 16) and scans
-// it row by row, holding each row as a 32-bit mask (bit c = column c).  The
-// paper's Kernel 1 assigns one thread per pixel and iterates over the whole
-// block; here one thread walks its rows sequentially, which makes the
-// label-equivalence work proportional to the number of row runs, and 128
-// such walks run side by side.
+// Geometry.  A CTA owns a block of (32 * BLX) x (8 * BLY) pixels and has one
+// thread per lane tile of 32 columns x 8 rows (tx = t % BLX, ty = t / BLX).
+// A thread scans its lane tile row by row, holding each row as a 32-bit mask
+// (bit c = column c).  The paper's Kernel 1 assigns one thread per pixel and
+// iterates over the whole block; here one thread walks its rows in order,
+// which makes the label-equivalence work proportional to the number of row
+// runs, and BLX * BLY such walks run side by side.  The block shape (BLX, BLY)
+// is a template parameter so that the batched path can pick it per workload.
 //
 // Label-equivalence lists.  Every lane tile numbers its own labels 0..127 in
 // creation order (creation order is raster order inside the lane tile, so the
@@ -14,8 +15,8 @@
 // 16-bit word in shared memory: a root holds kRoot | node, node = r*32 + c its
 // first pixel; any other entry holds the id (t << 7) | label of its parent,
 // which may belong to another lane tile once the tiles of a block are merged.
-// Entry of id i lives at par[(i & 127) * 128 + (i >> 7)], so the 32 lanes of a
-// warp touching their own label L hit 32 consecutive half-words.
+// Entry of id i lives at par[(i & 127) * threads + (i >> 7)], so the 32 lanes of
+// a warp touching their own label L hit 32 consecutive half-words.
 #pragma once
 
 #include <cstdint>
@@ -25,33 +26,47 @@ namespace ccl {
 
 constexpr int kLW = 32;                 // lane tile width (bits of a row mask)
 constexpr int kLH = 8;                  // lane tile height (rows walked by a thread)
-constexpr int kBLX = 16;                // lane tiles across a block
-constexpr int kBLY = 8;                 // lane tiles down a block
-constexpr int kBW = kLW * kBLX;         // 512
-constexpr int kBH = kLH * kBLY;         // 64
-constexpr int kBWLog2 = 9;
-constexpr int kThreads = kBLX * kBLY;   // 128
 constexpr int kLabCap = kLH * 16;       // labels per lane tile (<= 16 runs per row)
 constexpr int kRunCap = kLH * 16;       // runs per lane tile
-// A component touching the block border meets the border cycle (2*(512+64)-4
-// pixels) in at least one maximal foreground arc, and the cycle holds at
-// most half its length in arcs.
-constexpr int kSlots = kBW + kBH;       // 576 >= 574
-constexpr int kEdgeTop = 0;
-constexpr int kEdgeBottom = kBW;
-constexpr int kEdgeLeft = 2 * kBW;
-constexpr int kEdgeRight = 2 * kBW + kBH;
-constexpr int kEdge = 2 * kBW + 2 * kBH;
+constexpr int kLWords = kRunCap / 4;    // 4 one-byte labels per 32-bit word
+constexpr int kVChunks = kRunCap / 8;   // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
+constexpr uint16_t kRootBorder = 0x4000;
 constexpr uint16_t kBg = 0xFFFF;
 constexpr uint16_t kBorderFlag = 0x8000;  // per-run value: border slot, else block key
 constexpr unsigned kFull = 0xFFFFFFFFu;
-constexpr int kLabPitch = 132;          // bytes per column row of the label buffers
-constexpr int kLWords = kRunCap / 4;    // 4 one-byte labels per 32-bit word
-constexpr int kVChunks = kRunCap / 8;   // 8 two-byte values per 16-byte chunk
 
 constexpr int kErrLocalCap = 1;
 constexpr int kErrGlobalCap = 2;
+
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+
+template <int BLX_, int BLY_>
+struct Geo {
+    static constexpr int BLX = BLX_;                  // lane tiles across a block
+    static constexpr int BLY = BLY_;                  // lane tiles down a block
+    static constexpr int kThreads = BLX * BLY;
+    static constexpr int kBW = kLW * BLX;
+    static constexpr int kBH = kLH * BLY;
+    static constexpr int kBWLog2 = ilog2(kBW);
+    static constexpr int kBLXLog2 = ilog2(BLX);
+    // A component touching the block border meets the border cycle
+    // (2*(kBW + kBH) - 4 pixels) in at least one maximal foreground arc, and
+    // the cycle holds at most half its length in arcs.
+    static constexpr int kSlots = kBW + kBH;
+    static constexpr int kEdgeTop = 0;
+    static constexpr int kEdgeBottom = kBW;
+    static constexpr int kEdgeLeft = 2 * kBW;
+    static constexpr int kEdgeRight = 2 * kBW + kBH;
+    static constexpr int kEdge = 2 * kBW + 2 * kBH;
+    static constexpr int kLabPitch = kThreads + 4;    // bytes per column row of the label buffers
+    // ids carry the thread index above 7 label bits and stay below kRootBorder;
+    // block keys fit the 15 bits of a per-run value
+    static_assert(kThreads >= 32 && kThreads <= 128 && (kThreads & (kThreads - 1)) == 0,
+                  "32..128 threads, a power of two");
+    static_assert((BLX & (BLX - 1)) == 0, "BLX must be a power of two");
+    static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
+};
 
 // bits 0..c set (c in [0,31]); c == 31 wraps to all ones
 __device__ __forceinline__ uint32_t upto(int c) { return (2u << c) - 1u; }
@@ -94,27 +109,30 @@ __device__ __forceinline__ uint32_t touch_range(uint32_t rm) {
 // Shared-memory label-equivalence lists of one block.
 
 // (masked on both fields, so no entry value can address outside the table)
+template <class G>
 __device__ __forceinline__ int par_index(int id) {
-    return (id & (kLabCap - 1)) * kThreads + ((id >> 7) & (kThreads - 1));
+    return (id & (kLabCap - 1)) * G::kThreads + ((id >> 7) & (G::kThreads - 1));
 }
 
-// Block raster key (row * 512 + column) of a root, from its id and entry.
+// Block raster key (row * block width + column) of a root, from its id and entry.
+template <class G>
 __device__ __forceinline__ int root_key(int id, uint16_t entry) {
     const int t = id >> 7;
     const int node = entry & 0xFF;
-    return ((kLH * (t >> 4) + (node >> 5)) << kBWLog2) + kLW * (t & (kBLX - 1)) + (node & 31);
+    return ((kLH * (t >> G::kBLXLog2) + (node >> 5)) << G::kBWLog2) + kLW * (t & (G::BLX - 1)) + (node & 31);
 }
 
 // Root of id and the root's entry.  Path halving rewrites only non-root
 // entries, and links are only ever made on roots (by CAS), so the two never
 // overwrite each other.
+template <class G>
 __device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t &rentry, int cap, int &err) {
     for (int i = 0; i < cap; ++i) {
-        const uint16_t e = par[par_index(x)];
+        const uint16_t e = par[par_index<G>(x)];
         if (e & kRoot) { rentry = e; return x; }
-        const uint16_t g = par[par_index(e)];
+        const uint16_t g = par[par_index<G>(e)];
         if (g & kRoot) { rentry = g; return e; }
-        par[par_index(x)] = g;
+        par[par_index<G>(x)] = g;
         x = g;
     }
     err |= kErrLocalCap;
@@ -126,9 +144,10 @@ __device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t
 // by threads that then store the root into entries.  (A halving find there
 // could store an older grandparent over an entry that another thread had
 // already set to its root.)
+template <class G>
 __device__ __forceinline__ int find_root_ro(const volatile uint16_t *par, int x, int cap, int &err) {
     for (int i = 0; i < cap; ++i) {
-        const uint16_t e = par[par_index(x)];
+        const uint16_t e = par[par_index<G>(x)];
         if (e & kRoot) return x;
         x = e;
     }
@@ -136,46 +155,29 @@ __device__ __forceinline__ int find_root_ro(const volatile uint16_t *par, int x,
     return x;
 }
 
-// Merge the lists of ids a and b: the root with the larger key is hung under
-// the root with the smaller key (Sec. 3.1.3 and 3.2: the larger label points
-// to the smaller).  A failed CAS means the root changed meanwhile; retry.
-__device__ __forceinline__ void union_block(uint16_t *par, int a, int b, int cap, int &err) {
-    volatile uint16_t *vp = par;
-    for (int i = 0; i < cap; ++i) {
-        uint16_t ea, eb;
-        a = find_root(vp, a, ea, cap, err);
-        b = find_root(vp, b, eb, cap, err);
-        if (a == b || err) return;
-        if (root_key(a, ea) < root_key(b, eb)) {
-            const int t = a; a = b; b = t;
-            const uint16_t u = ea; ea = eb; eb = u;
-        }
-        const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index(a)),
-                                             (unsigned short)ea, (unsigned short)b);
-        if (old == ea) return;
-    }
-    err |= kErrLocalCap;
-}
-
-// union_block() called by all 32 lanes of a warp together; lanes with
-// valid == false only keep step.  The retry loop runs until no lane needs
-// another round, so the warp stays converged between rounds.
+// Merge the lists of ids a and b, called by all 32 lanes of a warp together
+// (lanes with valid == false only keep step): the root with the larger key is
+// hung under the root with the smaller key (Sec. 3.1.3 and 3.2: the larger
+// label points to the smaller).  A failed CAS means the root changed
+// meanwhile; the round repeats until no lane needs another, so the warp stays
+// converged between rounds.
+template <class G>
 __device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int a, int b, int cap, int &err) {
     volatile uint16_t *vp = par;
     bool pend = valid;
     for (int i = 0; __any_sync(kFull, pend); ++i) {
         if (pend) {
             uint16_t ea, eb;
-            a = find_root(vp, a, ea, cap, err);
-            b = find_root(vp, b, eb, cap, err);
+            a = find_root<G>(vp, a, ea, cap, err);
+            b = find_root<G>(vp, b, eb, cap, err);
             if (a == b || err) {
                 pend = false;
             } else {
-                if (root_key(a, ea) < root_key(b, eb)) {
+                if (root_key<G>(a, ea) < root_key<G>(b, eb)) {
                     const int t = a; a = b; b = t;
                     const uint16_t u = ea; ea = eb; eb = u;
                 }
-                const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index(a)),
+                const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index<G>(a)),
                                                      (unsigned short)ea, (unsigned short)b);
                 if (old == ea) pend = false;
             }
@@ -189,13 +191,12 @@ __device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int 
 
 // After the lists of a block are final, root entries are rewritten as the
 // value every run of that list needs later: kRootBorder | slot for a root
-// that owns a block-border pixel, kRoot | block key otherwise.  Non-root
-// entries (ids, < 0x4000) point straight at their root.
-constexpr uint16_t kRootBorder = 0x4000;
-
+// that owns a block-border pixel, kRoot | block key otherwise; non-root
+// entries then take their root's value.
+template <class G>
 __device__ __forceinline__ uint16_t run_value(const volatile uint16_t *par, int id) {
-    uint16_t e = par[par_index(id)];
-    if (e < kRootBorder) e = par[par_index(e)];
+    uint16_t e = par[par_index<G>(id)];
+    if (e < kRootBorder) e = par[par_index<G>(e)];
     // still a pointer only when an iteration cap cut the compression short
     // (the error word is set then); decode it as block key 0, never as a slot
     if (e < kRootBorder) return 0;
@@ -203,11 +204,12 @@ __device__ __forceinline__ uint16_t run_value(const volatile uint16_t *par, int 
 }
 
 // ---------------------------------------------------------------------------
-// Global union-find over border slots.  Slot s = block * kSlots + k stands for
-// the k-th border-touching component of a block; P[s] packs
+// Global union-find over border slots.  Slot s = block * slots-per-block + k
+// stands for the k-th border-touching component of a block; P[s] packs
 // (key of parent << 32) | parent slot, the key being the component's minimum
 // global raster position; a root has P[s] == (key(s) << 32) | s.  atomicMin on
 // the packed word hangs the root with the larger key under the smaller one.
+// Every walk checks pointers against `bound` (the number of slots).
 
 __device__ __forceinline__ uint64_t pack_slot(uint32_t key, uint32_t slot) {
     return ((uint64_t)key << 32) | slot;
@@ -235,7 +237,7 @@ __device__ __forceinline__ uint32_t find_global(uint64_t *P, uint32_t s, uint32_
     return s;
 }
 
-// Read-only root-find for the flatten step (see find_root_ro).
+// Read-only root-find, for threads that only need the final key.
 __device__ __forceinline__ uint32_t find_global_ro(const uint64_t *P, uint32_t s, uint32_t &key, int cap,
                                                    int &err, uint32_t bound) {
     const volatile uint64_t *vp = P;

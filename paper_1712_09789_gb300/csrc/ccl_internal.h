@@ -9,8 +9,57 @@
 
 namespace ccl {
 
+// One image of a launch.  Blocks of the image are the consecutive work items
+// block0 .. block0 + nbx*nby - 1, in raster order.
+constexpr unsigned kJobVecIn = 1;   // img and pitch are 16-byte aligned
+constexpr unsigned kJobVecOut = 2;  // labels are 16-byte aligned and W % 4 == 0
+struct Job {
+    const uint8_t *img;
+    int32_t *labels;
+    unsigned long long pitch;
+    int H, W;
+    int nbx, nby;
+    unsigned block0;
+    unsigned flags;
+};
+
+// Device header in front of a batch's job array.  The counters are the work
+// queues of the three kernels and must be zero when the launch starts.
+struct JobHeader {
+    unsigned njobs;
+    unsigned total;       // work items (blocks) over all jobs
+    unsigned counter[4];
+    unsigned pad[2];
+};
+
+// Kernel argument: a batch (hdr and jobs in device memory, persistent CTAs)
+// or, when hdr is null, the single job and its block count.
+struct JobTable {
+    JobHeader *hdr;
+    const Job *jobs;
+    Job single;
+    unsigned total;
+};
+
+// Block shapes (lane tiles across x down): 0 = 16x8 (512x64 pixels, 128
+// threads), 1 = 8x8 (256x64, 64 threads), 2 = 32x4 (1024x32, 128 threads).
+constexpr int kNumGeo = 3;
+const char *geo_name(int geo);
+size_t geo_blocks(int geo, int H, int W);
+size_t geo_workspace_bytes(int geo, size_t blocks);
+void geo_block_shape(int geo, int *bw, int *bh);
+
 // Scratch bytes needed by launch_label() for an H x W image.
 size_t workspace_bytes(int H, int W);
+
+// Per-device set-up of a block shape (kernel attributes, occupancy); done
+// implicitly by the launchers, and explicitly before a stream capture.
+int prepare_geo(int geo);
+
+// Enqueues the labelling of a batch: hdr/jobs are device copies (counters
+// zero) for `capacity` blocks of scratch in `ws`.  Persistent grids.
+int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t capacity,
+                cudaStream_t stream, int cap);
 
 // Enqueues the whole labelling of one image on `stream`.  `ws` must hold
 // workspace_bytes(H, W) bytes, 256-byte aligned.  `cap` <= 0 selects the
