@@ -161,6 +161,75 @@ ccl_status ccl_batched_tile(const ccl_image *images, int n, int connectivity, in
 int ccl_tile_count(void);
 const char *ccl_tile_name(int tile);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching server for frames held in host memory.  The
+ * paper labels single images; batching, admission and latency accounting are
+ * properties of this library.
+ *
+ * A scheduler thread keeps submitted requests in arrival order and starts a
+ * batch on an idle CUDA stream with as many requests from the front of the
+ * queue as fit: at most max_batch per batch, at most max_slots on the device
+ * at once, device buffers carved from a resident arena of hbm_budget_bytes
+ * (the admission is by free arena memory) and one connectivity per batch.
+ * Requests that arrive while others run are admitted as slots and memory free
+ * up.  A batch is: frame copies in, one batched labelling (ccl_label_batched
+ * with the tuned or default block shape), label copies out.  Batches on
+ * different streams overlap on the device.
+ */
+typedef struct {
+    int max_slots;            /* requests on the device at once, >= 1 */
+    int n_streams;            /* CUDA streams, 1..16 */
+    int max_batch;            /* requests per batch, >= 1 */
+    int device;               /* CUDA device ordinal */
+    size_t hbm_budget_bytes;  /* resident frame arena (inputs + labels), >= 1 MiB */
+} ccl_server_config;
+
+typedef struct {
+    uint64_t submitted, completed, rejected;
+    int in_flight, queued;
+    uint64_t pixels;                    /* labelled pixels */
+    size_t arena_bytes, arena_used_bytes;
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* submit -> labels in host memory */
+    double gpixel_s;                    /* pixels / (last completion - first submit) */
+} ccl_server_stats_t;
+
+typedef struct ccl_server ccl_server;
+
+/* Creates a server (allocates its arena and streams, starts its thread). */
+ccl_status ccl_server_create(const ccl_server_config *config, ccl_server **server);
+
+/*
+ * Queues one frame: host_img u8 [H][pitch], host_labels int32 [H][W], both
+ * owned by the caller and untouched by it until the request completes
+ * (page-locked memory gives asynchronous copies).  Writes a ticket.
+ * CCL_ERR_INVALID_ARG as ccl_label() (and for an empty frame),
+ * CCL_ERR_UNSUPPORTED for a frame larger than the whole arena.
+ */
+ccl_status ccl_server_submit(ccl_server *server, const uint8_t *host_img, int H, int W, size_t pitch,
+                             int connectivity, int32_t *host_labels, uint64_t *ticket);
+
+/*
+ * Waits for a request (timeout_ms < 0: no limit).  Returns the request's
+ * status once it completed and forgets the ticket; CCL_ERR_BUSY when the
+ * timeout passed first (the ticket stays valid); CCL_ERR_NOT_FOUND for an
+ * unknown or already collected ticket.
+ */
+ccl_status ccl_server_wait(ccl_server *server, uint64_t ticket, int timeout_ms);
+
+/* Non-blocking: the request's status if complete, else CCL_ERR_BUSY. */
+ccl_status ccl_server_poll(ccl_server *server, uint64_t ticket);
+
+/* Counters and latency percentiles since creation or the last reset. */
+ccl_status ccl_server_stats(ccl_server *server, ccl_server_stats_t *stats);
+ccl_status ccl_server_reset_stats(ccl_server *server);
+
+/*
+ * Stops admitting, lets the batches on the device finish, fails requests that
+ * never started with CCL_ERR_BUSY, and frees everything.  No call on the
+ * server may follow, and none may be in progress.
+ */
+void ccl_server_destroy(ccl_server *server);
+
 /*
  * ccl_label() for callers that may not allocate device memory while they run
  * -- e.g. a program that gave all of the GPU's memory to its own pool at

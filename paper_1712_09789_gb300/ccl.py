@@ -48,6 +48,21 @@ class CclImage(ctypes.Structure):
                 ("W", ctypes.c_int), ("pitch", ctypes.c_size_t)]
 
 
+class CclServerConfig(ctypes.Structure):
+    """``ccl_server_config``."""
+    _fields_ = [("max_slots", ctypes.c_int), ("n_streams", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("device", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_size_t)]
+
+
+class CclServerStats(ctypes.Structure):
+    """``ccl_server_stats_t``."""
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("in_flight", ctypes.c_int), ("queued", ctypes.c_int), ("pixels", ctypes.c_uint64),
+                ("arena_bytes", ctypes.c_size_t), ("arena_used_bytes", ctypes.c_size_t),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
+                ("mean_ms", ctypes.c_double), ("gpixel_s", ctypes.c_double)]
+
+
 _SIGS = {
     "ccl_status_string": (_c.c_char_p, [_c.c_int]),
     "ccl_version": (_c.c_int, []),
@@ -68,6 +83,14 @@ _SIGS = {
                                         _c.POINTER(_c.c_int)]),
     "ccl_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.POINTER(_c.c_int)]),
     "ccl_tile_count": (_c.c_int, []),
+    "ccl_server_create": (_c.c_int, [_c.POINTER(CclServerConfig), _c.POINTER(_c.c_void_p)]),
+    "ccl_server_submit": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
+                                     _c.c_void_p, _c.POINTER(_c.c_uint64)]),
+    "ccl_server_wait": (_c.c_int, [_c.c_void_p, _c.c_uint64, _c.c_int]),
+    "ccl_server_poll": (_c.c_int, [_c.c_void_p, _c.c_uint64]),
+    "ccl_server_stats": (_c.c_int, [_c.c_void_p, _c.POINTER(CclServerStats)]),
+    "ccl_server_reset_stats": (_c.c_int, [_c.c_void_p]),
+    "ccl_server_destroy": (None, [_c.c_void_p]),
     "ccl_tile_name": (_c.c_char_p, [_c.c_int]),
     "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
     "ccl_debug_kernel_timing": (None, [_c.c_int]),
@@ -282,3 +305,58 @@ def ccl_batched_tile(pairs, connectivity: int = 8) -> int:
 def ccl_tile_names() -> list:
     lib = load()
     return [lib.ccl_tile_name(i).decode() for i in range(lib.ccl_tile_count())]
+
+
+class CclServer:
+    """Binding of the ``ccl_server_*`` entry points.  Host frames are numpy
+    arrays (uint8 image, int32 labels of the same shape); the server keeps a
+    reference to both until the request is collected with ``wait``."""
+
+    def __init__(self, max_slots=64, n_streams=4, max_batch=32, hbm_budget_bytes=4 << 30, device=0):
+        cfg = CclServerConfig(max_slots, n_streams, max_batch, device, hbm_budget_bytes)
+        handle = ctypes.c_void_p()
+        _check(load().ccl_server_create(ctypes.byref(cfg), ctypes.byref(handle)), "ccl_server_create")
+        self._h = handle
+        self._keep = {}
+
+    def submit(self, img: np.ndarray, labels: np.ndarray, connectivity: int = 8) -> int:
+        if img.dtype != np.uint8 or img.ndim != 2 or (img.shape[0] > 1 and img.strides[1] != 1):
+            raise ValueError("image must be a 2D uint8 array with contiguous rows")
+        if labels.dtype != np.int32 or labels.shape != img.shape or not labels.flags.c_contiguous:
+            raise ValueError("labels must be a contiguous int32 array of the image's shape")
+        H, W = img.shape
+        pitch = img.strides[0] if H > 1 else W
+        t = ctypes.c_uint64(0)
+        _check(load().ccl_server_submit(self._h, img.ctypes.data, H, W, pitch, connectivity, labels.ctypes.data,
+                                        ctypes.byref(t)), "ccl_server_submit")
+        self._keep[t.value] = (img, labels)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        st = load().ccl_server_wait(self._h, ticket, timeout_ms)
+        if st != CCL_ERR_BUSY:
+            self._keep.pop(ticket, None)
+        return st
+
+    def poll(self, ticket: int) -> int:
+        return load().ccl_server_poll(self._h, ticket)
+
+    def stats(self) -> dict:
+        st = CclServerStats()
+        _check(load().ccl_server_stats(self._h, ctypes.byref(st)), "ccl_server_stats")
+        return {name: getattr(st, name) for name, _ in CclServerStats._fields_}
+
+    def reset_stats(self) -> None:
+        _check(load().ccl_server_reset_stats(self._h), "ccl_server_reset_stats")
+
+    def close(self) -> None:
+        if self._h:
+            load().ccl_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -225,14 +225,26 @@ void store_cache_locked(const std::string &key, int geo) {
     if (f) f << key << ' ' << geo << '\n';
 }
 
-std::string size_key(const ccl_image *images, int n, int conn) {
+// GPU name with blanks replaced, looked up once per device.
+std::string device_name() {
+    static std::mutex mu;
+    static std::map<int, std::string> names;
     int dev = 0;
     cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = names.find(dev);
+    if (it != names.end()) return it->second;
     cudaDeviceProp prop{};
     cudaGetDeviceProperties(&prop, dev);
     std::string name(prop.name);
     for (char &c : name)
         if (c == ' ') c = '_';
+    names[dev] = name;
+    return name;
+}
+
+std::string size_key(const ccl_image *images, int n, int conn) {
+    const std::string name = device_name();
     double area = 0;
     int m = 0;
     for (int i = 0; i < n; ++i)
