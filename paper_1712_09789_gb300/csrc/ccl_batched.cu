@@ -4,10 +4,10 @@
 // autotuner.
 //
 // Per (device, stream, connectivity, block shape) the library keeps a runner:
-// a device job table (header with the three work counters, then one Job per
+// a device job table (header with the kernels' work counters, then one Job per
 // image), the scratch for `capacity` blocks, and a ring of page-locked staging
 // copies of the job table, each with its own instantiated graph.  A graph is
-// [copy staging -> device table] + the three kernels; a call fills the next
+// [copy staging -> device table] + the labelling launches; a call fills the next
 // ring slot (after the slot's previous replay has finished) and replays that
 // slot's graph on the caller's stream.  Growing the capacity rebuilds the
 // graphs.

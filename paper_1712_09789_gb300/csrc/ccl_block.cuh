@@ -2,21 +2,28 @@
 //
 // Geometry.  A CTA owns a block of (32 * BLX) x (8 * BLY) pixels and has one
 // thread per lane tile of 32 columns x 8 rows (tx = t % BLX, ty = t / BLX).
-// A thread scans its lane tile row by row, holding each row as a 32-bit mask
-// (bit c = column c).  The paper's Kernel 1 assigns one thread per pixel and
-// iterates over the whole block; here one thread walks its rows in order,
-// which makes the label-equivalence work proportional to the number of row
-// runs, and BLX * BLY such walks run side by side.  The block shape (BLX, BLY)
-// is a template parameter so that the batched path can pick it per workload.
+// A thread holds each row of its lane tile as a 32-bit mask (bit c = column
+// c).  The block shape (BLX, BLY) is a template parameter so that the batched
+// path can pick it per workload.
 //
-// Label-equivalence lists.  Every lane tile numbers its own labels 0..127 in
-// creation order (creation order is raster order inside the lane tile, so the
-// smallest label of a list is also its smallest pixel).  A list entry is a
-// 16-bit word in shared memory: a root holds kRoot | node, node = r*32 + c its
-// first pixel; any other entry holds the id (t << 7) | label of its parent,
-// which may belong to another lane tile once the tiles of a block are merged.
-// Entry of id i lives at par[(i & 127) * threads + (i >> 7)], so the 32 lanes of
-// a warp touching their own label L hit 32 consecutive half-words.
+// Bands and pieces.  A lane tile is cut into bands of rows: one row for
+// 4-connectivity, two rows for 8-connectivity.  A piece is a maximal run of
+// set bits of the band's column mask (the OR of its rows).  With one row a
+// piece is a row run.  With two rows every foreground pixel of a column run of
+// the OR is 8-adjacent to every pixel of the neighbouring column (|dx| <= 1,
+// |dy| <= 1), so a piece is exactly one 8-connected component of the band:
+// the band's labelling costs bit operations only, and there are fewer pieces
+// than row runs.  Pieces are numbered per lane tile in band order, then
+// column order, which is recomputable from the masks by a popcount.
+//
+// Label-equivalence lists.  Piece `loc` of thread t has the id (t << 7) | loc
+// and one 16-bit entry in shared memory: a root holds kRoot | key, key being
+// the block raster position (row * block width + column) of the smallest
+// pixel of its list; any other entry holds the id of its parent.  Links go
+// from the larger key to the smaller (Sec. 3.1.3 and 3.2), so the root of a
+// component carries the component's smallest block raster position.  Entry of
+// id i lives at par[(i & 127) * threads + (i >> 7)], so 32 lanes touching
+// their own piece loc hit 32 consecutive half-words.
 #pragma once
 
 #include <cstdint>
@@ -25,15 +32,12 @@
 namespace ccl {
 
 constexpr int kLW = 32;                 // lane tile width (bits of a row mask)
-constexpr int kLH = 8;                  // lane tile height (rows walked by a thread)
-constexpr int kLabCap = kLH * 16;       // labels per lane tile (<= 16 runs per row)
-constexpr int kRunCap = kLH * 16;       // runs per lane tile
-constexpr int kLWords = kRunCap / 4;    // 4 one-byte labels per 32-bit word
-constexpr int kVChunks = kRunCap / 8;   // 8 two-byte values per 16-byte chunk
+constexpr int kLH = 8;                  // lane tile height (rows of a thread)
+constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile, one-row bands
+constexpr int kVChunksMax = kPieceCapMax / 8;  // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
-constexpr uint16_t kRootBorder = 0x4000;
 constexpr uint16_t kBg = 0xFFFF;
-constexpr uint16_t kBorderFlag = 0x8000;  // per-run value: border slot, else block key
+constexpr uint16_t kBorderFlag = 0x8000;  // per-piece value: border slot, else block key
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 constexpr int kErrLocalCap = 1;
@@ -59,13 +63,22 @@ struct Geo {
     static constexpr int kEdgeLeft = 2 * kBW;
     static constexpr int kEdgeRight = 2 * kBW + kBH;
     static constexpr int kEdge = 2 * kBW + 2 * kBH;
-    static constexpr int kLabPitch = kThreads + 4;    // bytes per column row of the label buffers
-    // ids carry the thread index above 7 label bits and stay below kRootBorder;
-    // block keys fit the 15 bits of a per-run value
+    // ids carry the thread index above 7 piece bits and stay below kRoot;
+    // block keys fit 15 bits
     static_assert(kThreads >= 32 && kThreads <= 128 && (kThreads & (kThreads - 1)) == 0,
                   "32..128 threads, a power of two");
     static_assert((BLX & (BLX - 1)) == 0, "BLX must be a power of two");
     static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
+    static_assert((kEdge * 2) % 16 == 0, "border records must stay 16-byte aligned");
+};
+
+// Band layout of a lane tile for one connectivity.
+template <bool kConn8>
+struct Bands {
+    static constexpr int kRows = kConn8 ? 2 : 1;  // rows per band
+    static constexpr int kN = kLH / kRows;         // bands per lane tile
+    static constexpr int kCap = 16 * kN;           // pieces per lane tile (<= 16 per band)
+    static constexpr int kVChunks = kCap / 8;
 };
 
 // bits 0..c set (c in [0,31]); c == 31 wraps to all ones
@@ -98,41 +111,36 @@ __device__ __forceinline__ uint4 ldg_nc16(const void *p) {
 // the bits a0..31.
 __device__ __forceinline__ uint32_t run_bits(int a0, int a1) { return (2u << a1) - (1u << a0); }
 
-// Columns of the neighbouring row that touch a run: the run itself, widened by
-// one column on each side for 8-connectivity.
+// Columns of the neighbouring row that touch the given pixels of a row: the
+// pixels themselves, widened by one column on each side for 8-connectivity.
 template <bool kConn8>
 __device__ __forceinline__ uint32_t touch_range(uint32_t rm) {
     return kConn8 ? (rm | (rm << 1) | (rm >> 1)) : rm;
 }
 
+// Last column of the piece (run of `ends`' mask) holding column u.
+__device__ __forceinline__ int piece_end(uint32_t ends, int u) { return u + lobit(ends >> u); }
+
 // ---------------------------------------------------------------------------
 // Shared-memory label-equivalence lists of one block.
 
 // (masked on both fields, so no entry value can address outside the table)
-template <class G>
+template <class G, int kCap>
 __device__ __forceinline__ int par_index(int id) {
-    return (id & (kLabCap - 1)) * G::kThreads + ((id >> 7) & (G::kThreads - 1));
-}
-
-// Block raster key (row * block width + column) of a root, from its id and entry.
-template <class G>
-__device__ __forceinline__ int root_key(int id, uint16_t entry) {
-    const int t = id >> 7;
-    const int node = entry & 0xFF;
-    return ((kLH * (t >> G::kBLXLog2) + (node >> 5)) << G::kBWLog2) + kLW * (t & (G::BLX - 1)) + (node & 31);
+    return (id & (kCap - 1)) * G::kThreads + ((id >> 7) & (G::kThreads - 1));
 }
 
 // Root of id and the root's entry.  Path halving rewrites only non-root
 // entries, and links are only ever made on roots (by CAS), so the two never
 // overwrite each other.
-template <class G>
+template <class G, int kCap>
 __device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t &rentry, int cap, int &err) {
     for (int i = 0; i < cap; ++i) {
-        const uint16_t e = par[par_index<G>(x)];
+        const uint16_t e = par[par_index<G, kCap>(x)];
         if (e & kRoot) { rentry = e; return x; }
-        const uint16_t g = par[par_index<G>(e)];
+        const uint16_t g = par[par_index<G, kCap>(e)];
         if (g & kRoot) { rentry = g; return e; }
-        par[par_index<G>(x)] = g;
+        par[par_index<G, kCap>(x)] = g;
         x = g;
     }
     err |= kErrLocalCap;
@@ -144,10 +152,10 @@ __device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t
 // by threads that then store the root into entries.  (A halving find there
 // could store an older grandparent over an entry that another thread had
 // already set to its root.)
-template <class G>
+template <class G, int kCap>
 __device__ __forceinline__ int find_root_ro(const volatile uint16_t *par, int x, int cap, int &err) {
     for (int i = 0; i < cap; ++i) {
-        const uint16_t e = par[par_index<G>(x)];
+        const uint16_t e = par[par_index<G, kCap>(x)];
         if (e & kRoot) return x;
         x = e;
     }
@@ -155,29 +163,41 @@ __device__ __forceinline__ int find_root_ro(const volatile uint16_t *par, int x,
     return x;
 }
 
+// Merge the lists of a and b when both belong to the calling thread's lane
+// tile and no other thread reads or writes its entries yet: plain finds and
+// a plain store, the root with the larger key hung under the other.
+template <class G, int kCap>
+__device__ __forceinline__ void union_private(uint16_t *par, int a, int b, int cap, int &err) {
+    uint16_t ea, eb;
+    a = find_root<G, kCap>(par, a, ea, cap, err);
+    b = find_root<G, kCap>(par, b, eb, cap, err);
+    if (a == b) return;
+    if ((ea & 0x7FFF) < (eb & 0x7FFF)) par[par_index<G, kCap>(b)] = (uint16_t)a;
+    else par[par_index<G, kCap>(a)] = (uint16_t)b;
+}
+
 // Merge the lists of ids a and b, called by all 32 lanes of a warp together
 // (lanes with valid == false only keep step): the root with the larger key is
-// hung under the root with the smaller key (Sec. 3.1.3 and 3.2: the larger
-// label points to the smaller).  A failed CAS means the root changed
-// meanwhile; the round repeats until no lane needs another, so the warp stays
-// converged between rounds.
-template <class G>
+// hung under the root with the smaller key.  A failed CAS means the root
+// changed meanwhile; the round repeats until no lane needs another, so the
+// warp stays converged between rounds.
+template <class G, int kCap>
 __device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int a, int b, int cap, int &err) {
     volatile uint16_t *vp = par;
     bool pend = valid;
     for (int i = 0; __any_sync(kFull, pend); ++i) {
         if (pend) {
             uint16_t ea, eb;
-            a = find_root<G>(vp, a, ea, cap, err);
-            b = find_root<G>(vp, b, eb, cap, err);
+            a = find_root<G, kCap>(vp, a, ea, cap, err);
+            b = find_root<G, kCap>(vp, b, eb, cap, err);
             if (a == b || err) {
                 pend = false;
             } else {
-                if (root_key<G>(a, ea) < root_key<G>(b, eb)) {
+                if ((ea & 0x7FFF) < (eb & 0x7FFF)) {
                     const int t = a; a = b; b = t;
                     const uint16_t u = ea; ea = eb; eb = u;
                 }
-                const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index<G>(a)),
+                const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index<G, kCap>(a)),
                                                      (unsigned short)ea, (unsigned short)b);
                 if (old == ea) pend = false;
             }
@@ -187,20 +207,6 @@ __device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int 
             break;
         }
     }
-}
-
-// After the lists of a block are final, root entries are rewritten as the
-// value every run of that list needs later: kRootBorder | slot for a root
-// that owns a block-border pixel, kRoot | block key otherwise; non-root
-// entries then take their root's value.
-template <class G>
-__device__ __forceinline__ uint16_t run_value(const volatile uint16_t *par, int id) {
-    uint16_t e = par[par_index<G>(id)];
-    if (e < kRootBorder) e = par[par_index<G>(e)];
-    // still a pointer only when an iteration cap cut the compression short
-    // (the error word is set then); decode it as block key 0, never as a slot
-    if (e < kRootBorder) return 0;
-    return (e & kRoot) ? (uint16_t)(e & 0x7FFF) : (uint16_t)(kBorderFlag | (e & 0x3FFF));
 }
 
 // ---------------------------------------------------------------------------

@@ -24,7 +24,7 @@ struct Job {
 };
 
 // Device header in front of a batch's job array.  The counters are the work
-// queues of the three kernels and must be zero when the launch starts.
+// queues of the kernels and must be zero when the launch starts.
 struct JobHeader {
     unsigned njobs;
     unsigned total;       // work items (blocks) over all jobs
@@ -76,8 +76,8 @@ ccl_status check_image_args_api(const void *img, int H, int W, size_t pitch, int
 int iteration_cap_api();
 
 // Benchmark timing of the kernels enqueued by launch_label().
-constexpr int kKindLocal = 0, kKindMerge = 1, kKindRelabel = 2;
-constexpr int kKernelKinds = 3;
+constexpr int kKindLocal = 0, kKindWrite = 1;
+constexpr int kKernelKinds = 2;
 void timing_enable(bool on);
 int timing_read(double *ms, long long *count, int n);
 const char *kernel_kind_name(int k);

@@ -1,20 +1,25 @@
-// ccl_kernels.cu -- the three steps of the block-based labeller as sm_103a
-// kernels, and the launchers that enqueue them on a stream.
+// ccl_kernels.cu -- the steps of the block-based labeller as sm_103a kernels,
+// and the launchers that enqueue them on a stream.
 //
 //   k_block_local   step 1, Kernel 1 (Sec. 3.1) on blocks of 32*BLX x 8*BLY
-//                   pixels: every thread labels its 32 x 8 lane tile by coarse
-//                   labelling (row connection by bit operations; column
-//                   connection to the first run above) and refinement (merging
-//                   the further runs above); the lane tiles of the block are
-//                   then merged along their seams.  Writes the block's row
-//                   masks, one value per run (block key of its root, or its
-//                   border slot), the border record of the block and one
-//                   global union-find entry per border component.
-//   k_block_merge   step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
-//                   pairs that straddle a block edge are examined.
+//                   pixels.  Every thread labels its 32 x 8 lane tile band by
+//                   band: coarse labelling hangs each piece under the first
+//                   piece of the band above that it touches (row connection
+//                   is free inside a piece; column connection by bit
+//                   operations), refinement merges the further pieces above
+//                   that it touches; the lane tiles of the block are then
+//                   merged along their seams.  Writes the row masks, one
+//                   value per piece (block key of its root, or its border
+//                   slot), the border record of the block and one global
+//                   union-find entry per border component.
+//                   Then step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
+//                   pairs that straddle a block edge are examined.  Each pair
+//                   of neighbouring blocks is merged by whichever of the two
+//                   finishes step 1 second (an arrival counter per pair tells
+//                   it), so no CTA waits for another.
 //   k_block_write   step 3 (Sec. 3.3): root-find for the block's border slots
-//                   in the merged union-find, then expands the per-run values
-//                   over the row masks and writes every label once.
+//                   in the merged union-find, then expands the per-piece
+//                   values over the row masks and writes every label once.
 //
 // Work items are blocks.  A single image launches one CTA per block; a batch
 // of images launches persistent CTAs that take blocks from a device counter
@@ -22,8 +27,8 @@
 // consecutive items, in raster order).
 //
 // HBM traffic per pixel: 1 B image read, 4 B label write, plus the row masks
-// (1/8 B written, 1/8 B read) and the per-run values (1 B label and 2 B value
-// per run, written and read once), most of which stay in L2.
+// (1/8 B written, 1/8 B read) and 2 B per piece written and read once, most
+// of which stay in L2.
 #include <algorithm>
 #include <cstdint>
 #include <deque>
@@ -43,11 +48,11 @@ __device__ int g_device_error = 0;
 // for capacity, only the used parts are touched.
 struct Scratch {
     uint32_t *masks;   // [blocks][threads][8 rows]
-    uint32_t *lstream; // [blocks][kLWords][threads]: run labels, 4 per word
-    uint4 *vstream;    // [blocks][kVChunks][threads]: run values, 8 per chunk
+    uint4 *vstream;    // [blocks][kVChunksMax][threads]: piece values, 8 per chunk
     uint16_t *edges;   // [blocks][edge entries]
     uint64_t *P;       // [blocks][slots]
     int32_t *nslots;   // [blocks]
+    uint32_t *arrive;  // [blocks][4]: arrivals at the block's left, up, up-left, up-right pairs
 };
 
 __device__ __forceinline__ void report(int err) {
@@ -93,32 +98,89 @@ __device__ __forceinline__ bool claim_item(const JobTable &jt, int which, unsign
 }
 
 // ---------------------------------------------------------------------------
+// Shared memory of step 2 on one pair of neighbouring blocks: a union-find
+// over the border slots of both blocks (owner's slots first), which keeps
+// only the pixel pairs that join two different slot sets; those few go to
+// the global union-find.
 template <class G>
-struct LocalSmem {
-    uint16_t par[kLabCap * G::kThreads];           // list entries, see ccl_block.cuh
-    uint8_t lab[3][kLW][G::kLabPitch];             // run-start labels: row 0, then two alternating rows
-    uint8_t lcol[kLH][G::kLabPitch];               // label of the run holding column 0, per row
-    uint8_t rcol[kLH][G::kLabPitch];               // label of the run holding column 31, per row
-    uint32_t mask[kLH][G::kThreads];               // row masks
-    union {
-        uint16_t qpair[16][G::kThreads];           // further contacts of the current row (scan)
-        struct {
-            uint32_t border[kLabCap * G::kThreads / 32];  // bit per id: root touching the block border
-            uint32_t prefix[kLabCap * G::kThreads / 32];
-        };
-    };
-    uint32_t warp_tot[G::kThreads / 32];
-    int nslots;
-    int err;
-    ItemSlot item;
+struct MergeSmem {
+    uint16_t lp[2 * G::kSlots];    // parent (a smaller node) or itself
+    uint32_t edge[2 * G::kSlots];  // joining pairs: (owner slot << 16) | partner slot
+    int nedge;
 };
 
-__device__ __forceinline__ int lab_buf(int r) { return r == 0 ? 0 : 1 + ((r - 1) & 1); }
+// Local root of node x with path halving (stores only ancestors, which a
+// concurrent CAS link on a root cannot lose).
+__device__ __forceinline__ int local_find(volatile uint16_t *lp, int x, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        const int p = lp[x];
+        if (p == x) return x;
+        const int g = lp[p];
+        if (g == p) return p;
+        lp[x] = (uint16_t)g;
+        x = g;
+    }
+    err |= kErrGlobalCap;
+    return x;
+}
 
-// Border record entry of a run value: its slot, or background when the value
+// Joins the sets of nodes a and b; true when this call linked two different
+// sets (the larger root hung under the smaller).
+__device__ __forceinline__ bool local_union(uint16_t *lp, int a, int b, int cap, int &err) {
+    volatile uint16_t *vp = lp;
+    for (int i = 0; i < cap; ++i) {
+        a = local_find(vp, a, cap, err);
+        b = local_find(vp, b, cap, err);
+        if (a == b || err) return false;
+        if (a < b) { const int t = a; a = b; b = t; }
+        if (atomicCAS(reinterpret_cast<unsigned short *>(lp + a), (unsigned short)a, (unsigned short)b) ==
+            (unsigned short)a)
+            return true;
+    }
+    err |= kErrGlobalCap;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+template <class G, bool kConn8>
+struct LocalSmem {
+    static constexpr int kCap = Bands<kConn8>::kCap;
+    static constexpr int kWords = kCap * G::kThreads / 32;  // bitmap words over all entries
+    union {
+        uint16_t par[kCap * G::kThreads];  // list entries, see ccl_block.cuh
+        MergeSmem<G> merge;                // step 2, once the lists are done with
+    };
+    uint32_t mask[kLH][G::kThreads];   // row masks
+    uint32_t border[kWords];           // bit per entry: root owning a block-border pixel
+    uint32_t prefix[kWords];           // border roots in the words before
+    uint32_t warp_tot[G::kThreads / 32];
+    uint8_t lastbase[G::kThreads];     // first piece of each lane tile's last band
+    int nslots;
+    int err;
+    int merges;                        // neighbour pairs this CTA merges, bit per pair
+    ItemSlot item;
+    static_assert(sizeof(MergeSmem<G>) <= sizeof(uint16_t) * kCap * G::kThreads,
+                  "step 2 reuses the list entries' space");
+};
+
+// Border record entry of a piece value: its slot, or background when the value
 // is not a border slot (only possible after an iteration cap was hit).
 __device__ __forceinline__ uint16_t border_slot(uint16_t v) {
-    return (v & kBorderFlag) ? (uint16_t)(v & 0x3FFF) : kBg;
+    return (v & kBorderFlag) ? (uint16_t)(v & 0x7FFF) : kBg;
+}
+
+// Block raster key of the smallest pixel of a piece: its first pixel in the
+// band's top row, else (8-connectivity, the piece has pixels in the lower row
+// only, where it is a row run) its first column in the lower row.
+template <class G, bool kConn8>
+__device__ __forceinline__ int piece_key(int tx, int ty, int k, uint32_t A, uint32_t rb, int a0) {
+    int row = k, col = a0;
+    if (kConn8) {
+        const uint32_t top = A & rb;
+        row = 2 * k + (top ? 0 : 1);
+        col = top ? lobit(top) : a0;
+    }
+    return ((kLH * ty + row) << G::kBWLog2) + kLW * tx + col;
 }
 
 // 8 two-byte values collected low half first in a 128-bit shift register.
@@ -133,12 +195,124 @@ struct HalfQueue {
     __device__ __forceinline__ uint4 bits() const { return make_uint4(q0, q1, q2, q3); }
 };
 
+// ---------------------------------------------------------------------------
+// Step 2 on one pair of neighbouring blocks: `owner` and the block left of it
+// (kind 0), above it (1), above-left (2) or above-right (3).  The pairs across
+// the owner's top edge, left edge or corner are examined; a pair that repeats
+// the pair of the neighbouring pixel is skipped, and of the rest only those
+// that join two slot sets of the local union-find reach the global one.  The
+// partner's records were written by another CTA, so they are read with
+// volatile loads.  Called by the whole CTA (barriers inside).
+template <class G, bool kConn8>
+__device__ void merge_pair(const Scratch &s, MergeSmem<G> &ms, unsigned owner, int kind, int nbx, int lcap,
+                           int gcap, int &err, uint32_t bound) {
+    const unsigned partner = kind == 0 ? owner - 1u
+                           : kind == 1 ? owner - (unsigned)nbx
+                           : kind == 2 ? owner - (unsigned)nbx - 1u
+                                       : owner - (unsigned)nbx + 1u;
+    const volatile uint16_t *E = s.edges + (size_t)owner * G::kEdge;
+    const volatile uint16_t *F = s.edges + (size_t)partner * G::kEdge;
+    const volatile int32_t *vn = s.nslots;
+    const int nso = vn[owner], nsp = vn[partner];
+    const uint32_t obase = owner * (uint32_t)G::kSlots, pbase = partner * (uint32_t)G::kSlots;
+    const auto ok_o = [&](uint16_t v) { return v != kBg && (int)v < nso; };
+    const auto ok_p = [&](uint16_t v) { return v != kBg && (int)v < nsp; };
+    const int t = threadIdx.x;
+    if (kind >= 2) {
+        // the corner pixel pair of two diagonal neighbours (8-connectivity)
+        if (t == 0) {
+            const uint16_t a = E[G::kEdgeTop + (kind == 2 ? 0 : G::kBW - 1)];
+            const uint16_t c = F[G::kEdgeBottom + (kind == 2 ? G::kBW - 1 : 0)];
+            if (ok_o(a) && ok_p(c)) union_global(s.P, obase + a, pbase + c, gcap, err, bound);
+        }
+        return;
+    }
+    const int nn = nso + nsp;
+    for (int i = t; i < nn; i += G::kThreads) ms.lp[i] = (uint16_t)i;
+    if (t == 0) ms.nedge = 0;
+    __syncthreads();
+    const auto link = [&](uint16_t a, uint16_t c) {
+        if (local_union(ms.lp, a, nso + c, lcap, err)) {
+            const int k = atomicAdd(&ms.nedge, 1);
+            if (k < 2 * G::kSlots) ms.edge[k] = ((uint32_t)a << 16) | c;
+        }
+    };
+    if (kind == 1) {
+        for (int j = t; j < G::kBW; j += G::kThreads) {
+            const uint16_t a = E[G::kEdgeTop + j];
+            if (!ok_o(a)) continue;
+            const uint16_t aL = j > 0 ? E[G::kEdgeTop + j - 1] : kBg;
+            const uint16_t aR = j + 1 < G::kBW ? E[G::kEdgeTop + j + 1] : kBg;
+            const uint16_t c = F[G::kEdgeBottom + j];
+            const uint16_t cL = j > 0 ? F[G::kEdgeBottom + j - 1] : kBg;
+            if (ok_p(c) && !(aL == a && cL == c)) link(a, c);
+            if (kConn8) {
+                if (j > 0 && ok_p(cL) && aL != a) link(a, cL);
+                if (j + 1 < G::kBW) {
+                    const uint16_t cR = F[G::kEdgeBottom + j + 1];
+                    if (ok_p(cR) && aR != a) link(a, cR);
+                }
+            }
+        }
+    } else {
+        for (int j = t; j < G::kBH; j += G::kThreads) {
+            const uint16_t a = E[G::kEdgeLeft + j];
+            if (!ok_o(a)) continue;
+            const uint16_t aU = j > 0 ? E[G::kEdgeLeft + j - 1] : kBg;
+            const uint16_t aD = j + 1 < G::kBH ? E[G::kEdgeLeft + j + 1] : kBg;
+            const uint16_t c = F[G::kEdgeRight + j];
+            const uint16_t cU = j > 0 ? F[G::kEdgeRight + j - 1] : kBg;
+            if (ok_p(c) && !(aU == a && cU == c)) link(a, c);
+            if (kConn8) {
+                if (j > 0 && ok_p(cU) && aU != a) link(a, cU);
+                if (j + 1 < G::kBH) {
+                    const uint16_t cD = F[G::kEdgeRight + j + 1];
+                    if (ok_p(cD) && aD != a) link(a, cD);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int ne = ms.nedge < 2 * G::kSlots ? ms.nedge : 2 * G::kSlots;
+    for (int i = t; i < ne; i += G::kThreads) {
+        const uint32_t e = ms.edge[i];
+        union_global(s.P, obase + (e >> 16), pbase + (e & 0xFFFFu), gcap, err, bound);
+    }
+    __syncthreads();
+}
+
+// The pair that arrival r of block b (bx, by) belongs to: r < 4 are b's own
+// pairs (left, up, up-left, up-right), r >= 4 the pairs of the blocks right,
+// below, below-right and below-left of b, where b is the partner.
+template <bool kConn8>
+__device__ __forceinline__ bool arrival_pair(int r, unsigned b, int bx, int by, int nbx, int nby, unsigned &owner,
+                                             int &kind) {
+    kind = r & 3;
+    switch (r) {
+        case 0: owner = b; return bx > 0;
+        case 1: owner = b; return by > 0;
+        case 2: owner = b; return kConn8 && bx > 0 && by > 0;
+        case 3: owner = b; return kConn8 && bx + 1 < nbx && by > 0;
+        case 4: owner = b + 1u; return bx + 1 < nbx;
+        case 5: owner = b + (unsigned)nbx; return by + 1 < nby;
+        case 6: owner = b + (unsigned)nbx + 1u; return kConn8 && bx + 1 < nbx && by + 1 < nby;
+        default: owner = b + (unsigned)nbx - 1u; return kConn8 && bx > 0 && by + 1 < nby;
+    }
+}
+
 template <class G, bool kConn8>
 __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
-                                              LocalSmem<G> &sm, int cap) {
+                                              LocalSmem<G, kConn8> &sm, int cap, int gcap, uint32_t bound) {
+    using Bd = Bands<kConn8>;
+    constexpr int kCap = Bd::kCap;
+    constexpr int R = Bd::kRows;
+    constexpr int NB = Bd::kN;
+    constexpr int T = G::kThreads;
+    constexpr int kWPT = kCap / 32;  // bitmap words per thread
 
     const unsigned b = gb;
-    const int bx = (int)(lb % (unsigned)job.nbx), by = (int)(lb / (unsigned)job.nbx);
+    const int nbx = job.nbx, nby = job.nby;
+    const int bx = (int)(lb % (unsigned)nbx), by = (int)(lb / (unsigned)nbx);
     const int H = job.H, W = job.W;
     const uint8_t *const img = job.img;
     const size_t pitch = (size_t)job.pitch;
@@ -149,8 +323,11 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
     int err = 0;
 
-    if (t == 0) sm.err = 0;
-    __syncthreads();
+    if (t == 0) {
+        sm.err = 0;
+        sm.merges = 0;
+    }
+    for (int i = t; i < LocalSmem<G, kConn8>::kWords; i += T) sm.border[i] = 0u;
 
     // -- initialization: the lane tile's 8 rows as masks (all loads in flight
     // at once; pixels outside the image are background)
@@ -181,246 +358,185 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 #pragma unroll
     for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
 
-    // -- coarse labelling and refinement, row by row.  Every loop below runs
-    // the same number of rounds on all 32 lanes of a warp (the maximum any
-    // lane needs), so the 32 lane tiles advance in lockstep.
-    //
-    // Coarse labelling: a run with foreground above takes the label value of
-    // the first run above it (row connection by bit operations, column
-    // connection to that run); labels therefore travel down unchanged and
-    // no list is walked here.  A run without foreground above opens a new
-    // list.  Refinement: every further run above that a run touches is
-    // queued and the queued pairs of the row are merged after the row, the
-    // larger root hung under the smaller.
-    volatile uint16_t *vpar = sm.par;
-    uint32_t prevM = 0, prevS = 0;
-    int nlab = 0, nrun = 0;
-    uint32_t lacc = 0;                              // 4 run labels, first in the low byte
-    uint32_t *lout = s.lstream + (size_t)b * kLWords * G::kThreads + t;
-#pragma unroll 1
-    for (int r = 0; r < kLH; ++r) {
-        const uint32_t m = sm.mask[r][t];
-        uint32_t S = m & ~(m << 1);                 // run starts
-        uint32_t E = m & ~(m >> 1);                 // run ends
-        uint8_t *cur = &sm.lab[lab_buf(r)][0][t];
-        const uint8_t *prev = &sm.lab[lab_buf(r > 0 ? r - 1 : 0)][0][t];
-        int nq = 0;
-        const int nmax = __reduce_max_sync(kFull, __popc(S));
-        for (int k = 0; k < nmax; ++k) {
-            const bool act = S != 0u;
-            // an exhausted lane sees a dummy run at bit 31 and stores nothing
-            const int a0 = lobit(S | 0x80000000u);
-            const int a1 = lobit(E | 0x80000000u);
-            S &= S - 1u;
-            E &= E - 1u;
-            const uint32_t P = prevM & touch_range<kConn8>(run_bits(a0, a1)) & (0u - (uint32_t)act);
-            const int u0 = P ? lobit(P) : 0;
-            int L = nlab;
-            if (P) L = prev[hibit(prevS & upto(u0)) * G::kLabPitch];
-            else if (act) {
-                vpar[nlab * G::kThreads + t] = (uint16_t)(kRoot | (r * kLW + a0));
-                ++nlab;
-            }
-            uint32_t Q = P ? (prevS & P & ~upto(u0)) : 0u;
-            while (__any_sync(kFull, Q != 0u)) {
-                if (Q) {
-                    sm.qpair[nq][t] = (uint16_t)(L | (prev[lobit(Q) * G::kLabPitch] << 8));
-                    ++nq;
-                    Q &= Q - 1u;
-                }
-            }
-            if (act) {
-                cur[a0 * G::kLabPitch] = (uint8_t)L;
-                lacc = (lacc >> 8) | ((uint32_t)L << 24);
-                ++nrun;
-                if ((nrun & 3) == 0) lout[(size_t)((nrun >> 2) - 1) * G::kThreads] = lacc;
-            }
-        }
-        sm.lcol[r][t] = (m & 1u) ? cur[0] : (uint8_t)0xFF;
-        sm.rcol[r][t] = (m >> 31) ? cur[hibit(m & ~(m << 1)) * G::kLabPitch] : (uint8_t)0xFF;
-        prevM = m;
-        prevS = m & ~(m << 1);
-        // refinement of the row: merge the queued pairs (own lists only)
-        const int nqmax = __reduce_max_sync(kFull, nq);
-        for (int j = 0; j < nqmax; ++j) {
-            const bool hq = j < nq;
-            const uint16_t pr = hq ? sm.qpair[j][t] : (uint16_t)0;
-            int A = pr & 0xFF, B = pr >> 8;
-            bool pa = hq, pb = hq;
-            for (int i = 0; __any_sync(kFull, pa || pb); ++i) {
-                // root-finds with path halving (own lists, no other writer)
-                if (pa) {
-                    const uint16_t e = vpar[A * G::kThreads + t];
-                    if (e & kRoot) {
-                        pa = false;
-                    } else {
-                        const int p = e & (kLabCap - 1);
-                        const uint16_t g = vpar[p * G::kThreads + t];
-                        if (g & kRoot) { A = p; pa = false; }
-                        else { vpar[A * G::kThreads + t] = g; A = g & (kLabCap - 1); }
+    // -- coarse labelling and refinement, band by band, on the thread's own
+    // entries only.  A piece touching the band above takes the first piece it
+    // touches there as parent (a root of its own otherwise, keyed by its
+    // smallest pixel); every further piece it touches is merged with it.
+    uint16_t *const par = sm.par;
+    int base_prev = 0, npieces = 0;
+    {
+        uint32_t pB = 0u, pS = 0u, pE = 0u;  // band above: lower row, piece starts, piece ends
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1];
+            const uint32_t OR = A | Bm;
+            const uint32_t S0 = OR & ~(OR << 1), E0 = OR & ~(OR >> 1);
+            uint32_t S = S0, E = E0;
+            int loc = npieces;
+            while (S) {
+                const int a0 = lobit(S), a1 = lobit(E);
+                S &= S - 1u;
+                E &= E - 1u;
+                const uint32_t rb = run_bits(a0, a1);
+                const uint32_t P = pB & touch_range<kConn8>(A & rb);
+                if (P) {
+                    // parent: the root the first touched piece above had when
+                    // it was placed (its entry holds that root's id)
+                    const int u0 = lobit(P);
+                    const int up = base_prev + __popc(pS & upto(u0)) - 1;
+                    const uint16_t ue = par[up * T + t];
+                    par[loc * T + t] = (ue & kRoot) ? (uint16_t)((t << 7) | up) : ue;
+                    uint32_t P2 = P & ~upto(piece_end(pE, u0));
+                    while (P2) {
+                        const int u = lobit(P2);
+                        union_private<G, kCap>(par, (t << 7) | loc, (t << 7) | (base_prev + __popc(pS & upto(u)) - 1),
+                                               cap, err);
+                        P2 &= ~upto(piece_end(pE, u));
                     }
+                } else {
+                    par[loc * T + t] = (uint16_t)(kRoot | piece_key<G, kConn8>(tx, ty, k, A, rb, a0));
                 }
-                if (pb) {
-                    const uint16_t e = vpar[B * G::kThreads + t];
-                    if (e & kRoot) {
-                        pb = false;
-                    } else {
-                        const int p = e & (kLabCap - 1);
-                        const uint16_t g = vpar[p * G::kThreads + t];
-                        if (g & kRoot) { B = p; pb = false; }
-                        else { vpar[B * G::kThreads + t] = g; B = g & (kLabCap - 1); }
-                    }
-                }
-                if (i >= cap) {
-                    if (pa || pb) err |= kErrLocalCap;
-                    break;
-                }
+                ++loc;
             }
-            if (hq && A != B) {
-                const int lo = A < B ? A : B, hi = A < B ? B : A;
-                vpar[hi * G::kThreads + t] = (uint16_t)lo;
-            }
-        }
-        __syncwarp();
-    }
-    if (nrun & 3) lout[(size_t)(nrun >> 2) * G::kThreads] = lacc >> (8 * (4 - (nrun & 3)));
-    // compress the own lists (labels are still lane-local here, so no other
-    // lane reads them) and turn parent links into block-wide ids: the thread
-    // index joins the label
-    const int nlab_max = __reduce_max_sync(kFull, nlab);
-    for (int L = 0; L < nlab_max; ++L) {
-        if (L < nlab) {
-            // entries already converted by earlier rounds carry this thread's
-            // index in their high bits; the low bits are the lane-local label
-            int x = L;
-            uint16_t e = vpar[x * G::kThreads + t];
-            for (int i = 0; !(e & kRoot) && i < cap; ++i) {
-                x = e & (kLabCap - 1);
-                e = vpar[x * G::kThreads + t];
-            }
-            if (x != L) vpar[L * G::kThreads + t] = (uint16_t)((t << 7) | x);
+            base_prev = npieces;
+            npieces = loc;
+            pB = Bm;
+            pS = S0;
+            pE = E0;
         }
     }
+    sm.lastbase[t] = (uint8_t)base_prev;
     __syncthreads();
-
-    // the refinement queue is dead now; its space holds the border bitmap
-    for (int i = t; i < kLabCap * G::kThreads / 32; i += G::kThreads) sm.border[i] = 0u;
 
     // -- block merge of the lane tiles along their seams (Kernel 2's boundary
     // analysis applied inside the block, on the shared lists)
-    const uint32_t m0 = mrow[0];
+    const auto seam = [&](bool valid, int a, int b) { union_block_sync<G, kCap>(par, valid, a, b, cap, err); };
     {
         const bool hasl = tx > 0;
         const int tl = hasl ? t - 1 : t;
+        int mb = 0, lbase = 0;
 #pragma unroll
-        for (int r = 0; r < kLH; ++r) {
-            const bool me_fg = hasl && (mrow[r] & 1u);
-            const int me = (t << 7) | sm.lcol[r][t];
-            // a pair repeating the row above's pair (both columns continue
-            // vertically) adds nothing
-            const bool up_me = r > 0 && (mrow[r > 0 ? r - 1 : 0] & 1u);
-            const bool dn_me = r + 1 < kLH && (mrow[r + 1 < kLH ? r + 1 : r] & 1u);
-            const bool up_l = r > 0 && (sm.mask[r > 0 ? r - 1 : 0][tl] >> 31);
-            const bool dn_l = r + 1 < kLH && (sm.mask[r + 1 < kLH ? r + 1 : r][tl] >> 31);
-            const bool at_l = sm.mask[r][tl] >> 31;
-            union_block_sync<G>(sm.par, me_fg && at_l && !(up_me && up_l), me, (tl << 7) | sm.rcol[r][tl], cap, err);
-            if (kConn8) {
-                union_block_sync<G>(sm.par, me_fg && up_l && !up_me, me,
-                                 (tl << 7) | sm.rcol[r > 0 ? r - 1 : 0][tl], cap, err);
-                union_block_sync<G>(sm.par, me_fg && dn_l && !dn_me, me,
-                                 (tl << 7) | sm.rcol[r + 1 < kLH ? r + 1 : r][tl], cap, err);
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1], OR = A | Bm;
+            const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl], lOR = lA | lB;
+            const int np = __popc(OR & ~(OR << 1));
+            const int lnp = __popc(lOR & ~(lOR << 1));
+            const int me_first = (t << 7) | mb;
+            const int l_last = (tl << 7) | (lbase + lnp - 1);
+            seam(hasl && (OR & 1u) && (lOR >> 31), me_first, l_last);
+            if (kConn8 && k + 1 < NB) {
+                const uint32_t nA = mrow[(k + 1) * R];
+                const uint32_t lnA = sm.mask[(k + 1) * R][tl];
+                const uint32_t lnOR = lnA | sm.mask[(k + 1) * R + R - 1][tl];
+                const int l_next_last = (tl << 7) | (lbase + lnp + __popc(lnOR & ~(lnOR << 1)) - 1);
+                // lower row of my band k, column 0 ~ upper row of the left band k+1, column 31
+                seam(hasl && (Bm & 1u) && (lnA >> 31), me_first, l_next_last);
+                // upper row of my band k+1, column 0 ~ lower row of the left band k, column 31
+                seam(hasl && (nA & 1u) && (lB >> 31), (t << 7) | (mb + np), l_last);
             }
+            mb += np;
+            lbase += lnp;
         }
     }
+    const uint32_t A0 = mrow[0], OR0 = A0 | mrow[R - 1];
+    const uint32_t S00 = OR0 & ~(OR0 << 1), E00 = OR0 & ~(OR0 >> 1);
     {
         const bool hasu = ty > 0;
         const int tu = hasu ? t - G::BLX : t;
-        const uint32_t mU = hasu ? sm.mask[kLH - 1][tu] : 0u;
-        const uint32_t SU = mU & ~(mU << 1);
-        const uint8_t *top = &sm.lab[0][0][t];
-        const uint8_t *bot = &sm.lab[lab_buf(kLH - 1)][0][tu];
-        uint32_t S = hasu ? (m0 & ~(m0 << 1)) : 0u;
-        uint32_t E = m0 & ~(m0 >> 1);
+        const uint32_t uB = sm.mask[kLH - 1][tu], uOR = sm.mask[kLH - R][tu] | uB;
+        const uint32_t uS = uOR & ~(uOR << 1), uE = uOR & ~(uOR >> 1);
+        const int ubase = sm.lastbase[tu];
+        uint32_t S = hasu ? S00 : 0u;
+        uint32_t E = hasu ? E00 : 0u;
         const int nmax = __reduce_max_sync(kFull, __popc(S));
-        for (int k = 0; k < nmax; ++k) {
+        for (int i = 0; i < nmax; ++i) {
             const bool act = S != 0u;
-            const int a0 = act ? lobit(S) : 0;
-            const int a1 = act ? lobit(E) : 0;
+            const int a0 = act ? lobit(S) : 0, a1 = act ? lobit(E) : 0;
             S &= S - 1u;
             E &= E - 1u;
-            const uint32_t P = act ? (mU & touch_range<kConn8>(run_bits(a0, a1))) : 0u;
-            const int me = (t << 7) | top[a0 * G::kLabPitch];
-            const int u0 = P ? lobit(P) : 0;
-            union_block_sync<G>(sm.par, P != 0u, me, (tu << 7) | bot[hibit((SU & upto(u0)) | 1u) * G::kLabPitch], cap,
-                             err);
-            uint32_t Q = P ? (SU & P & ~upto(u0)) : 0u;
-            while (__any_sync(kFull, Q != 0u)) {
-                const bool hq = Q != 0u;
-                const int q = hq ? lobit(Q) : 0;
-                Q &= Q - 1u;
-                union_block_sync<G>(sm.par, hq, me, (tu << 7) | bot[q * G::kLabPitch], cap, err);
+            uint32_t P = act ? (uB & touch_range<kConn8>(A0 & run_bits(a0, a1))) : 0u;
+            const int me = (t << 7) | i;
+            while (__any_sync(kFull, P != 0u)) {
+                const bool hp = P != 0u;
+                const int u = hp ? lobit(P) : 0;
+                seam(hp, me, (tu << 7) | (ubase + __popc(uS & upto(u)) - 1));
+                if (hp) P &= ~upto(piece_end(uE, u));
             }
         }
         if (kConn8) {
             // corners: the lane tiles up-left and up-right
-            const bool ul = hasu && tx > 0 && (m0 & 1u);
+            const bool ul = hasu && tx > 0 && (A0 & 1u);
             const int tul = ul ? tu - 1 : t;
-            const uint32_t mUL = ul ? sm.mask[kLH - 1][tul] : 0u;
-            const uint32_t SUL = mUL & ~(mUL << 1);
-            union_block_sync<G>(sm.par, ul && (mUL >> 31), (t << 7) | top[0],
-                             (tul << 7) | sm.lab[lab_buf(kLH - 1)][hibit(SUL | 1u)][tul], cap, err);
-            const bool ur = hasu && tx + 1 < G::BLX && (m0 >> 31);
+            const uint32_t ulB = sm.mask[kLH - 1][tul];
+            const uint32_t ulOR = sm.mask[kLH - 2][tul] | ulB;
+            seam(ul && (ulB >> 31), t << 7, (tul << 7) | (sm.lastbase[tul] + __popc(ulOR & ~(ulOR << 1)) - 1));
+            const bool ur = hasu && tx + 1 < G::BLX && (A0 >> 31);
             const int tur = ur ? tu + 1 : t;
-            const uint32_t S0 = m0 & ~(m0 << 1);
-            union_block_sync<G>(sm.par, ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | top[hibit(S0 | 1u) * G::kLabPitch],
-                             (tur << 7) | sm.lab[lab_buf(kLH - 1)][0][tur], cap, err);
+            seam(ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | (__popc(S00) - 1), (tur << 7) | sm.lastbase[tur]);
         }
     }
     __syncthreads();
 
-    // -- compress: every own list entry points straight at its root (the
-    // finds only read, so every store here is a final root)
-    for (int L = 0; L < nlab_max; ++L) {
-        if (L < nlab) {
-            const int id = (t << 7) | L;
-            const int root = find_root_ro<G>(vpar, id, cap, err);
-            if (root != id) vpar[L * G::kThreads + t] = (uint16_t)root;
-        }
+    // -- compress: every own entry points straight at its root (the finds
+    // only read, so every store here is a final root)
+    volatile uint16_t *const vpar = sm.par;
+    for (int loc = 0; loc < npieces; ++loc) {
+        const int id = (t << 7) | loc;
+        const int root = find_root_ro<G, kCap>(vpar, id, cap, err);
+        if (root != id) vpar[loc * T + t] = (uint16_t)root;
     }
     __syncthreads();
 
     // -- roots that own a pixel of the block border
-    auto root_of = [&](int id) -> int {
-        const uint16_t e = vpar[par_index<G>(id)];
+    const auto root_of = [&](int id) -> int {
+        const uint16_t e = vpar[par_index<G, kCap>(id)];
         return (e & kRoot) ? id : (int)e;
     };
-    auto mark = [&](int id) {
-        const int root = root_of(id);
-        atomicOr(&sm.border[root >> 5], 1u << (root & 31));
+    const auto mark = [&](int id) {
+        const int bit = par_index<G, kCap>(root_of(id));
+        atomicOr(&sm.border[bit >> 5], 1u << (bit & 31));
     };
-    if (ty == 0)
-        for (uint32_t S = m0 & ~(m0 << 1); S; S &= S - 1) mark((t << 7) | sm.lab[0][lobit(S)][t]);
+    const uint32_t AL = mrow[kLH - R], BL = mrow[kLH - 1], ORL = AL | BL;
+    const uint32_t SL = ORL & ~(ORL << 1), EL = ORL & ~(ORL >> 1);
+    if (ty == 0) {
+        uint32_t S = S00, E = E00;
+        for (int i = 0; S; ++i) {
+            const int a0 = lobit(S), a1 = lobit(E);
+            S &= S - 1u;
+            E &= E - 1u;
+            if (A0 & run_bits(a0, a1)) mark((t << 7) | i);
+        }
+    }
     if (ty == G::BLY - 1) {
-        const uint32_t m7 = mrow[kLH - 1];
-        for (uint32_t S = m7 & ~(m7 << 1); S; S &= S - 1)
-            mark((t << 7) | sm.lab[lab_buf(kLH - 1)][lobit(S)][t]);
+        uint32_t S = SL, E = EL;
+        for (int i = base_prev; S; ++i) {
+            const int a0 = lobit(S), a1 = lobit(E);
+            S &= S - 1u;
+            E &= E - 1u;
+            if (BL & run_bits(a0, a1)) mark((t << 7) | i);
+        }
     }
-    if (tx == 0) {
+    if (tx == 0 || tx == G::BLX - 1) {
+        int mb = 0;
 #pragma unroll
-        for (int r = 0; r < kLH; ++r)
-            if (mrow[r] & 1u) mark((t << 7) | sm.lcol[r][t]);
-    }
-    if (tx == G::BLX - 1) {
-#pragma unroll
-        for (int r = 0; r < kLH; ++r)
-            if (mrow[r] >> 31) mark((t << 7) | sm.rcol[r][t]);
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
+            const int np = __popc(OR & ~(OR << 1));
+            if (tx == 0 && (OR & 1u)) mark((t << 7) | mb);
+            if (tx == G::BLX - 1 && (OR >> 31)) mark((t << 7) | (mb + np - 1));
+            mb += np;
+        }
     }
     __syncthreads();
     {
-        // exclusive popcount prefix over 512 words: 4 per thread, then a scan
-        uint32_t c[4], sum = 0;
+        // exclusive popcount prefix over the bitmap: kWPT words per thread,
+        // then a scan over threads
+        uint32_t c[kWPT], sum = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { c[k] = __popc(sm.border[4 * t + k]); sum += c[k]; }
+        for (int k = 0; k < kWPT; ++k) {
+            c[k] = __popc(sm.border[kWPT * t + k]);
+            sum += c[k];
+        }
         const int lane = t & 31, w = t >> 5;
         uint32_t incl = sum;
 #pragma unroll
@@ -434,210 +550,163 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         for (int i = 0; i < w; ++i) base += sm.warp_tot[i];
         uint32_t run = base + incl - sum;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) { sm.prefix[4 * t + k] = run; run += c[k]; }
+        for (int k = 0; k < kWPT; ++k) {
+            sm.prefix[kWPT * t + k] = run;
+            run += c[k];
+        }
         // at most G::kSlots border components exist; more marks only after an
         // iteration cap was hit, and the surplus slots are dropped
-        if (t == G::kThreads - 1) {
+        if (t == T - 1) {
             sm.nslots = (int)(base + incl) < G::kSlots ? (int)(base + incl) : G::kSlots;
             if ((int)(base + incl) > G::kSlots) sm.err |= kErrLocalCap;
         }
     }
     __syncthreads();
-    auto slot_of = [&](int root) -> int {
-        return (int)(sm.prefix[root >> 5] + __popc(sm.border[root >> 5] & ((1u << (root & 31)) - 1u)));
-    };
 
     // -- one global union-find entry per border component, keyed by its
     // minimum global raster position (ID conversion, Sec. 3.1.4)
     {
-        const uint32_t sbase = (uint32_t)b * G::kSlots;
+        const uint32_t sbase = b * (uint32_t)G::kSlots;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int word = 4 * t + k;
+        for (int k = 0; k < kWPT; ++k) {
+            const int word = kWPT * t + k;
             uint32_t bits = sm.border[word];
             uint32_t slot = sm.prefix[word];
             for (; bits && slot < (uint32_t)G::kSlots; bits &= bits - 1, ++slot) {
-                const int root = word * 32 + lobit(bits);
-                const int key = root_key<G>(root, vpar[par_index<G>(root)]);
+                const int key = vpar[word * 32 + lobit(bits)] & 0x7FFF;
                 const uint32_t g = (uint32_t)(y0 + (key >> G::kBWLog2)) * (uint32_t)W +
                                    (uint32_t)(x0 + (key & (G::kBW - 1)));
                 s.P[sbase + slot] = pack_slot(g, sbase + slot);
             }
         }
     }
-    __syncthreads();
-    // -- each own root entry becomes the value its runs carry from now on
-    for (int L = 0; L < nlab_max; ++L) {
-        if (L < nlab) {
-            const int id = (t << 7) | L;
-            const uint16_t e = vpar[L * G::kThreads + t];
-            if (e & kRoot) {
-                const bool border = (sm.border[id >> 5] >> (id & 31)) & 1u;
-                vpar[L * G::kThreads + t] = border ? (uint16_t)(kRootBorder | slot_of(id))
-                                                : (uint16_t)(kRoot | root_key<G>(id, e));
-            }
-        }
-    }
-    __syncthreads();
-    // ... and so does every own non-root entry (it points straight at a root,
-    // whose value is final), making a run's value a single lookup
-    for (int L = 0; L < nlab_max; ++L) {
-        if (L < nlab) {
-            const uint16_t e = vpar[L * G::kThreads + t];
-            if (e < kRootBorder) vpar[L * G::kThreads + t] = vpar[par_index<G>(e)];
-        }
-    }
+    // value every piece carries from now on: kBorderFlag | slot of its root,
+    // or the block key of its root
+    const auto value_of = [&](int id) -> uint16_t {
+        const uint16_t e = vpar[par_index<G, kCap>(id)];
+        const int root = (e & kRoot) ? id : (int)e;
+        const uint16_t re = (e & kRoot) ? e : vpar[par_index<G, kCap>(root)];
+        // still a pointer only when an iteration cap cut the merges short
+        // (the error word is set then); decode it as block key 0
+        if (!(re & kRoot)) return 0;
+        const int bit = par_index<G, kCap>(root);
+        const uint32_t word = sm.border[bit >> 5];
+        if ((word >> (bit & 31)) & 1u)
+            return (uint16_t)(kBorderFlag | (sm.prefix[bit >> 5] + __popc(word & ((1u << (bit & 31)) - 1u))));
+        return (uint16_t)(re & 0x7FFF);
+    };
 
     // -- border record of the block: the slot of every border pixel
-    uint16_t *Eb = s.edges + (size_t)b * G::kEdge;
-    if (ty == 0 || ty == G::BLY - 1) {
-        const int rr = ty == 0 ? 0 : kLH - 1;
-        const uint32_t m = mrow[rr];
-        const uint32_t S = m & ~(m << 1);
-        const uint8_t *lb = &sm.lab[lab_buf(rr)][0][t];
-        uint16_t *dst = Eb + (ty == 0 ? G::kEdgeTop : G::kEdgeBottom) + kLW * tx;
-#pragma unroll 4
+    uint16_t *const Eb = s.edges + (size_t)b * G::kEdge;
+    const auto edge_row = [&](uint32_t S, uint32_t Mr, int first, uint16_t *dst) {
+        uint32_t wv[kLW / 2];
+        int idx = first - 1;
+        uint16_t v = kBg;
+#pragma unroll
         for (int c = 0; c < kLW; ++c) {
-            uint16_t v = kBg;
-            if ((m >> c) & 1u) v = border_slot(run_value<G>(vpar, (t << 7) | lb[hibit(S & upto(c)) * G::kLabPitch]));
-            dst[c] = v;
-        }
-    }
-    if (tx == 0 || tx == G::BLX - 1) {
-        uint16_t *dst = Eb + (tx == 0 ? G::kEdgeLeft : G::kEdgeRight) + kLH * ty;
-#pragma unroll
-        for (int r = 0; r < kLH; ++r) {
-            const bool fg = tx == 0 ? (mrow[r] & 1u) : (mrow[r] >> 31);
-            const int L = tx == 0 ? sm.lcol[r][t] : sm.rcol[r][t];
-            dst[r] = fg ? border_slot(run_value<G>(vpar, (t << 7) | L)) : kBg;
-        }
-    }
-    // -- per-run values: block key of the root, or kBorderFlag | slot
-    {
-        const uint32_t *lin = s.lstream + (size_t)b * kLWords * G::kThreads + t;
-        uint4 *vout = s.vstream + (size_t)b * kVChunks * G::kThreads + t;
-        HalfQueue vq;
-        const int nrun_max = __reduce_max_sync(kFull, nrun);
-        for (int k = 0; k < nrun_max; k += 4) {
-            const uint32_t w = k < nrun ? lin[(size_t)(k >> 2) * G::kThreads] : 0u;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                if (k + j < nrun) {
-                    vq.push(run_value<G>(vpar, (t << 7) | ((w >> (8 * j)) & 0xFF)));
-                    if (((k + j + 1) & 7) == 0) vout[(size_t)((k + j) >> 3) * G::kThreads] = vq.bits();
-                }
+            if ((S >> c) & 1u) {
+                ++idx;
+                v = border_slot(value_of((t << 7) | idx));
             }
+            const uint32_t o = ((Mr >> c) & 1u) ? v : kBg;
+            if (c & 1) wv[c >> 1] |= o << 16;
+            else wv[c >> 1] = o;
         }
-        if (nrun & 7) {
-            for (int k = nrun & 7; k < 8; ++k) vq.push(0);
-            vout[(size_t)(nrun >> 3) * G::kThreads] = vq.bits();
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+        for (int q = 0; q < kLW / 8; ++q) d4[q] = make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
+    };
+    if (ty == 0) edge_row(S00, A0, 0, Eb + G::kEdgeTop + kLW * tx);
+    if (ty == G::BLY - 1) edge_row(SL, BL, base_prev, Eb + G::kEdgeBottom + kLW * tx);
+    if (tx == 0 || tx == G::BLX - 1) {
+        uint32_t wv[kLH / 2];
+        int mb = 0;
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
+            const int np = __popc(OR & ~(OR << 1));
+            const int id = (t << 7) | (tx == 0 ? mb : mb + np - 1);
+            const bool any = tx == 0 ? (OR & 1u) : (OR >> 31);
+            const uint16_t v = any ? border_slot(value_of(id)) : kBg;
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int r = k * R + rr;
+                const bool fg = tx == 0 ? (mrow[r] & 1u) : (mrow[r] >> 31);
+                const uint32_t o = fg ? v : kBg;
+                if (r & 1) wv[r >> 1] |= o << 16;
+                else wv[r >> 1] = o;
+            }
+            mb += np;
+        }
+        *reinterpret_cast<uint4 *>(Eb + (tx == 0 ? G::kEdgeLeft : G::kEdgeRight) + kLH * ty) =
+            make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    }
+    // -- per-piece values, in piece order
+    {
+        uint4 *vout = s.vstream + (size_t)b * kVChunksMax * T + t;
+        HalfQueue vq;
+        for (int loc = 0; loc < npieces; ++loc) {
+            vq.push(value_of((t << 7) | loc));
+            if ((loc & 7) == 7) vout[(size_t)(loc >> 3) * T] = vq.bits();
+        }
+        if (npieces & 7) {
+            for (int k = npieces & 7; k < 8; ++k) vq.push(0);
+            vout[(size_t)(npieces >> 3) * T] = vq.bits();
         }
     }
     // -- row masks for the write-out pass
     {
-        uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * G::kThreads + t) * kLH);
+        uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
         mo[0] = make_uint4(mrow[0], mrow[1], mrow[2], mrow[3]);
         mo[1] = make_uint4(mrow[4], mrow[5], mrow[6], mrow[7]);
     }
     if (err) atomicOr(&sm.err, err);
     __syncthreads();
-    if (t == 0) {
-        s.nslots[b] = sm.nslots;
-        report(sm.err);
+    if (t == 0) s.nslots[b] = sm.nslots;
+    __syncthreads();
+
+    // -- step 2: announce this block to its neighbour pairs; a pair whose
+    // other block has arrived already is merged here.  (The fence orders
+    // this CTA's records before the arrival; the second arrival fences again
+    // before it reads the first one's records.)
+    if (t < 8) {
+        unsigned owner;
+        int kind;
+        if (arrival_pair<kConn8>(t, b, bx, by, nbx, nby, owner, kind)) {
+            __threadfence();
+            if (atomicAdd(&s.arrive[(size_t)owner * 4 + kind], 1u) == 1u) {
+                __threadfence();
+                atomicOr(&sm.merges, 1 << t);
+            }
+        }
     }
+    __syncthreads();
+    const int merges = sm.merges;
+    if (merges) {
+        __threadfence();
+        int gerr = 0;
+        for (int r = 0; r < 8; ++r) {
+            if (!((merges >> r) & 1)) continue;
+            unsigned owner;
+            int kind;
+            arrival_pair<kConn8>(r, b, bx, by, nbx, nby, owner, kind);
+            merge_pair<G, kConn8>(s, sm.merge, owner, kind, nbx, cap, gcap, gerr, bound);
+        }
+        if (gerr) atomicOr(&sm.err, gerr);
+    }
+    __syncthreads();
+    if (t == 0) report(sm.err);
 }
 
 template <class G, bool kConn8>
-__global__ void __launch_bounds__(G::kThreads, 4) k_block_local(JobTable jt, Scratch s, int cap) {
+__global__ void __launch_bounds__(G::kThreads) k_block_local(JobTable jt, Scratch s, int cap, int gcap,
+                                                             uint32_t bound) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LocalSmem<G> &sm = *reinterpret_cast<LocalSmem<G> *>(smem_raw);
+    LocalSmem<G, kConn8> &sm = *reinterpret_cast<LocalSmem<G, kConn8> *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 0, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
-        process_local<G, kConn8>(job, lb, gb, s, sm, cap);
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// Each block examines the pixel pairs across its top edge, its left edge and
-// (8-connectivity) its two upper corners; the right, bottom and lower corners
-// belong to the neighbouring blocks.  A pair that repeats the pair of the
-// neighbouring pixel is skipped.  One thread per top-edge column.
-template <class G, bool kConn8>
-__device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsigned gb, const Scratch &s, int cap,
-                                              uint32_t bound) {
-
-    const unsigned b = gb;
-    const int nbx = job.nbx;
-    const int bx = (int)(lb % (unsigned)nbx), by = (int)(lb / (unsigned)nbx);
-    const uint16_t *E = s.edges + (size_t)b * G::kEdge;
-    const uint32_t base = (uint32_t)b * G::kSlots;
-    int err = 0;
-    // every slot named by a border record is below its block's slot count;
-    // checking it keeps the finds inside initialised entries whatever happened
-    const auto valid = [&](unsigned blk, uint16_t v) { return v != kBg && (int)v < s.nslots[blk]; };
-
-    if (by > 0) {
-        const unsigned bu = b - (unsigned)nbx;
-        const uint16_t *Eu = s.edges + (size_t)bu * G::kEdge;
-        const uint32_t ubase = (uint32_t)bu * G::kSlots;
-        for (int j = threadIdx.x; j < G::kBW; j += G::kBW) {
-            const uint16_t a = E[G::kEdgeTop + j];
-            if (!valid(b, a)) continue;
-            const uint16_t aL = j > 0 ? E[G::kEdgeTop + j - 1] : kBg;
-            const uint16_t aR = j + 1 < G::kBW ? E[G::kEdgeTop + j + 1] : kBg;
-            const uint16_t c = Eu[G::kEdgeBottom + j];
-            const uint16_t cL = j > 0 ? Eu[G::kEdgeBottom + j - 1] : kBg;
-            if (valid(bu, c) && !(aL == a && cL == c)) union_global(s.P, base + a, ubase + c, cap, err, bound);
-            if (kConn8) {
-                if (j > 0) {
-                    if (valid(bu, cL) && aL != a) union_global(s.P, base + a, ubase + cL, cap, err, bound);
-                } else if (bx > 0) {
-                    const uint16_t d = s.edges[(size_t)(bu - 1) * G::kEdge + G::kEdgeBottom + G::kBW - 1];
-                    if (valid(bu - 1, d)) union_global(s.P, base + a, (uint32_t)(bu - 1) * G::kSlots + d, cap, err, bound);
-                }
-                if (j + 1 < G::kBW) {
-                    const uint16_t cR = Eu[G::kEdgeBottom + j + 1];
-                    if (valid(bu, cR) && aR != a) union_global(s.P, base + a, ubase + cR, cap, err, bound);
-                } else if (bx + 1 < nbx) {
-                    const uint16_t d = s.edges[(size_t)(bu + 1) * G::kEdge + G::kEdgeBottom + 0];
-                    if (valid(bu + 1, d)) union_global(s.P, base + a, (uint32_t)(bu + 1) * G::kSlots + d, cap, err, bound);
-                }
-            }
-        }
-    }
-    if (bx > 0) {
-        const unsigned bl = b - 1;
-        const uint16_t *El = s.edges + (size_t)bl * G::kEdge;
-        const uint32_t lbase = (uint32_t)bl * G::kSlots;
-        for (int j = threadIdx.x; j < G::kBH; j += G::kBW) {
-            const uint16_t a = E[G::kEdgeLeft + j];
-            if (!valid(b, a)) continue;
-            const uint16_t aU = j > 0 ? E[G::kEdgeLeft + j - 1] : kBg;
-            const uint16_t aD = j + 1 < G::kBH ? E[G::kEdgeLeft + j + 1] : kBg;
-            const uint16_t c = El[G::kEdgeRight + j];
-            const uint16_t cU = j > 0 ? El[G::kEdgeRight + j - 1] : kBg;
-            if (valid(bl, c) && !(aU == a && cU == c)) union_global(s.P, base + a, lbase + c, cap, err, bound);
-            if (kConn8) {
-                if (j > 0 && valid(bl, cU) && aU != a) union_global(s.P, base + a, lbase + cU, cap, err, bound);
-                if (j + 1 < G::kBH) {
-                    const uint16_t cD = El[G::kEdgeRight + j + 1];
-                    if (valid(bl, cD) && aD != a) union_global(s.P, base + a, lbase + cD, cap, err, bound);
-                }
-            }
-        }
-    }
-    report(err);
-}
-
-template <class G, bool kConn8>
-__global__ void __launch_bounds__(G::kBW) k_block_merge(JobTable jt, Scratch s, int cap, uint32_t bound) {
-    __shared__ ItemSlot item;
-    for (unsigned iter = 0; claim_item(jt, 1, iter, item); ++iter) {
-        const Job &job = item.job;
-        const unsigned lb = item.lb, gb = item.gb;
-        process_merge<G, kConn8>(job, lb, gb, s, cap, bound);
+        process_local<G, kConn8>(job, lb, gb, s, sm, cap, gcap, bound);
         __syncthreads();
     }
 }
@@ -646,7 +715,7 @@ __global__ void __launch_bounds__(G::kBW) k_block_merge(JobTable jt, Scratch s, 
 template <class G>
 struct WriteSmem {
     int slot_label[G::kSlots];
-    int runlab[G::BLY][G::kBW];          // label of every run at its start column, one row of all lane tiles
+    int runlab[G::BLY][G::kBW];          // label of every piece at its start column, one band of all lane tiles
     uint32_t mask[kLH][G::kThreads];     // row masks of the block
     ItemSlot item;
 };
@@ -657,9 +726,13 @@ struct WriteSmem {
 template <class G>
 __device__ __forceinline__ int runlab_index(int tx, int c) { return kLW * tx + (c ^ ((tx & 3) << 3)); }
 
-template <class G>
+template <class G, bool kConn8>
 __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
                                               WriteSmem<G> &sm, int cap, uint32_t bound) {
+    using Bd = Bands<kConn8>;
+    constexpr int R = Bd::kRows;
+    constexpr int NB = Bd::kN;
+    constexpr int T = G::kThreads;
 
     const unsigned b = gb;
     const int bx = (int)(lb % (unsigned)job.nbx), by = (int)(lb / (unsigned)job.nbx);
@@ -674,75 +747,83 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     // (read-only; every union is complete when this kernel starts)
     const int ns = s.nslots[b];
     int err = 0;
-    for (int k = t; k < ns; k += G::kThreads) {
+    for (int k = t; k < ns; k += T) {
         uint32_t key;
-        find_global_ro(s.P, (uint32_t)b * G::kSlots + (uint32_t)k, key, cap, err, bound);
+        find_global_ro(s.P, b * (uint32_t)G::kSlots + (uint32_t)k, key, cap, err, bound);
         sm.slot_label[k] = (int)key + 1;
     }
     report(err);
 
-    const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * G::kThreads + t) * kLH);
+    const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
     const uint4 mA = mi[0], mB = mi[1];
     const uint32_t mrow[kLH] = {mA.x, mA.y, mA.z, mA.w, mB.x, mB.y, mB.z, mB.w};
 #pragma unroll
     for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
-    // per-run values, 8 per chunk; the next chunk is always already in flight
-    const uint4 *vin = s.vstream + (size_t)b * kVChunks * G::kThreads + t;
-    int nrun = 0;
+    // per-piece values, 8 per chunk; the next chunk is always already in flight
+    const uint4 *vin = s.vstream + (size_t)b * kVChunksMax * T + t;
+    int npieces = 0;
 #pragma unroll
-    for (int r = 0; r < kLH; ++r) nrun += __popc(mrow[r] & ~(mrow[r] << 1));
-    const int nchunks = (nrun + 7) >> 3;
+    for (int k = 0; k < NB; ++k) {
+        const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
+        npieces += __popc(OR & ~(OR << 1));
+    }
+    const int nchunks = (npieces + 7) >> 3;
     uint4 vq = nchunks > 0 ? vin[0] : make_uint4(0, 0, 0, 0);
-    uint4 vnext = nchunks > 1 ? vin[G::kThreads] : make_uint4(0, 0, 0, 0);
+    uint4 vnext = nchunks > 1 ? vin[T] : make_uint4(0, 0, 0, 0);
     int vi = 0, vc = 2;
     __syncthreads();
 
 #pragma unroll
-    for (int r = 0; r < kLH; ++r) {
-        // each lane tile: one label per run of its row r, at the run start
-        const uint32_t m = mrow[r];
-        uint32_t S = m & ~(m << 1);
-        const int nmax = __reduce_max_sync(kFull, __popc(S));
-        for (int k = 0; k < nmax; ++k) {
-            if (S) {
-                const int a0 = lobit(S);
-                S &= S - 1u;
-                if (vi == 8) {
-                    vq = vnext;
-                    if (vc < nchunks) vnext = vin[(size_t)vc * G::kThreads];
-                    ++vc;
-                    vi = 0;
-                }
-                const uint32_t w = vi < 2 ? vq.x : vi < 4 ? vq.y : vi < 6 ? vq.z : vq.w;
-                const uint32_t v = (w >> ((vi & 1) * 16)) & 0xFFFFu;
-                ++vi;
-                const uint32_t slot = v & 0x7FFFu;
-                const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
-                                                   : (int)((uint32_t)(y0 + (int)(v >> G::kBWLog2)) * (uint32_t)W +
-                                                           (uint32_t)(x0 + (int)(v & (G::kBW - 1)))) + 1;
-                sm.runlab[ty][runlab_index<G>(tx, a0)] = lab;
+    for (int k = 0; k < NB; ++k) {
+        // each lane tile: one label per piece of its band k, at the piece start
+        const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
+        uint32_t S = OR & ~(OR << 1);
+        while (S) {
+            const int a0 = lobit(S);
+            S &= S - 1u;
+            if (vi == 8) {
+                vq = vnext;
+                if (vc < nchunks) vnext = vin[(size_t)vc * T];
+                ++vc;
+                vi = 0;
             }
+            const uint32_t w = vi < 2 ? vq.x : vi < 4 ? vq.y : vi < 6 ? vq.z : vq.w;
+            const uint32_t v = (w >> ((vi & 1) * 16)) & 0xFFFFu;
+            ++vi;
+            const uint32_t slot = v & 0x7FFFu;
+            const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
+                                               : (int)((uint32_t)(y0 + (int)(v >> G::kBWLog2)) * (uint32_t)W +
+                                                       (uint32_t)(x0 + (int)(v & (G::kBW - 1)))) + 1;
+            sm.runlab[ty][runlab_index<G>(tx, a0)] = lab;
         }
         __syncthreads();
-        // coalesced write-out of image rows y0 + 8*ry + r: every pixel takes
-        // the label stored at the start of its run; a thread covers 4 pixels
-        // per step
-        for (int i = t; i < G::BLY * (G::kBW / 4); i += G::kThreads) {
+        // coalesced write-out of the band's rows: every pixel takes the label
+        // stored at the start of its piece; a thread covers 4 columns per step
+        for (int i = t; i < G::BLY * (G::kBW / 4); i += T) {
             const int ry = i / (G::kBW / 4);
             const int q = i % (G::kBW / 4);         // 4-pixel chunk of the row
             const int ctx = q >> 3;                 // its lane tile
             const int c0 = (q & 7) * 4;             // its first column in the lane tile
             const int x = x0 + 4 * q;
-            const int y = y0 + kLH * ry + r;
-            if (y < H && x < W) {
-                const uint32_t mm = sm.mask[r][ry * G::BLX + ctx];
-                const uint32_t SS = mm & ~(mm << 1);
+            if (x >= W) continue;
+            const uint32_t ma = sm.mask[k * R][ry * G::BLX + ctx];
+            const uint32_t mbm = sm.mask[k * R + R - 1][ry * G::BLX + ctx];
+            const uint32_t mo = ma | mbm;
+            const uint32_t SS = mo & ~(mo << 1);
+            int lab[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = c0 + j;
+                lab[j] = ((mo >> c) & 1u) ? sm.runlab[ry][runlab_index<G>(ctx, hibit(SS & upto(c)))] : 0;
+            }
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr) {
+                const int y = y0 + kLH * ry + k * R + rr;
+                if (y >= H) break;
+                const uint32_t m = rr == 0 ? ma : mbm;
                 int v[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = c0 + j;
-                    v[j] = ((mm >> c) & 1u) ? sm.runlab[ry][runlab_index<G>(ctx, hibit(SS & upto(c)))] : 0;
-                }
+                for (int j = 0; j < 4; ++j) v[j] = ((m >> (c0 + j)) & 1u) ? lab[j] : 0;
                 int32_t *dst = labels + (size_t)y * W + x;
                 if (vec_out && x + 4 <= W) {
                     __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
@@ -758,13 +839,13 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     }
 }
 
-template <class G>
-__global__ void __launch_bounds__(G::kThreads, 4) k_block_write(JobTable jt, Scratch s, int cap, uint32_t bound) {
+template <class G, bool kConn8>
+__global__ void __launch_bounds__(G::kThreads) k_block_write(JobTable jt, Scratch s, int cap, uint32_t bound) {
     __shared__ WriteSmem<G> sm;
-    for (unsigned iter = 0; claim_item(jt, 2, iter, sm.item); ++iter) {
+    for (unsigned iter = 0; claim_item(jt, 1, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
-        process_write<G>(job, lb, gb, s, sm, cap, bound);
+        process_write<G, kConn8>(job, lb, gb, s, sm, cap, bound);
         __syncthreads();
     }
 }
@@ -781,7 +862,7 @@ namespace {
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t masks, lstream, vstream, edges, P, nslots, total;
+    size_t masks, vstream, edges, P, nslots, arrive, total;
 };
 
 template <class G>
@@ -789,11 +870,11 @@ Layout layout_for(size_t nb) {
     Layout l;
     size_t off = 0;
     l.masks = off;   off += up256(nb * G::kThreads * kLH * sizeof(uint32_t));
-    l.lstream = off; off += up256(nb * kLWords * G::kThreads * sizeof(uint32_t));
-    l.vstream = off; off += up256(nb * kVChunks * G::kThreads * sizeof(uint4));
+    l.vstream = off; off += up256(nb * kVChunksMax * G::kThreads * sizeof(uint4));
     l.edges = off;   off += up256(nb * G::kEdge * sizeof(uint16_t));
     l.P = off;       off += up256(nb * G::kSlots * sizeof(uint64_t));
     l.nslots = off;  off += up256(nb * sizeof(int32_t));
+    l.arrive = off;  off += up256(nb * 4 * sizeof(uint32_t));
     l.total = off;
     return l;
 }
@@ -804,11 +885,11 @@ Scratch carve(void *ws, size_t nb) {
     char *p = static_cast<char *>(ws);
     Scratch s;
     s.masks = reinterpret_cast<uint32_t *>(p + l.masks);
-    s.lstream = reinterpret_cast<uint32_t *>(p + l.lstream);
     s.vstream = reinterpret_cast<uint4 *>(p + l.vstream);
     s.edges = reinterpret_cast<uint16_t *>(p + l.edges);
     s.P = reinterpret_cast<uint64_t *>(p + l.P);
     s.nslots = reinterpret_cast<int32_t *>(p + l.nslots);
+    s.arrive = reinterpret_cast<uint32_t *>(p + l.arrive);
     return s;
 }
 
@@ -921,7 +1002,7 @@ int timing_read(double *ms, long long *count, int n) {
 }
 
 const char *kernel_kind_name(int k) {
-    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write"};
+    static const char *names[kKernelKinds] = {"k_block_local", "k_block_write"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
 }
 
@@ -934,8 +1015,25 @@ namespace {
 struct GeoLaunch {
     bool ready = false;
     int sms = 0;
-    int occ_local = 0, occ_merge = 0, occ_write = 0;
+    int occ_local[2] = {0, 0}, occ_write[2] = {0, 0};  // [conn8]
 };
+
+template <class G, bool kConn8>
+bool geo_launch_conn(int dev, GeoLaunch &g) {
+    const int bytes = (int)sizeof(LocalSmem<G, kConn8>);
+    if (cudaFuncSetAttribute(k_block_local<G, kConn8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
+        cudaSuccess)
+        return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_local[kConn8], k_block_local<G, kConn8>,
+                                                      G::kThreads, bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_write[kConn8], k_block_write<G, kConn8>,
+                                                      G::kThreads, 0) != cudaSuccess)
+        return false;
+    g.occ_local[kConn8] = std::max(1, g.occ_local[kConn8]);
+    g.occ_write[kConn8] = std::max(1, g.occ_write[kConn8]);
+    (void)dev;
+    return true;
+}
 
 template <class G>
 bool geo_launch(GeoLaunch &out) {
@@ -946,23 +1044,8 @@ bool geo_launch(GeoLaunch &out) {
     std::lock_guard<std::mutex> lk(mu);
     GeoLaunch &g = per_dev[dev];
     if (!g.ready) {
-        const int bytes = (int)sizeof(LocalSmem<G>);
-        if (cudaFuncSetAttribute(k_block_local<G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(k_block_local<G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-                cudaSuccess)
-            return false;
         if (cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_local, k_block_local<G, true>, G::kThreads,
-                                                          bytes) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_merge, k_block_merge<G, true>, G::kBW, 0) !=
-                cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_write, k_block_write<G>, G::kThreads, 0) !=
-                cudaSuccess)
-            return false;
-        g.occ_local = std::max(1, g.occ_local);
-        g.occ_merge = std::max(1, g.occ_merge);
-        g.occ_write = std::max(1, g.occ_write);
+        if (!geo_launch_conn<G, true>(dev, g) || !geo_launch_conn<G, false>(dev, g)) return false;
         g.ready = true;
     }
     out = g;
@@ -974,27 +1057,30 @@ bool geo_launch(GeoLaunch &out) {
 template <class G>
 void caps_for(size_t nb, int cap, int &local_cap, int &global_cap, uint32_t &bound) {
     const long long slots = (long long)nb * G::kSlots;
-    local_cap = cap > 0 ? cap : kLabCap * G::kThreads + 16;
+    local_cap = cap > 0 ? cap : kPieceCapMax * G::kThreads + 16;
     global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
     bound = (uint32_t)slots;
 }
 
+// The arrival counters of the neighbour pairs start at zero in every launch;
+// then the labelling kernel (steps 1 and 2) and the write-out (step 3).
 template <class G>
-int launch_table(int conn, const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
+int launch_table(int conn, const JobTable &jt, size_t nb, unsigned grid_local, unsigned grid_write,
                  const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream) {
+    if (cudaMemsetAsync(s.arrive, 0, nb * 4 * sizeof(uint32_t), stream) != cudaSuccess) return -1;
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G>), stream>>>(jt, s, local_cap);
+        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, true>), stream>>>(
+            jt, s, local_cap, global_cap, bound);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<G, true><<<grid_merge, G::kBW, 0, stream>>>(jt, s, global_cap, bound);
+        k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     } else {
-        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G>), stream>>>(jt, s, local_cap);
+        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, false>), stream>>>(
+            jt, s, local_cap, global_cap, bound);
         ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<G, false><<<grid_merge, G::kBW, 0, stream>>>(jt, s, global_cap, bound);
+        k_block_write<G, false><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     }
-    ev = timing_mark(stream, ev, kKindMerge);
-    k_block_write<G><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
-    ev = timing_mark(stream, ev, kKindRelabel);
+    ev = timing_mark(stream, ev, kKindWrite);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1021,8 +1107,8 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
     int local_cap, global_cap;
     uint32_t bound;
     caps_for<G>(nb, cap, local_cap, global_cap, bound);
-    return launch_table<G>(conn, jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve<G>(ws, nb), local_cap,
-                           global_cap, bound, stream);
+    return launch_table<G>(conn, jt, nb, (unsigned)nb, (unsigned)nb, carve<G>(ws, nb), local_cap, global_cap,
+                           bound, stream);
 }
 
 template <class G>
@@ -1037,8 +1123,9 @@ int launch_batch(int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t cap
     int local_cap, global_cap;
     uint32_t bound;
     caps_for<G>(capacity, cap, local_cap, global_cap, bound);
-    return launch_table<G>(conn, jt, (unsigned)(gl.sms * gl.occ_local), (unsigned)(gl.sms * gl.occ_merge),
-                           (unsigned)(gl.sms * gl.occ_write), carve<G>(ws, capacity), local_cap, global_cap,
+    const int c8 = conn == 8 ? 1 : 0;
+    return launch_table<G>(conn, jt, capacity, (unsigned)(gl.sms * gl.occ_local[c8]),
+                           (unsigned)(gl.sms * gl.occ_write[c8]), carve<G>(ws, capacity), local_cap, global_cap,
                            bound, stream);
 }
 
