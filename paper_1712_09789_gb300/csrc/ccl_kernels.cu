@@ -154,6 +154,7 @@ struct LocalSmem {
     uint32_t border[kWords];           // bit per entry: root owning a block-border pixel
     uint32_t prefix[kWords];           // border roots in the words before
     uint32_t warp_tot[G::kThreads / 32];
+    uint16_t xq[16][G::kThreads];      // further contacts of a band: (piece << 7) | piece above
     uint8_t lastbase[G::kThreads];     // first piece of each lane tile's last band
     int nslots;
     int err;
@@ -161,6 +162,8 @@ struct LocalSmem {
     ItemSlot item;
     static_assert(sizeof(MergeSmem<G>) <= sizeof(uint16_t) * kCap * G::kThreads,
                   "step 2 reuses the list entries' space");
+    static_assert(2 * G::kBW * sizeof(uint16_t) <= sizeof(uint32_t) * kLH * G::kThreads,
+                  "step 2 stages two block edges in the row masks' space");
 };
 
 // Border record entry of a piece value: its slot, or background when the value
@@ -201,19 +204,19 @@ struct HalfQueue {
 // the owner's top edge, left edge or corner are examined; a pair that repeats
 // the pair of the neighbouring pixel is skipped, and of the rest only those
 // that join two slot sets of the local union-find reach the global one.  The
-// partner's records were written by another CTA, so they are read with
-// volatile loads.  Called by the whole CTA (barriers inside).
+// partner's records were written by another CTA: they are read from L2 (the
+// two facing edges staged into `stage`, 2 x kBW entries, with 16-byte
+// loads).  Called by the whole CTA (barriers inside).
 template <class G, bool kConn8>
-__device__ void merge_pair(const Scratch &s, MergeSmem<G> &ms, unsigned owner, int kind, int nbx, int lcap,
-                           int gcap, int &err, uint32_t bound) {
+__device__ void merge_pair(const Scratch &s, MergeSmem<G> &ms, uint16_t *stage, unsigned owner, int kind, int nbx,
+                           int lcap, int gcap, int &err, uint32_t bound) {
     const unsigned partner = kind == 0 ? owner - 1u
                            : kind == 1 ? owner - (unsigned)nbx
                            : kind == 2 ? owner - (unsigned)nbx - 1u
                                        : owner - (unsigned)nbx + 1u;
-    const volatile uint16_t *E = s.edges + (size_t)owner * G::kEdge;
-    const volatile uint16_t *F = s.edges + (size_t)partner * G::kEdge;
-    const volatile int32_t *vn = s.nslots;
-    const int nso = vn[owner], nsp = vn[partner];
+    const uint16_t *E = s.edges + (size_t)owner * G::kEdge;
+    const uint16_t *F = s.edges + (size_t)partner * G::kEdge;
+    const int nso = __ldcg(s.nslots + owner), nsp = __ldcg(s.nslots + partner);
     const uint32_t obase = owner * (uint32_t)G::kSlots, pbase = partner * (uint32_t)G::kSlots;
     const auto ok_o = [&](uint16_t v) { return v != kBg && (int)v < nso; };
     const auto ok_p = [&](uint16_t v) { return v != kBg && (int)v < nsp; };
@@ -221,54 +224,44 @@ __device__ void merge_pair(const Scratch &s, MergeSmem<G> &ms, unsigned owner, i
     if (kind >= 2) {
         // the corner pixel pair of two diagonal neighbours (8-connectivity)
         if (t == 0) {
-            const uint16_t a = E[G::kEdgeTop + (kind == 2 ? 0 : G::kBW - 1)];
-            const uint16_t c = F[G::kEdgeBottom + (kind == 2 ? G::kBW - 1 : 0)];
+            const uint16_t a = __ldcg(E + G::kEdgeTop + (kind == 2 ? 0 : G::kBW - 1));
+            const uint16_t c = __ldcg(F + G::kEdgeBottom + (kind == 2 ? G::kBW - 1 : 0));
             if (ok_o(a) && ok_p(c)) union_global(s.P, obase + a, pbase + c, gcap, err, bound);
         }
         return;
     }
+    // n facing pixels: the owner's top row over the partner's bottom row, or
+    // the owner's left column beside the partner's right column
+    const int n = kind == 1 ? G::kBW : G::kBH;
+    const uint4 *src_o = reinterpret_cast<const uint4 *>(E + (kind == 1 ? G::kEdgeTop : G::kEdgeLeft));
+    const uint4 *src_p = reinterpret_cast<const uint4 *>(F + (kind == 1 ? G::kEdgeBottom : G::kEdgeRight));
+    uint4 *dst = reinterpret_cast<uint4 *>(stage);
+    for (int i = t; i < n / 4; i += G::kThreads)
+        dst[i] = __ldcg(i < n / 8 ? src_o + i : src_p + (i - n / 8));
     const int nn = nso + nsp;
     for (int i = t; i < nn; i += G::kThreads) ms.lp[i] = (uint16_t)i;
     if (t == 0) ms.nedge = 0;
     __syncthreads();
+    const uint16_t *so = stage, *sp = stage + n;
     const auto link = [&](uint16_t a, uint16_t c) {
         if (local_union(ms.lp, a, nso + c, lcap, err)) {
             const int k = atomicAdd(&ms.nedge, 1);
             if (k < 2 * G::kSlots) ms.edge[k] = ((uint32_t)a << 16) | c;
         }
     };
-    if (kind == 1) {
-        for (int j = t; j < G::kBW; j += G::kThreads) {
-            const uint16_t a = E[G::kEdgeTop + j];
-            if (!ok_o(a)) continue;
-            const uint16_t aL = j > 0 ? E[G::kEdgeTop + j - 1] : kBg;
-            const uint16_t aR = j + 1 < G::kBW ? E[G::kEdgeTop + j + 1] : kBg;
-            const uint16_t c = F[G::kEdgeBottom + j];
-            const uint16_t cL = j > 0 ? F[G::kEdgeBottom + j - 1] : kBg;
-            if (ok_p(c) && !(aL == a && cL == c)) link(a, c);
-            if (kConn8) {
-                if (j > 0 && ok_p(cL) && aL != a) link(a, cL);
-                if (j + 1 < G::kBW) {
-                    const uint16_t cR = F[G::kEdgeBottom + j + 1];
-                    if (ok_p(cR) && aR != a) link(a, cR);
-                }
-            }
-        }
-    } else {
-        for (int j = t; j < G::kBH; j += G::kThreads) {
-            const uint16_t a = E[G::kEdgeLeft + j];
-            if (!ok_o(a)) continue;
-            const uint16_t aU = j > 0 ? E[G::kEdgeLeft + j - 1] : kBg;
-            const uint16_t aD = j + 1 < G::kBH ? E[G::kEdgeLeft + j + 1] : kBg;
-            const uint16_t c = F[G::kEdgeRight + j];
-            const uint16_t cU = j > 0 ? F[G::kEdgeRight + j - 1] : kBg;
-            if (ok_p(c) && !(aU == a && cU == c)) link(a, c);
-            if (kConn8) {
-                if (j > 0 && ok_p(cU) && aU != a) link(a, cU);
-                if (j + 1 < G::kBH) {
-                    const uint16_t cD = F[G::kEdgeRight + j + 1];
-                    if (ok_p(cD) && aD != a) link(a, cD);
-                }
+    for (int j = t; j < n; j += G::kThreads) {
+        const uint16_t a = so[j];
+        if (!ok_o(a)) continue;
+        const uint16_t aL = j > 0 ? so[j - 1] : kBg;
+        const uint16_t aR = j + 1 < n ? so[j + 1] : kBg;
+        const uint16_t c = sp[j];
+        const uint16_t cL = j > 0 ? sp[j - 1] : kBg;
+        if (ok_p(c) && !(aL == a && cL == c)) link(a, c);
+        if (kConn8) {
+            if (j > 0 && ok_p(cL) && aL != a) link(a, cL);
+            if (j + 1 < n) {
+                const uint16_t cR = sp[j + 1];
+                if (ok_p(cR) && aR != a) link(a, cR);
             }
         }
     }
@@ -361,7 +354,10 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     // -- coarse labelling and refinement, band by band, on the thread's own
     // entries only.  A piece touching the band above takes the first piece it
     // touches there as parent (a root of its own otherwise, keyed by its
-    // smallest pixel); every further piece it touches is merged with it.
+    // smallest pixel); every further piece it touches is queued and merged
+    // with it once the band is placed.  The 32 lanes of a warp step through
+    // their pieces together (lanes past their last piece see a dummy one and
+    // store nothing), and the queued merges run as one round per entry.
     uint16_t *const par = sm.par;
     int base_prev = 0, npieces = 0;
     {
@@ -372,34 +368,43 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const uint32_t OR = A | Bm;
             const uint32_t S0 = OR & ~(OR << 1), E0 = OR & ~(OR >> 1);
             uint32_t S = S0, E = E0;
-            int loc = npieces;
-            while (S) {
-                const int a0 = lobit(S), a1 = lobit(E);
+            const int nk = __popc(S0);
+            const int nmax = __reduce_max_sync(kFull, nk);
+            int nq = 0;
+            for (int i = 0; i < nmax; ++i) {
+                const int a0 = lobit(S | 0x80000000u), a1 = lobit(E | 0x80000000u);
                 S &= S - 1u;
                 E &= E - 1u;
+                const bool act = i < nk;
                 const uint32_t rb = run_bits(a0, a1);
-                const uint32_t P = pB & touch_range<kConn8>(A & rb);
-                if (P) {
-                    // parent: the root the first touched piece above had when
-                    // it was placed (its entry holds that root's id)
-                    const int u0 = lobit(P);
-                    const int up = base_prev + __popc(pS & upto(u0)) - 1;
-                    const uint16_t ue = par[up * T + t];
-                    par[loc * T + t] = (ue & kRoot) ? (uint16_t)((t << 7) | up) : ue;
-                    uint32_t P2 = P & ~upto(piece_end(pE, u0));
-                    while (P2) {
-                        const int u = lobit(P2);
-                        union_private<G, kCap>(par, (t << 7) | loc, (t << 7) | (base_prev + __popc(pS & upto(u)) - 1),
-                                               cap, err);
-                        P2 &= ~upto(piece_end(pE, u));
-                    }
-                } else {
-                    par[loc * T + t] = (uint16_t)(kRoot | piece_key<G, kConn8>(tx, ty, k, A, rb, a0));
+                const uint32_t P = act ? (pB & touch_range<kConn8>(A & rb)) : 0u;
+                // parent: the root the first touched piece above had when it
+                // was placed (its entry holds that root's id)
+                const int u0 = lobit(P | 0x80000000u);
+                const int up = P ? base_prev + __popc(pS & upto(u0)) - 1 : 0;
+                const uint16_t ue = par[up * T + t];
+                const uint16_t ent = P ? ((ue & kRoot) ? (uint16_t)((t << 7) | up) : ue)
+                                       : (uint16_t)(kRoot | piece_key<G, kConn8>(tx, ty, k, A, rb, a0));
+                if (act) par[(npieces + i) * T + t] = ent;
+                uint32_t P2 = P ? (P & ~upto(piece_end(pE, u0))) : 0u;
+                // (a piece above is a further contact of at most one piece of
+                // the band, the leftmost that touches it, so at most 16 queue)
+                while (P2) {
+                    const int u = lobit(P2);
+                    if (nq < 16) sm.xq[nq++][t] = (uint16_t)(((npieces + i) << 7) | (base_prev + __popc(pS & upto(u)) - 1));
+                    else err |= kErrLocalCap;
+                    P2 &= ~upto(piece_end(pE, u));
                 }
-                ++loc;
+            }
+            const int nqmax = __reduce_max_sync(kFull, nq);
+            for (int j = 0; j < nqmax; ++j) {
+                if (j < nq) {
+                    const int q = sm.xq[j][t];
+                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err);
+                }
             }
             base_prev = npieces;
-            npieces = loc;
+            npieces += nk;
             pB = Bm;
             pS = S0;
             pE = E0;
@@ -596,50 +601,43 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         return (uint16_t)(re & 0x7FFF);
     };
 
-    // -- border record of the block: the slot of every border pixel
+    // -- border record of the block: the slot of every border pixel, one
+    // pixel per thread and step (any thread can read any lane tile's lists)
     uint16_t *const Eb = s.edges + (size_t)b * G::kEdge;
-    const auto edge_row = [&](uint32_t S, uint32_t Mr, int first, uint16_t *dst) {
-        uint32_t wv[kLW / 2];
-        int idx = first - 1;
+    for (int c = t; c < G::kBW; c += T) {
+        // top row: band 0 of the lane tiles with ty == 0
+        const int lt = c >> 5, bit = c & 31;
+        const uint32_t A = sm.mask[0][lt], OR = A | sm.mask[R - 1][lt];
         uint16_t v = kBg;
-#pragma unroll
-        for (int c = 0; c < kLW; ++c) {
-            if ((S >> c) & 1u) {
-                ++idx;
-                v = border_slot(value_of((t << 7) | idx));
+        if ((A >> bit) & 1u) v = border_slot(value_of((lt << 7) | (__popc(OR & ~(OR << 1) & upto(bit)) - 1)));
+        Eb[G::kEdgeTop + c] = v;
+        // bottom row: the last band of the lane tiles with ty == BLY - 1
+        const int lb2 = (G::BLY - 1) * G::BLX + lt;
+        const uint32_t Bl = sm.mask[kLH - 1][lb2], ORl = Bl | sm.mask[kLH - R][lb2];
+        v = kBg;
+        if ((Bl >> bit) & 1u)
+            v = border_slot(value_of((lb2 << 7) | (sm.lastbase[lb2] + __popc(ORl & ~(ORl << 1) & upto(bit)) - 1)));
+        Eb[G::kEdgeBottom + c] = v;
+    }
+    for (int i = t; i < 2 * G::kBH; i += T) {
+        // left column (first G::kBH indices) and right column of the block
+        const bool right = i >= G::kBH;
+        const int r = right ? i - G::kBH : i;
+        const int lt = (r >> 3) * G::BLX + (right ? G::BLX - 1 : 0);
+        const int rr = r & (kLH - 1), k = rr / R;
+        const uint32_t m = sm.mask[rr][lt];
+        uint16_t v = kBg;
+        if (right ? (m >> 31) : (m & 1u)) {
+            int base = 0;
+            for (int j = 0; j < k; ++j) {
+                const uint32_t o = sm.mask[j * R][lt] | sm.mask[j * R + R - 1][lt];
+                base += __popc(o & ~(o << 1));
             }
-            const uint32_t o = ((Mr >> c) & 1u) ? v : kBg;
-            if (c & 1) wv[c >> 1] |= o << 16;
-            else wv[c >> 1] = o;
+            const uint32_t o = sm.mask[k * R][lt] | sm.mask[k * R + R - 1][lt];
+            const int loc = right ? base + __popc(o & ~(o << 1)) - 1 : base;
+            v = border_slot(value_of((lt << 7) | loc));
         }
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
-#pragma unroll
-        for (int q = 0; q < kLW / 8; ++q) d4[q] = make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
-    };
-    if (ty == 0) edge_row(S00, A0, 0, Eb + G::kEdgeTop + kLW * tx);
-    if (ty == G::BLY - 1) edge_row(SL, BL, base_prev, Eb + G::kEdgeBottom + kLW * tx);
-    if (tx == 0 || tx == G::BLX - 1) {
-        uint32_t wv[kLH / 2];
-        int mb = 0;
-#pragma unroll
-        for (int k = 0; k < NB; ++k) {
-            const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
-            const int np = __popc(OR & ~(OR << 1));
-            const int id = (t << 7) | (tx == 0 ? mb : mb + np - 1);
-            const bool any = tx == 0 ? (OR & 1u) : (OR >> 31);
-            const uint16_t v = any ? border_slot(value_of(id)) : kBg;
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr) {
-                const int r = k * R + rr;
-                const bool fg = tx == 0 ? (mrow[r] & 1u) : (mrow[r] >> 31);
-                const uint32_t o = fg ? v : kBg;
-                if (r & 1) wv[r >> 1] |= o << 16;
-                else wv[r >> 1] = o;
-            }
-            mb += np;
-        }
-        *reinterpret_cast<uint4 *>(Eb + (tx == 0 ? G::kEdgeLeft : G::kEdgeRight) + kLH * ty) =
-            make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        Eb[(right ? G::kEdgeRight : G::kEdgeLeft) + r] = v;
     }
     // -- per-piece values, in piece order
     {
@@ -690,7 +688,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             unsigned owner;
             int kind;
             arrival_pair<kConn8>(r, b, bx, by, nbx, nby, owner, kind);
-            merge_pair<G, kConn8>(s, sm.merge, owner, kind, nbx, cap, gcap, gerr, bound);
+            merge_pair<G, kConn8>(s, sm.merge, reinterpret_cast<uint16_t *>(&sm.mask[0][0]), owner, kind, nbx, cap,
+                                  gcap, gerr, bound);
         }
         if (gerr) atomicOr(&sm.err, gerr);
     }
