@@ -43,7 +43,8 @@ METRIC = "Gpixel/s & % HBM roofline, plain vs batched persistent; serving p50/p9
 UNIT = "Gpixel/s"
 BYTES_PER_PIXEL = 5          # 1 B image read + 4 B label written
 KERNEL_BYTES_PER_PIXEL = {   # the path's algorithmic bytes each kernel moves, per pixel
-    "k_block_local": 1,      # reads the image once (and merges block borders)
+    "k_block_local": 1,      # reads the image once
+    "k_block_merge": 0,      # block border records only
     "k_block_write": 4,      # writes every label once
 }
 SIDE = 4096

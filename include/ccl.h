@@ -272,10 +272,9 @@ void ccl_debug_set_iteration_cap(int cap);
 
 /*
  * Benchmark hook.  While enabled, every call records CUDA events on its own
- * stream around each of its kernels (kind 0: block-local labelling with the
- * block merges, 1: root-find and label write-out) and their durations
- * accumulate per kind.  Enabling or disabling waits for pending events and
- * clears the sums.
+ * stream around each of its kernels (kind 0: block-local labelling, 1: block
+ * merge, 2: root-find and label write-out) and their durations accumulate per
+ * kind.  Enabling or disabling waits for pending events and clears the sums.
  */
 void ccl_debug_kernel_timing(int enable);
 

@@ -6,15 +6,16 @@
 // c).  The block shape (BLX, BLY) is a template parameter so that the batched
 // path can pick it per workload.
 //
-// Bands and pieces.  A lane tile is cut into bands of rows: one row for
-// 4-connectivity, two rows for 8-connectivity.  A piece is a maximal run of
-// set bits of the band's column mask (the OR of its rows).  With one row a
-// piece is a row run.  With two rows every foreground pixel of a column run of
-// the OR is 8-adjacent to every pixel of the neighbouring column (|dx| <= 1,
-// |dy| <= 1), so a piece is exactly one 8-connected component of the band:
-// the band's labelling costs bit operations only, and there are fewer pieces
-// than row runs.  Pieces are numbered per lane tile in band order, then
-// column order, which is recomputable from the masks by a popcount.
+// Bands and pieces.  A lane tile is cut into bands of two rows.  A piece is
+// one connected component of a band, and it is found by bit operations: the
+// two pixels of a column of a band always touch, so a component is a run of
+// columns, each linked to the next (see band_link).  Under 8-connectivity
+// every pixel of a column is adjacent to every pixel of the next (|dx| <= 1,
+// |dy| <= 1), so the pieces are the runs of the OR of the two rows; under
+// 4-connectivity a run of the OR splits where its columns meet only
+// diagonally.  There are fewer pieces than row runs, so the label-equivalence
+// work shrinks.  Pieces are numbered per lane tile in band order, then column
+// order, which is recomputable from the masks by a popcount.
 //
 // Label-equivalence lists.  Piece `loc` of thread t has the id (t << 7) | loc
 // and one 16-bit entry in shared memory: a root holds kRoot | key, key being
@@ -33,7 +34,7 @@ namespace ccl {
 
 constexpr int kLW = 32;                 // lane tile width (bits of a row mask)
 constexpr int kLH = 8;                  // lane tile height (rows of a thread)
-constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile, one-row bands
+constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile: at most 32 per two-row band
 constexpr int kVChunksMax = kPieceCapMax / 8;  // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
 constexpr uint16_t kBg = 0xFFFF;
@@ -72,12 +73,14 @@ struct Geo {
     static_assert((kEdge * 2) % 16 == 0, "border records must stay 16-byte aligned");
 };
 
-// Band layout of a lane tile for one connectivity.
+// Band layout of a lane tile for one connectivity: bands of two rows; a band
+// holds at most 16 pieces under 8-connectivity (pieces are runs of the OR of
+// its rows), 32 under 4-connectivity (one per column at most).
 template <bool kConn8>
 struct Bands {
-    static constexpr int kRows = kConn8 ? 2 : 1;  // rows per band
+    static constexpr int kRows = 2;                // rows per band
     static constexpr int kN = kLH / kRows;         // bands per lane tile
-    static constexpr int kCap = 16 * kN;           // pieces per lane tile (<= 16 per band)
+    static constexpr int kCap = (kConn8 ? 16 : 32) * kN;  // pieces per lane tile
     static constexpr int kVChunks = kCap / 8;
 };
 
@@ -116,6 +119,27 @@ __device__ __forceinline__ uint32_t run_bits(int a0, int a1) { return (2u << a1)
 template <bool kConn8>
 __device__ __forceinline__ uint32_t touch_range(uint32_t rm) {
     return kConn8 ? (rm | (rm << 1) | (rm >> 1)) : rm;
+}
+
+// Links of a band with rows A (upper) and B (lower): bit c is set when
+// columns c and c+1 hold pixels of one piece.  The pixels of one column of a
+// band always touch.  Under 8-connectivity any pixel of a column touches any
+// pixel of the next one, so two occupied columns are linked; under
+// 4-connectivity only a row holding both pixels links them.
+template <bool kConn8>
+__device__ __forceinline__ uint32_t band_link(uint32_t A, uint32_t B) {
+    const uint32_t OR = A | B;
+    return kConn8 ? (OR & (OR >> 1)) : ((A & (A >> 1)) | (B & (B >> 1)));
+}
+
+// First and last columns of the band's pieces.
+template <bool kConn8>
+__device__ __forceinline__ uint32_t band_starts(uint32_t A, uint32_t B) {
+    return (A | B) & ~(band_link<kConn8>(A, B) << 1);
+}
+template <bool kConn8>
+__device__ __forceinline__ uint32_t band_ends(uint32_t A, uint32_t B) {
+    return (A | B) & ~band_link<kConn8>(A, B);
 }
 
 // Last column of the piece (run of `ends`' mask) holding column u.

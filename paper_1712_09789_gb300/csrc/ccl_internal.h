@@ -76,8 +76,8 @@ ccl_status check_image_args_api(const void *img, int H, int W, size_t pitch, int
 int iteration_cap_api();
 
 // Benchmark timing of the kernels enqueued by launch_label().
-constexpr int kKindLocal = 0, kKindWrite = 1;
-constexpr int kKernelKinds = 2;
+constexpr int kKindLocal = 0, kKindMerge = 1, kKindWrite = 2;
+constexpr int kKernelKinds = 3;
 void timing_enable(bool on);
 int timing_read(double *ms, long long *count, int n);
 const char *kernel_kind_name(int k);

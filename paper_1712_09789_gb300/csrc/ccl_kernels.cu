@@ -12,11 +12,11 @@
 //                   value per piece (block key of its root, or its border
 //                   slot), the border record of the block and one global
 //                   union-find entry per border component.
-//                   Then step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
-//                   pairs that straddle a block edge are examined.  Each pair
-//                   of neighbouring blocks is merged by whichever of the two
-//                   finishes step 1 second (an arrival counter per pair tells
-//                   it), so no CTA waits for another.
+//   k_block_merge   step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): only the pixel
+//                   pairs that straddle a block edge are examined; the block's
+//                   pairs are first joined in a shared-memory union-find and
+//                   only the pairs that join two of its sets reach the global
+//                   union-find.
 //   k_block_write   step 3 (Sec. 3.3): root-find for the block's border slots
 //                   in the merged union-find, then expands the per-piece
 //                   values over the row masks and writes every label once.
@@ -52,7 +52,6 @@ struct Scratch {
     uint16_t *edges;   // [blocks][edge entries]
     uint64_t *P;       // [blocks][slots]
     int32_t *nslots;   // [blocks]
-    uint32_t *arrive;  // [blocks][4]: arrivals at the block's left, up, up-left, up-right pairs
 };
 
 __device__ __forceinline__ void report(int err) {
@@ -98,17 +97,6 @@ __device__ __forceinline__ bool claim_item(const JobTable &jt, int which, unsign
 }
 
 // ---------------------------------------------------------------------------
-// Shared memory of step 2 on one pair of neighbouring blocks: a union-find
-// over the border slots of both blocks (owner's slots first), which keeps
-// only the pixel pairs that join two different slot sets; those few go to
-// the global union-find.
-template <class G>
-struct MergeSmem {
-    uint16_t lp[2 * G::kSlots];    // parent (a smaller node) or itself
-    uint32_t edge[2 * G::kSlots];  // joining pairs: (owner slot << 16) | partner slot
-    int nedge;
-};
-
 // Local root of node x with path halving (stores only ancestors, which a
 // concurrent CAS link on a root cannot lose).
 __device__ __forceinline__ int local_find(volatile uint16_t *lp, int x, int cap, int &err) {
@@ -146,10 +134,7 @@ template <class G, bool kConn8>
 struct LocalSmem {
     static constexpr int kCap = Bands<kConn8>::kCap;
     static constexpr int kWords = kCap * G::kThreads / 32;  // bitmap words over all entries
-    union {
-        uint16_t par[kCap * G::kThreads];  // list entries, see ccl_block.cuh
-        MergeSmem<G> merge;                // step 2, once the lists are done with
-    };
+    uint16_t par[kCap * G::kThreads];  // list entries, see ccl_block.cuh
     uint32_t mask[kLH][G::kThreads];   // row masks
     uint32_t border[kWords];           // bit per entry: root owning a block-border pixel
     uint32_t prefix[kWords];           // border roots in the words before
@@ -158,12 +143,7 @@ struct LocalSmem {
     uint8_t lastbase[G::kThreads];     // first piece of each lane tile's last band
     int nslots;
     int err;
-    int merges;                        // neighbour pairs this CTA merges, bit per pair
     ItemSlot item;
-    static_assert(sizeof(MergeSmem<G>) <= sizeof(uint16_t) * kCap * G::kThreads,
-                  "step 2 reuses the list entries' space");
-    static_assert(2 * G::kBW * sizeof(uint16_t) <= sizeof(uint32_t) * kLH * G::kThreads,
-                  "step 2 stages two block edges in the row masks' space");
 };
 
 // Border record entry of a piece value: its slot, or background when the value
@@ -173,16 +153,13 @@ __device__ __forceinline__ uint16_t border_slot(uint16_t v) {
 }
 
 // Block raster key of the smallest pixel of a piece: its first pixel in the
-// band's top row, else (8-connectivity, the piece has pixels in the lower row
-// only, where it is a row run) its first column in the lower row.
-template <class G, bool kConn8>
+// band's upper row, else (the piece has pixels in the lower row only, where
+// it is a row run) its first column.
+template <class G>
 __device__ __forceinline__ int piece_key(int tx, int ty, int k, uint32_t A, uint32_t rb, int a0) {
-    int row = k, col = a0;
-    if (kConn8) {
-        const uint32_t top = A & rb;
-        row = 2 * k + (top ? 0 : 1);
-        col = top ? lobit(top) : a0;
-    }
+    const uint32_t top = A & rb;
+    const int row = 2 * k + (top ? 0 : 1);
+    const int col = top ? lobit(top) : a0;
     return ((kLH * ty + row) << G::kBWLog2) + kLW * tx + col;
 }
 
@@ -198,104 +175,9 @@ struct HalfQueue {
     __device__ __forceinline__ uint4 bits() const { return make_uint4(q0, q1, q2, q3); }
 };
 
-// ---------------------------------------------------------------------------
-// Step 2 on one pair of neighbouring blocks: `owner` and the block left of it
-// (kind 0), above it (1), above-left (2) or above-right (3).  The pairs across
-// the owner's top edge, left edge or corner are examined; a pair that repeats
-// the pair of the neighbouring pixel is skipped, and of the rest only those
-// that join two slot sets of the local union-find reach the global one.  The
-// partner's records were written by another CTA: they are read from L2 (the
-// two facing edges staged into `stage`, 2 x kBW entries, with 16-byte
-// loads).  Called by the whole CTA (barriers inside).
-template <class G, bool kConn8>
-__device__ void merge_pair(const Scratch &s, MergeSmem<G> &ms, uint16_t *stage, unsigned owner, int kind, int nbx,
-                           int lcap, int gcap, int &err, uint32_t bound) {
-    const unsigned partner = kind == 0 ? owner - 1u
-                           : kind == 1 ? owner - (unsigned)nbx
-                           : kind == 2 ? owner - (unsigned)nbx - 1u
-                                       : owner - (unsigned)nbx + 1u;
-    const uint16_t *E = s.edges + (size_t)owner * G::kEdge;
-    const uint16_t *F = s.edges + (size_t)partner * G::kEdge;
-    const int nso = __ldcg(s.nslots + owner), nsp = __ldcg(s.nslots + partner);
-    const uint32_t obase = owner * (uint32_t)G::kSlots, pbase = partner * (uint32_t)G::kSlots;
-    const auto ok_o = [&](uint16_t v) { return v != kBg && (int)v < nso; };
-    const auto ok_p = [&](uint16_t v) { return v != kBg && (int)v < nsp; };
-    const int t = threadIdx.x;
-    if (kind >= 2) {
-        // the corner pixel pair of two diagonal neighbours (8-connectivity)
-        if (t == 0) {
-            const uint16_t a = __ldcg(E + G::kEdgeTop + (kind == 2 ? 0 : G::kBW - 1));
-            const uint16_t c = __ldcg(F + G::kEdgeBottom + (kind == 2 ? G::kBW - 1 : 0));
-            if (ok_o(a) && ok_p(c)) union_global(s.P, obase + a, pbase + c, gcap, err, bound);
-        }
-        return;
-    }
-    // n facing pixels: the owner's top row over the partner's bottom row, or
-    // the owner's left column beside the partner's right column
-    const int n = kind == 1 ? G::kBW : G::kBH;
-    const uint4 *src_o = reinterpret_cast<const uint4 *>(E + (kind == 1 ? G::kEdgeTop : G::kEdgeLeft));
-    const uint4 *src_p = reinterpret_cast<const uint4 *>(F + (kind == 1 ? G::kEdgeBottom : G::kEdgeRight));
-    uint4 *dst = reinterpret_cast<uint4 *>(stage);
-    for (int i = t; i < n / 4; i += G::kThreads)
-        dst[i] = __ldcg(i < n / 8 ? src_o + i : src_p + (i - n / 8));
-    const int nn = nso + nsp;
-    for (int i = t; i < nn; i += G::kThreads) ms.lp[i] = (uint16_t)i;
-    if (t == 0) ms.nedge = 0;
-    __syncthreads();
-    const uint16_t *so = stage, *sp = stage + n;
-    const auto link = [&](uint16_t a, uint16_t c) {
-        if (local_union(ms.lp, a, nso + c, lcap, err)) {
-            const int k = atomicAdd(&ms.nedge, 1);
-            if (k < 2 * G::kSlots) ms.edge[k] = ((uint32_t)a << 16) | c;
-        }
-    };
-    for (int j = t; j < n; j += G::kThreads) {
-        const uint16_t a = so[j];
-        if (!ok_o(a)) continue;
-        const uint16_t aL = j > 0 ? so[j - 1] : kBg;
-        const uint16_t aR = j + 1 < n ? so[j + 1] : kBg;
-        const uint16_t c = sp[j];
-        const uint16_t cL = j > 0 ? sp[j - 1] : kBg;
-        if (ok_p(c) && !(aL == a && cL == c)) link(a, c);
-        if (kConn8) {
-            if (j > 0 && ok_p(cL) && aL != a) link(a, cL);
-            if (j + 1 < n) {
-                const uint16_t cR = sp[j + 1];
-                if (ok_p(cR) && aR != a) link(a, cR);
-            }
-        }
-    }
-    __syncthreads();
-    const int ne = ms.nedge < 2 * G::kSlots ? ms.nedge : 2 * G::kSlots;
-    for (int i = t; i < ne; i += G::kThreads) {
-        const uint32_t e = ms.edge[i];
-        union_global(s.P, obase + (e >> 16), pbase + (e & 0xFFFFu), gcap, err, bound);
-    }
-    __syncthreads();
-}
-
-// The pair that arrival r of block b (bx, by) belongs to: r < 4 are b's own
-// pairs (left, up, up-left, up-right), r >= 4 the pairs of the blocks right,
-// below, below-right and below-left of b, where b is the partner.
-template <bool kConn8>
-__device__ __forceinline__ bool arrival_pair(int r, unsigned b, int bx, int by, int nbx, int nby, unsigned &owner,
-                                             int &kind) {
-    kind = r & 3;
-    switch (r) {
-        case 0: owner = b; return bx > 0;
-        case 1: owner = b; return by > 0;
-        case 2: owner = b; return kConn8 && bx > 0 && by > 0;
-        case 3: owner = b; return kConn8 && bx + 1 < nbx && by > 0;
-        case 4: owner = b + 1u; return bx + 1 < nbx;
-        case 5: owner = b + (unsigned)nbx; return by + 1 < nby;
-        case 6: owner = b + (unsigned)nbx + 1u; return kConn8 && bx + 1 < nbx && by + 1 < nby;
-        default: owner = b + (unsigned)nbx - 1u; return kConn8 && bx > 0 && by + 1 < nby;
-    }
-}
-
 template <class G, bool kConn8>
 __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
-                                              LocalSmem<G, kConn8> &sm, int cap, int gcap, uint32_t bound) {
+                                              LocalSmem<G, kConn8> &sm, int cap) {
     using Bd = Bands<kConn8>;
     constexpr int kCap = Bd::kCap;
     constexpr int R = Bd::kRows;
@@ -304,7 +186,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     constexpr int kWPT = kCap / 32;  // bitmap words per thread
 
     const unsigned b = gb;
-    const int nbx = job.nbx, nby = job.nby;
+    const int nbx = job.nbx;
     const int bx = (int)(lb % (unsigned)nbx), by = (int)(lb / (unsigned)nbx);
     const int H = job.H, W = job.W;
     const uint8_t *const img = job.img;
@@ -316,10 +198,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
     int err = 0;
 
-    if (t == 0) {
-        sm.err = 0;
-        sm.merges = 0;
-    }
+    if (t == 0) sm.err = 0;
     for (int i = t; i < LocalSmem<G, kConn8>::kWords; i += T) sm.border[i] = 0u;
 
     // -- initialization: the lane tile's 8 rows as masks (all loads in flight
@@ -365,8 +244,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1];
-            const uint32_t OR = A | Bm;
-            const uint32_t S0 = OR & ~(OR << 1), E0 = OR & ~(OR >> 1);
+            const uint32_t S0 = band_starts<kConn8>(A, Bm), E0 = band_ends<kConn8>(A, Bm);
             uint32_t S = S0, E = E0;
             const int nk = __popc(S0);
             const int nmax = __reduce_max_sync(kFull, nk);
@@ -384,15 +262,22 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const int up = P ? base_prev + __popc(pS & upto(u0)) - 1 : 0;
                 const uint16_t ue = par[up * T + t];
                 const uint16_t ent = P ? ((ue & kRoot) ? (uint16_t)((t << 7) | up) : ue)
-                                       : (uint16_t)(kRoot | piece_key<G, kConn8>(tx, ty, k, A, rb, a0));
+                                       : (uint16_t)(kRoot | piece_key<G>(tx, ty, k, A, rb, a0));
                 if (act) par[(npieces + i) * T + t] = ent;
                 uint32_t P2 = P ? (P & ~upto(piece_end(pE, u0))) : 0u;
                 // (a piece above is a further contact of at most one piece of
-                // the band, the leftmost that touches it, so at most 16 queue)
+                // the band, the leftmost that touches it; a full queue, which
+                // takes 16 of them, is merged by its thread on the spot)
                 while (P2) {
                     const int u = lobit(P2);
-                    if (nq < 16) sm.xq[nq++][t] = (uint16_t)(((npieces + i) << 7) | (base_prev + __popc(pS & upto(u)) - 1));
-                    else err |= kErrLocalCap;
+                    if (nq == 16) {
+                        for (int j = 0; j < 16; ++j) {
+                            const int q = sm.xq[j][t];
+                            union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err);
+                        }
+                        nq = 0;
+                    }
+                    sm.xq[nq++][t] = (uint16_t)(((npieces + i) << 7) | (base_prev + __popc(pS & upto(u)) - 1));
                     P2 &= ~upto(piece_end(pE, u));
                 }
             }
@@ -414,26 +299,62 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     __syncthreads();
 
     // -- block merge of the lane tiles along their seams (Kernel 2's boundary
-    // analysis applied inside the block, on the shared lists)
-    const auto seam = [&](bool valid, int a, int b) { union_block_sync<G, kCap>(par, valid, a, b, cap, err); };
+    // analysis applied inside the block, on the shared lists).  A thread
+    // queues the pairs it finds (as the roots their entries name, a pair
+    // equal to the one queued before it dropped) and the warp merges the
+    // queues in rounds of one pair per lane, whenever a queue may overflow
+    // and at the end.
+    volatile uint16_t *const vpar = sm.par;
+    constexpr int kSQ = 8;  // queue entries per thread, in the space of the band queue
+    uint32_t *const sq = reinterpret_cast<uint32_t *>(&sm.xq[0][0]);
+    static_assert(sizeof(uint32_t) * kSQ <= sizeof(uint16_t) * 16, "seam queue fits the band queue");
+    int nsq = 0;
+    uint32_t lastq = 0xFFFFFFFFu;
+    const auto seam = [&](bool valid, int a, int b) {
+        if (valid) {
+            const uint16_t ea = vpar[par_index<G, kCap>(a)], eb = vpar[par_index<G, kCap>(b)];
+            const int ra = (ea & kRoot) ? a : (int)ea, rb = (eb & kRoot) ? b : (int)eb;
+            const uint32_t q = ((uint32_t)ra << 16) | (uint32_t)rb;
+            if (ra != rb && q != lastq) {
+                sq[nsq * T + t] = q;
+                ++nsq;
+                lastq = q;
+            }
+        }
+    };
+    const auto flush = [&]() {
+        const int m = __reduce_max_sync(kFull, nsq);
+        for (int j = 0; j < m; ++j) {
+            const bool v = j < nsq;
+            const uint32_t q = v ? sq[j * T + t] : 0u;
+            union_block_sync<G, kCap>(par, v, (int)(q >> 16), (int)(q & 0xFFFFu), cap, err);
+        }
+        nsq = 0;
+    };
+    const auto room = [&](int n) {
+        if (__any_sync(kFull, nsq > kSQ - n)) flush();
+    };
     {
         const bool hasl = tx > 0;
         const int tl = hasl ? t - 1 : t;
         int mb = 0, lbase = 0;
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
-            const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1], OR = A | Bm;
-            const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl], lOR = lA | lB;
-            const int np = __popc(OR & ~(OR << 1));
-            const int lnp = __popc(lOR & ~(lOR << 1));
+            room(3);
+            const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1];
+            const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl];
+            const int np = __popc(band_starts<kConn8>(A, Bm));
+            const int lnp = __popc(band_starts<kConn8>(lA, lB));
             const int me_first = (t << 7) | mb;
             const int l_last = (tl << 7) | (lbase + lnp - 1);
-            seam(hasl && (OR & 1u) && (lOR >> 31), me_first, l_last);
+            // column 0 of my band k beside column 31 of the left band k
+            const uint32_t side = kConn8 ? (A | Bm) & ((lA | lB) >> 31) : (A & (lA >> 31)) | (Bm & (lB >> 31));
+            seam(hasl && (side & 1u), me_first, l_last);
             if (kConn8 && k + 1 < NB) {
                 const uint32_t nA = mrow[(k + 1) * R];
                 const uint32_t lnA = sm.mask[(k + 1) * R][tl];
-                const uint32_t lnOR = lnA | sm.mask[(k + 1) * R + R - 1][tl];
-                const int l_next_last = (tl << 7) | (lbase + lnp + __popc(lnOR & ~(lnOR << 1)) - 1);
+                const int l_next_last =
+                    (tl << 7) | (lbase + lnp + __popc(band_starts<kConn8>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
                 // lower row of my band k, column 0 ~ upper row of the left band k+1, column 31
                 seam(hasl && (Bm & 1u) && (lnA >> 31), me_first, l_next_last);
                 // upper row of my band k+1, column 0 ~ lower row of the left band k, column 31
@@ -443,13 +364,13 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             lbase += lnp;
         }
     }
-    const uint32_t A0 = mrow[0], OR0 = A0 | mrow[R - 1];
-    const uint32_t S00 = OR0 & ~(OR0 << 1), E00 = OR0 & ~(OR0 >> 1);
+    const uint32_t A0 = mrow[0];
+    const uint32_t S00 = band_starts<kConn8>(A0, mrow[R - 1]), E00 = band_ends<kConn8>(A0, mrow[R - 1]);
     {
         const bool hasu = ty > 0;
         const int tu = hasu ? t - G::BLX : t;
-        const uint32_t uB = sm.mask[kLH - 1][tu], uOR = sm.mask[kLH - R][tu] | uB;
-        const uint32_t uS = uOR & ~(uOR << 1), uE = uOR & ~(uOR >> 1);
+        const uint32_t uA = sm.mask[kLH - R][tu], uB = sm.mask[kLH - 1][tu];
+        const uint32_t uS = band_starts<kConn8>(uA, uB), uE = band_ends<kConn8>(uA, uB);
         const int ubase = sm.lastbase[tu];
         uint32_t S = hasu ? S00 : 0u;
         uint32_t E = hasu ? E00 : 0u;
@@ -462,6 +383,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             uint32_t P = act ? (uB & touch_range<kConn8>(A0 & run_bits(a0, a1))) : 0u;
             const int me = (t << 7) | i;
             while (__any_sync(kFull, P != 0u)) {
+                room(1);
                 const bool hp = P != 0u;
                 const int u = hp ? lobit(P) : 0;
                 seam(hp, me, (tu << 7) | (ubase + __popc(uS & upto(u)) - 1));
@@ -470,21 +392,22 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         }
         if (kConn8) {
             // corners: the lane tiles up-left and up-right
+            room(2);
             const bool ul = hasu && tx > 0 && (A0 & 1u);
             const int tul = ul ? tu - 1 : t;
             const uint32_t ulB = sm.mask[kLH - 1][tul];
-            const uint32_t ulOR = sm.mask[kLH - 2][tul] | ulB;
-            seam(ul && (ulB >> 31), t << 7, (tul << 7) | (sm.lastbase[tul] + __popc(ulOR & ~(ulOR << 1)) - 1));
+            seam(ul && (ulB >> 31), t << 7,
+                 (tul << 7) | (sm.lastbase[tul] + __popc(band_starts<kConn8>(sm.mask[kLH - 2][tul], ulB)) - 1));
             const bool ur = hasu && tx + 1 < G::BLX && (A0 >> 31);
             const int tur = ur ? tu + 1 : t;
             seam(ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | (__popc(S00) - 1), (tur << 7) | sm.lastbase[tur]);
         }
+        flush();
     }
     __syncthreads();
 
     // -- compress: every own entry points straight at its root (the finds
     // only read, so every store here is a final root)
-    volatile uint16_t *const vpar = sm.par;
     for (int loc = 0; loc < npieces; ++loc) {
         const int id = (t << 7) | loc;
         const int root = find_root_ro<G, kCap>(vpar, id, cap, err);
@@ -501,8 +424,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         const int bit = par_index<G, kCap>(root_of(id));
         atomicOr(&sm.border[bit >> 5], 1u << (bit & 31));
     };
-    const uint32_t AL = mrow[kLH - R], BL = mrow[kLH - 1], ORL = AL | BL;
-    const uint32_t SL = ORL & ~(ORL << 1), EL = ORL & ~(ORL >> 1);
+    const uint32_t AL = mrow[kLH - R], BL = mrow[kLH - 1];
+    const uint32_t SL = band_starts<kConn8>(AL, BL), EL = band_ends<kConn8>(AL, BL);
     if (ty == 0) {
         uint32_t S = S00, E = E00;
         for (int i = 0; S; ++i) {
@@ -526,7 +449,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
-            const int np = __popc(OR & ~(OR << 1));
+            const int np = __popc(band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]));
             if (tx == 0 && (OR & 1u)) mark((t << 7) | mb);
             if (tx == G::BLX - 1 && (OR >> 31)) mark((t << 7) | (mb + np - 1));
             mb += np;
@@ -607,16 +530,18 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     for (int c = t; c < G::kBW; c += T) {
         // top row: band 0 of the lane tiles with ty == 0
         const int lt = c >> 5, bit = c & 31;
-        const uint32_t A = sm.mask[0][lt], OR = A | sm.mask[R - 1][lt];
+        const uint32_t A = sm.mask[0][lt];
         uint16_t v = kBg;
-        if ((A >> bit) & 1u) v = border_slot(value_of((lt << 7) | (__popc(OR & ~(OR << 1) & upto(bit)) - 1)));
+        if ((A >> bit) & 1u)
+            v = border_slot(value_of((lt << 7) | (__popc(band_starts<kConn8>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
         Eb[G::kEdgeTop + c] = v;
         // bottom row: the last band of the lane tiles with ty == BLY - 1
         const int lb2 = (G::BLY - 1) * G::BLX + lt;
-        const uint32_t Bl = sm.mask[kLH - 1][lb2], ORl = Bl | sm.mask[kLH - R][lb2];
+        const uint32_t Bl = sm.mask[kLH - 1][lb2];
         v = kBg;
         if ((Bl >> bit) & 1u)
-            v = border_slot(value_of((lb2 << 7) | (sm.lastbase[lb2] + __popc(ORl & ~(ORl << 1) & upto(bit)) - 1)));
+            v = border_slot(value_of(
+                (lb2 << 7) | (sm.lastbase[lb2] + __popc(band_starts<kConn8>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
         Eb[G::kEdgeBottom + c] = v;
     }
     for (int i = t; i < 2 * G::kBH; i += T) {
@@ -629,12 +554,9 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         uint16_t v = kBg;
         if (right ? (m >> 31) : (m & 1u)) {
             int base = 0;
-            for (int j = 0; j < k; ++j) {
-                const uint32_t o = sm.mask[j * R][lt] | sm.mask[j * R + R - 1][lt];
-                base += __popc(o & ~(o << 1));
-            }
-            const uint32_t o = sm.mask[k * R][lt] | sm.mask[k * R + R - 1][lt];
-            const int loc = right ? base + __popc(o & ~(o << 1)) - 1 : base;
+            for (int j = 0; j < k; ++j) base += __popc(band_starts<kConn8>(sm.mask[j * R][lt], sm.mask[j * R + R - 1][lt]));
+            const int loc = right ? base + __popc(band_starts<kConn8>(sm.mask[k * R][lt], sm.mask[k * R + R - 1][lt])) - 1
+                                  : base;
             v = border_slot(value_of((lt << 7) | loc));
         }
         Eb[(right ? G::kEdgeRight : G::kEdgeLeft) + r] = v;
@@ -660,52 +582,170 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     }
     if (err) atomicOr(&sm.err, err);
     __syncthreads();
-    if (t == 0) s.nslots[b] = sm.nslots;
-    __syncthreads();
-
-    // -- step 2: announce this block to its neighbour pairs; a pair whose
-    // other block has arrived already is merged here.  (The fence orders
-    // this CTA's records before the arrival; the second arrival fences again
-    // before it reads the first one's records.)
-    if (t < 8) {
-        unsigned owner;
-        int kind;
-        if (arrival_pair<kConn8>(t, b, bx, by, nbx, nby, owner, kind)) {
-            __threadfence();
-            if (atomicAdd(&s.arrive[(size_t)owner * 4 + kind], 1u) == 1u) {
-                __threadfence();
-                atomicOr(&sm.merges, 1 << t);
-            }
-        }
+    if (t == 0) {
+        s.nslots[b] = sm.nslots;
+        report(sm.err);
     }
-    __syncthreads();
-    const int merges = sm.merges;
-    if (merges) {
-        __threadfence();
-        int gerr = 0;
-        for (int r = 0; r < 8; ++r) {
-            if (!((merges >> r) & 1)) continue;
-            unsigned owner;
-            int kind;
-            arrival_pair<kConn8>(r, b, bx, by, nbx, nby, owner, kind);
-            merge_pair<G, kConn8>(s, sm.merge, reinterpret_cast<uint16_t *>(&sm.mask[0][0]), owner, kind, nbx, cap,
-                                  gcap, gerr, bound);
-        }
-        if (gerr) atomicOr(&sm.err, gerr);
-    }
-    __syncthreads();
-    if (t == 0) report(sm.err);
 }
 
 template <class G, bool kConn8>
-__global__ void __launch_bounds__(G::kThreads) k_block_local(JobTable jt, Scratch s, int cap, int gcap,
-                                                             uint32_t bound) {
+__global__ void __launch_bounds__(G::kThreads, (kConn8 ? 1024 : 640) / G::kThreads) k_block_local(JobTable jt, Scratch s,
+                                                                                           int cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     LocalSmem<G, kConn8> &sm = *reinterpret_cast<LocalSmem<G, kConn8> *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 0, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
-        process_local<G, kConn8>(job, lb, gb, s, sm, cap, gcap, bound);
+        process_local<G, kConn8>(job, lb, gb, s, sm, cap);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Step 2, Kernel 2 (Sec. 3.2, Eq. 1-2): each block examines the pixel pairs
+// across its top edge, its left edge and (8-connectivity) its two upper
+// corners; the right, bottom and lower corners belong to the neighbouring
+// blocks.  A pair that repeats the pair of the neighbouring pixel, or the
+// pair the thread linked last, is skipped.  The slots of the block and of the
+// blocks above and to the left are joined first in a shared-memory
+// union-find; only the pairs that join two of its sets reach the global
+// union-find, all in one round.
+template <class G>
+struct __align__(16) MergeSmem {  // (16-byte aligned: the edges are staged with 16-byte stores)
+    uint16_t up_o[G::kBW], up_p[G::kBW];  // top row of the block, bottom row of the block above
+    uint16_t lf_o[G::kBH], lf_p[G::kBH];  // left column of the block, right column of the block to the left
+    uint16_t lp[3 * G::kSlots];           // local nodes: own slots, then those above, then those to the left
+    uint32_t edge[3 * G::kSlots];         // joining pairs of local nodes: (a << 16) | b
+    int nedge;
+    ItemSlot item;
+};
+
+template <class G, bool kConn8>
+__device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
+                                              MergeSmem<G> &sm, int lcap, int gcap, uint32_t bound) {
+    constexpr int T = G::kThreads;
+    const unsigned b = gb;
+    const int nbx = job.nbx;
+    const int bx = (int)(lb % (unsigned)nbx), by = (int)(lb / (unsigned)nbx);
+    const int t = threadIdx.x;
+    const bool up = by > 0, left = bx > 0;
+    const unsigned bu = b - (unsigned)nbx, bl = b - 1u;
+    const int nso = s.nslots[b];
+    const int nsu = up ? s.nslots[bu] : 0;
+    const int nsl = left ? s.nslots[bl] : 0;
+    const uint16_t *Eo = s.edges + (size_t)b * G::kEdge;
+    int err = 0;
+
+    // stage the facing edges (16-byte loads) and set up the local union-find
+    if (up) {
+        const uint4 *src_o = reinterpret_cast<const uint4 *>(Eo + G::kEdgeTop);
+        const uint4 *src_p = reinterpret_cast<const uint4 *>(s.edges + (size_t)bu * G::kEdge + G::kEdgeBottom);
+        for (int i = t; i < G::kBW / 4; i += T) {
+            if (i < G::kBW / 8) reinterpret_cast<uint4 *>(sm.up_o)[i] = __ldg(src_o + i);
+            else reinterpret_cast<uint4 *>(sm.up_p)[i - G::kBW / 8] = __ldg(src_p + (i - G::kBW / 8));
+        }
+    }
+    if (left) {
+        const uint4 *src_o = reinterpret_cast<const uint4 *>(Eo + G::kEdgeLeft);
+        const uint4 *src_p = reinterpret_cast<const uint4 *>(s.edges + (size_t)bl * G::kEdge + G::kEdgeRight);
+        for (int i = t; i < G::kBH / 4; i += T) {
+            if (i < G::kBH / 8) reinterpret_cast<uint4 *>(sm.lf_o)[i] = __ldg(src_o + i);
+            else reinterpret_cast<uint4 *>(sm.lf_p)[i - G::kBH / 8] = __ldg(src_p + (i - G::kBH / 8));
+        }
+    }
+    const int nn = nso + nsu + nsl;
+    for (int i = t; i < nn; i += T) sm.lp[i] = (uint16_t)i;
+    if (t == 0) sm.nedge = 0;
+    __syncthreads();
+
+    uint32_t last = 0xFFFFFFFFu;
+    const auto link = [&](int na, int nb) {
+        const uint32_t q = ((uint32_t)na << 16) | (uint32_t)nb;
+        if (q == last) return;
+        last = q;
+        if (local_union(sm.lp, na, nb, lcap, err)) {
+            const int k = atomicAdd(&sm.nedge, 1);
+            if (k < 3 * G::kSlots) sm.edge[k] = q;
+        }
+    };
+    const auto ok = [](uint16_t v, int ns) { return v != kBg && (int)v < ns; };
+    if (up) {
+        // a run of consecutive columns per thread, so repeats meet the same thread
+        constexpr int kPer = (G::kBW + T - 1) / T;
+        const int j0 = t * kPer, j1 = j0 + kPer < G::kBW ? j0 + kPer : G::kBW;
+        for (int j = j0; j < j1; ++j) {
+            const uint16_t a = sm.up_o[j];
+            if (!ok(a, nso)) continue;
+            const uint16_t aL = j > 0 ? sm.up_o[j - 1] : kBg;
+            const uint16_t aR = j + 1 < G::kBW ? sm.up_o[j + 1] : kBg;
+            const uint16_t c = sm.up_p[j];
+            const uint16_t cL = j > 0 ? sm.up_p[j - 1] : kBg;
+            if (ok(c, nsu) && !(aL == a && cL == c)) link(a, nso + c);
+            if (kConn8) {
+                if (j > 0 && ok(cL, nsu) && aL != a) link(a, nso + cL);
+                if (j + 1 < G::kBW) {
+                    const uint16_t cR = sm.up_p[j + 1];
+                    if (ok(cR, nsu) && aR != a) link(a, nso + cR);
+                }
+            }
+        }
+    }
+    if (left) {
+        for (int j = t; j < G::kBH; j += T) {
+            const uint16_t a = sm.lf_o[j];
+            if (!ok(a, nso)) continue;
+            const uint16_t aU = j > 0 ? sm.lf_o[j - 1] : kBg;
+            const uint16_t aD = j + 1 < G::kBH ? sm.lf_o[j + 1] : kBg;
+            const uint16_t c = sm.lf_p[j];
+            const uint16_t cU = j > 0 ? sm.lf_p[j - 1] : kBg;
+            if (ok(c, nsl) && !(aU == a && cU == c)) link(a, nso + nsu + c);
+            if (kConn8) {
+                if (j > 0 && ok(cU, nsl) && aU != a) link(a, nso + nsu + cU);
+                if (j + 1 < G::kBH) {
+                    const uint16_t cD = sm.lf_p[j + 1];
+                    if (ok(cD, nsl) && aD != a) link(a, nso + nsu + cD);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // the joining pairs, then the two corner pairs (8-connectivity)
+    const auto slot_of = [&](int node) -> uint32_t {
+        if (node < nso) return b * (uint32_t)G::kSlots + (uint32_t)node;
+        if (node < nso + nsu) return bu * (uint32_t)G::kSlots + (uint32_t)(node - nso);
+        return bl * (uint32_t)G::kSlots + (uint32_t)(node - nso - nsu);
+    };
+    const int ne = sm.nedge < 3 * G::kSlots ? sm.nedge : 3 * G::kSlots;
+    for (int i = t; i < ne; i += T) {
+        const uint32_t e = sm.edge[i];
+        union_global(s.P, slot_of((int)(e >> 16)), slot_of((int)(e & 0xFFFFu)), gcap, err, bound);
+    }
+    if (kConn8 && up) {
+        if (t == T - 1 && left) {
+            const unsigned bd = bu - 1u;
+            const uint16_t a = sm.up_o[0], d = s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom + G::kBW - 1];
+            if (ok(a, nso) && ok(d, s.nslots[bd]))
+                union_global(s.P, b * (uint32_t)G::kSlots + a, bd * (uint32_t)G::kSlots + d, gcap, err, bound);
+        }
+        if (t == T - 2 && bx + 1 < nbx) {
+            const unsigned bd = bu + 1u;
+            const uint16_t a = sm.up_o[G::kBW - 1], d = s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom];
+            if (ok(a, nso) && ok(d, s.nslots[bd]))
+                union_global(s.P, b * (uint32_t)G::kSlots + a, bd * (uint32_t)G::kSlots + d, gcap, err, bound);
+        }
+    }
+    report(err);
+}
+
+template <class G, bool kConn8>
+__global__ void __launch_bounds__(G::kThreads) k_block_merge(JobTable jt, Scratch s, int lcap, int gcap,
+                                                             uint32_t bound) {
+    __shared__ MergeSmem<G> sm;
+    for (unsigned iter = 0; claim_item(jt, 1, iter, sm.item); ++iter) {
+        const Job &job = sm.item.job;
+        const unsigned lb = sm.item.lb, gb = sm.item.gb;
+        process_merge<G, kConn8>(job, lb, gb, s, sm, lcap, gcap, bound);
         __syncthreads();
     }
 }
@@ -763,8 +803,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     int npieces = 0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
-        const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
-        npieces += __popc(OR & ~(OR << 1));
+        npieces += __popc(band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]));
     }
     const int nchunks = (npieces + 7) >> 3;
     uint4 vq = nchunks > 0 ? vin[0] : make_uint4(0, 0, 0, 0);
@@ -775,8 +814,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         // each lane tile: one label per piece of its band k, at the piece start
-        const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
-        uint32_t S = OR & ~(OR << 1);
+        uint32_t S = band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]);
         while (S) {
             const int a0 = lobit(S);
             S &= S - 1u;
@@ -808,7 +846,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
             const uint32_t ma = sm.mask[k * R][ry * G::BLX + ctx];
             const uint32_t mbm = sm.mask[k * R + R - 1][ry * G::BLX + ctx];
             const uint32_t mo = ma | mbm;
-            const uint32_t SS = mo & ~(mo << 1);
+            const uint32_t SS = band_starts<kConn8>(ma, mbm);
             int lab[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -841,7 +879,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
 template <class G, bool kConn8>
 __global__ void __launch_bounds__(G::kThreads) k_block_write(JobTable jt, Scratch s, int cap, uint32_t bound) {
     __shared__ WriteSmem<G> sm;
-    for (unsigned iter = 0; claim_item(jt, 1, iter, sm.item); ++iter) {
+    for (unsigned iter = 0; claim_item(jt, 2, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
         process_write<G, kConn8>(job, lb, gb, s, sm, cap, bound);
@@ -861,7 +899,7 @@ namespace {
 size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t masks, vstream, edges, P, nslots, arrive, total;
+    size_t masks, vstream, edges, P, nslots, total;
 };
 
 template <class G>
@@ -873,7 +911,6 @@ Layout layout_for(size_t nb) {
     l.edges = off;   off += up256(nb * G::kEdge * sizeof(uint16_t));
     l.P = off;       off += up256(nb * G::kSlots * sizeof(uint64_t));
     l.nslots = off;  off += up256(nb * sizeof(int32_t));
-    l.arrive = off;  off += up256(nb * 4 * sizeof(uint32_t));
     l.total = off;
     return l;
 }
@@ -888,7 +925,6 @@ Scratch carve(void *ws, size_t nb) {
     s.edges = reinterpret_cast<uint16_t *>(p + l.edges);
     s.P = reinterpret_cast<uint64_t *>(p + l.P);
     s.nslots = reinterpret_cast<int32_t *>(p + l.nslots);
-    s.arrive = reinterpret_cast<uint32_t *>(p + l.arrive);
     return s;
 }
 
@@ -1001,7 +1037,7 @@ int timing_read(double *ms, long long *count, int n) {
 }
 
 const char *kernel_kind_name(int k) {
-    static const char *names[kKernelKinds] = {"k_block_local", "k_block_write"};
+    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
 }
 
@@ -1014,7 +1050,7 @@ namespace {
 struct GeoLaunch {
     bool ready = false;
     int sms = 0;
-    int occ_local[2] = {0, 0}, occ_write[2] = {0, 0};  // [conn8]
+    int occ_local[2] = {0, 0}, occ_merge[2] = {0, 0}, occ_write[2] = {0, 0};  // [conn8]
 };
 
 template <class G, bool kConn8>
@@ -1025,10 +1061,13 @@ bool geo_launch_conn(int dev, GeoLaunch &g) {
         return false;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_local[kConn8], k_block_local<G, kConn8>,
                                                       G::kThreads, bytes) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_merge[kConn8], k_block_merge<G, kConn8>,
+                                                      G::kThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g.occ_write[kConn8], k_block_write<G, kConn8>,
                                                       G::kThreads, 0) != cudaSuccess)
         return false;
     g.occ_local[kConn8] = std::max(1, g.occ_local[kConn8]);
+    g.occ_merge[kConn8] = std::max(1, g.occ_merge[kConn8]);
     g.occ_write[kConn8] = std::max(1, g.occ_write[kConn8]);
     (void)dev;
     return true;
@@ -1061,22 +1100,22 @@ void caps_for(size_t nb, int cap, int &local_cap, int &global_cap, uint32_t &bou
     bound = (uint32_t)slots;
 }
 
-// The arrival counters of the neighbour pairs start at zero in every launch;
-// then the labelling kernel (steps 1 and 2) and the write-out (step 3).
+// The labelling kernel (step 1), the merge (step 2) and the write-out (step 3).
 template <class G>
-int launch_table(int conn, const JobTable &jt, size_t nb, unsigned grid_local, unsigned grid_write,
+int launch_table(int conn, const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
                  const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream) {
-    if (cudaMemsetAsync(s.arrive, 0, nb * 4 * sizeof(uint32_t), stream) != cudaSuccess) return -1;
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, true>), stream>>>(
-            jt, s, local_cap, global_cap, bound);
+        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, true>), stream>>>(jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
+        k_block_merge<G, true><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
+        ev = timing_mark(stream, ev, kKindMerge);
         k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     } else {
-        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, false>), stream>>>(
-            jt, s, local_cap, global_cap, bound);
+        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, false>), stream>>>(jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
+        k_block_merge<G, false><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
+        ev = timing_mark(stream, ev, kKindMerge);
         k_block_write<G, false><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     }
     ev = timing_mark(stream, ev, kKindWrite);
@@ -1106,8 +1145,8 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
     int local_cap, global_cap;
     uint32_t bound;
     caps_for<G>(nb, cap, local_cap, global_cap, bound);
-    return launch_table<G>(conn, jt, nb, (unsigned)nb, (unsigned)nb, carve<G>(ws, nb), local_cap, global_cap,
-                           bound, stream);
+    return launch_table<G>(conn, jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve<G>(ws, nb), local_cap,
+                           global_cap, bound, stream);
 }
 
 template <class G>
@@ -1123,7 +1162,7 @@ int launch_batch(int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t cap
     uint32_t bound;
     caps_for<G>(capacity, cap, local_cap, global_cap, bound);
     const int c8 = conn == 8 ? 1 : 0;
-    return launch_table<G>(conn, jt, capacity, (unsigned)(gl.sms * gl.occ_local[c8]),
+    return launch_table<G>(conn, jt, (unsigned)(gl.sms * gl.occ_local[c8]), (unsigned)(gl.sms * gl.occ_merge[c8]),
                            (unsigned)(gl.sms * gl.occ_write[c8]), carve<G>(ws, capacity), local_cap, global_cap,
                            bound, stream);
 }
