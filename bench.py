@@ -18,7 +18,9 @@ The JSON line carries, besides the contract keys:
                 copies inside the timed region);
   clocks        SM clocks and throttle reasons sampled during the timed region;
   extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
-                between repetitions) with its per-kernel breakdown.
+                between repetitions) with its per-kernel breakdown; the
+                256-image uneven batch (batched graph vs plain launches); the
+                serving stream at 2k/5k/10k requests/s (p50/p99, Gpixel/s).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 """
@@ -319,6 +321,11 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
 
+    # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
+    # frames through the continuous-batching server)
+    if rank == 0 and not args.no_extra:
+        line.setdefault("extra", {})["serving"] = bench_serving(torch, ccl, args.serving_seconds)
+
     # -- e2e through host buffers (copies inside the timed region)
     if not args.no_e2e:
         line["e2e"] = bench_e2e(torch, ccl, host, work, args, world, max_over_ranks)
@@ -424,6 +431,64 @@ def bench_batched(torch, ccl, hbm_gbs):
             "device_status": ccl.ccl_status_string(status)}
 
 
+def bench_serving(torch, ccl, seconds, rates=(2000, 5000, 10000), warm=0.5):
+    """Serving stream: Poisson arrivals (exponential gaps, seeded per rate) of
+    frames 640x480 (50%), 1920x1080 (35%), 3840x2160 (15%), sigma=6 smoothed
+    noise at density 0.3..0.6 whose blobs move 1-4 px per frame, 8-connectivity,
+    submitted from pinned host memory to ``CclServer`` (copies in both
+    directions are part of every request).  Frames are generated before the
+    clock starts.  After `warm` seconds the server's statistics are reset;
+    p50/p99/max are submit -> labels in host memory, Gpixel/s is delivered
+    pixels over the span from the first counted submission to the last
+    completion."""
+    from paper_1712_09789_gb300 import synth
+
+    frames = synth.serving_frames(128, n_streams=4, seed=0)
+    host = [torch.from_numpy(f).pin_memory() for f in frames]
+    outs = [torch.empty(f.shape, dtype=torch.int32).pin_memory() for f in frames]
+    hv = [h.numpy() for h in host]
+    ov = [o.numpy() for o in outs]
+    mean_px = sum(f.size for f in frames) / len(frames)
+    res = {"workload": "Poisson arrivals of 640x480/1920x1080/3840x2160 frames (50/35/15%), smoothed noise "
+                       "sigma=6 density 0.3-0.6, 8-connectivity, host frames in pinned memory",
+           "seconds_per_rate": seconds, "pool_frames": len(frames), "mean_frame_px": mean_px, "rates": {}}
+    with ccl.CclServer(max_slots=64, n_streams=4, max_batch=32, hbm_budget_bytes=8 << 30) as srv:
+        for i in range(len(frames)):       # warm the server, its graphs and the autotuner
+            srv.wait(srv.submit(hv[i], ov[i], 8))
+        for rate in rates:
+            arr = synth.poisson_arrivals(rate, warm + seconds, seed=rate)
+            owner = [None] * len(frames)
+            t0 = time.perf_counter()
+            reset = False
+            late = 0
+            for i, ta in enumerate(arr):
+                if not reset and ta >= warm:
+                    srv.reset_stats()
+                    reset = True
+                while True:
+                    now = time.perf_counter() - t0
+                    if now >= ta:
+                        break
+                    if ta - now > 2e-4:
+                        time.sleep(ta - now - 1e-4)
+                if now - ta > 1e-3:
+                    late += 1
+                j = i % len(frames)
+                if owner[j] is not None:
+                    srv.wait(owner[j])     # the buffer's previous request is still out
+                owner[j] = srv.submit(hv[j], ov[j], 8)
+            for tk in owner:
+                if tk is not None:
+                    srv.wait(tk)
+            st = srv.stats()
+            res["rates"][str(rate)] = {
+                "offered_gpixel_s": rate * mean_px / 1e9, "requests": int(st["completed"]),
+                "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
+                "delivered_gpixel_s": st["gpixel_s"], "rejected": int(st["rejected"]),
+                "late_submissions": late}
+    return res
+
+
 def bench_e2e(torch, ccl, host, work, args, world, max_over_ranks):
     import numpy as np
 
@@ -482,6 +547,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
