@@ -143,6 +143,22 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def max_over_ranks_tensor(torch, v: float, world: int, device) -> float:
+    """Largest `v` over all ranks (the step time every rank waited for)."""
+    if world == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(world: int, px_per_rank_step: int, steps: int, ms_max: float) -> float:
+    """Whole-job Gpixel/s: every rank labels its own copy of the step's work
+    (independent images, no collective on the data path), timed by the
+    slowest rank."""
+    return world * px_per_rank_step * steps / (ms_max / 1e3) / 1e9
+
+
 def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,11 +247,7 @@ def run_ours(args):
             torch.distributed.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_tensor(torch, v, world, "cuda")
 
     named = noise_4096_images()
     host = [img for _, img in named]
@@ -276,7 +288,7 @@ def run_ours(args):
     if status != ccl.CCL_OK:
         raise RuntimeError(f"device status after timed region: {ccl.ccl_status_string(status)}")
     ms = max_over_ranks(e0.elapsed_time(e1))
-    value = world * px_step * args.steps / (ms / 1e3) / 1e9
+    value = weak_scaling_value(world, px_step, args.steps, ms)
 
     hbm_gbs, peak_kind, _ = load_peaks()
     total_kernel_ms = sum(v[0] for v in ktimes.values()) or 1.0
