@@ -37,6 +37,7 @@ constexpr int kLH = 8;                  // lane tile height (rows of a thread)
 constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile: at most 32 per two-row band
 constexpr int kVChunksMax = kPieceCapMax / 8;  // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
+constexpr uint16_t kBorderRoot = 0x4000;  // entry of a root once its border slot is known: kBorderRoot | slot
 constexpr uint16_t kBg = 0xFFFF;
 constexpr uint16_t kBorderFlag = 0x8000;  // per-piece value: border slot, else block key
 constexpr unsigned kFull = 0xFFFFFFFFu;

@@ -501,27 +501,27 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             uint32_t bits = sm.border[word];
             uint32_t slot = sm.prefix[word];
             for (; bits && slot < (uint32_t)G::kSlots; bits &= bits - 1, ++slot) {
-                const int key = vpar[word * 32 + lobit(bits)] & 0x7FFF;
+                const int at = word * 32 + lobit(bits);
+                const int key = vpar[at] & 0x7FFF;
                 const uint32_t g = (uint32_t)(y0 + (key >> G::kBWLog2)) * (uint32_t)W +
                                    (uint32_t)(x0 + (key & (G::kBW - 1)));
                 s.P[sbase + slot] = pack_slot(g, sbase + slot);
+                // from here on the root's entry is its slot (kBorderRoot | slot)
+                vpar[at] = (uint16_t)(kBorderRoot | slot);
             }
         }
     }
+    __syncthreads();
     // value every piece carries from now on: kBorderFlag | slot of its root,
     // or the block key of its root
     const auto value_of = [&](int id) -> uint16_t {
-        const uint16_t e = vpar[par_index<G, kCap>(id)];
-        const int root = (e & kRoot) ? id : (int)e;
-        const uint16_t re = (e & kRoot) ? e : vpar[par_index<G, kCap>(root)];
+        uint16_t e = vpar[par_index<G, kCap>(id)];
+        if (e < kBorderRoot) e = vpar[par_index<G, kCap>(e)];  // a piece: its entry names the root
+        if (e & kRoot) return (uint16_t)(e & 0x7FFF);
         // still a pointer only when an iteration cap cut the merges short
         // (the error word is set then); decode it as block key 0
-        if (!(re & kRoot)) return 0;
-        const int bit = par_index<G, kCap>(root);
-        const uint32_t word = sm.border[bit >> 5];
-        if ((word >> (bit & 31)) & 1u)
-            return (uint16_t)(kBorderFlag | (sm.prefix[bit >> 5] + __popc(word & ((1u << (bit & 31)) - 1u))));
-        return (uint16_t)(re & 0x7FFF);
+        if (!(e & kBorderRoot)) return 0;
+        return (uint16_t)(kBorderFlag | (e & 0x3FFF));
     };
 
     // -- border record of the block: the slot of every border pixel, one
