@@ -263,6 +263,20 @@ size_t ccl_noalloc_max_workspace_bytes(void);
 ccl_status ccl_get_device_status(void *stream);
 
 /*
+ * Coarse-labelling variants of Sec. 4.2, for the paper's comparison of the
+ * coarse-to-fine strategy: variant 0 is the method (C2FL, what ccl_label
+ * computes), 1 keeps the coarse labelling along rows only (RC2FL), 2 along
+ * columns only (CC2FL), 3 drops it (NC2FL: the refinement does all merging).
+ * All four write the same canonical labels.  Runs on 512x64 blocks with
+ * library-owned scratch (as ccl_label).  When `counters` is not NULL the call
+ * is synchronous and writes 3 counts of step 1 (Kernel 1) over the image:
+ * [0] merges (list unions), [1] root-walk steps, [2] atomic CAS attempts.
+ * Arguments as ccl_label; variant outside 0..3 -> CCL_ERR_INVALID_ARG.
+ */
+ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int connectivity, int variant,
+                             int32_t *labels, unsigned long long *counters, void *stream);
+
+/*
  * Test hook for failure detection: caps every find/union loop in the kernels
  * at `cap` iterations (cap <= 0 restores the default, which no valid input
  * can reach).  A low cap makes the loops give up, set the device error word

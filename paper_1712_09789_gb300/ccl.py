@@ -77,6 +77,8 @@ _SIGS = {
     "ccl_label_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
                                      _c.c_void_p]),
     "ccl_noalloc_max_workspace_bytes": (_c.c_size_t, []),
+    "ccl_label_variant": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_int, _c.c_void_p,
+                                     _c.POINTER(_c.c_ulonglong), _c.c_void_p]),
     "ccl_label_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p]),
     "ccl_label_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_int, _c.c_void_p]),
     "ccl_autotune_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p,
@@ -187,6 +189,26 @@ def ccl_label_noalloc(img, connectivity: int = 8, labels=None, stream=None):
     st = load().ccl_label_noalloc(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                                   _stream_ptr(stream, img.device))
     _check(st, "ccl_label_noalloc")
+    return labels
+
+
+VARIANTS = ("C2FL", "RC2FL", "CC2FL", "NC2FL")
+
+
+def ccl_label_variant(img, connectivity: int = 8, variant: int = 0, labels=None, stream=None,
+                      counters: bool = False):
+    """One of the coarse-labelling variants of Sec. 4.2 (``ccl_label_variant``):
+    0 C2FL (the method), 1 RC2FL, 2 CC2FL, 3 NC2FL; all give the same labels.
+    With ``counters`` the call is synchronous and also returns the counts of
+    step 1: {"merges", "find_steps", "atomics"}."""
+    H, W, pitch = _image_args(img)
+    labels = _labels_for(img, labels)
+    cnt = (ctypes.c_ulonglong * 3)()
+    st = load().ccl_label_variant(img.data_ptr(), H, W, pitch, connectivity, variant, labels.data_ptr(),
+                                  cnt if counters else None, _stream_ptr(stream, img.device))
+    _check(st, "ccl_label_variant")
+    if counters:
+        return labels, {"merges": cnt[0], "find_steps": cnt[1], "atomics": cnt[2]}
     return labels
 
 

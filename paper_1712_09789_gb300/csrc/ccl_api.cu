@@ -150,6 +150,44 @@ ccl_status ccl_label(const uint8_t *img, int H, int W, size_t pitch, int connect
     return CCL_OK;
 }
 
+ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int connectivity, int variant,
+                             int32_t *labels, unsigned long long *counters, void *stream) {
+    if (variant < 0 || variant > 3) return CCL_ERR_INVALID_ARG;
+    ccl_status st = check_image_args(img, H, W, pitch, connectivity, labels);
+    if (st != CCL_OK) return st;
+    if (counters) {
+        unsigned long long tmp[3];
+        if (cudaDeviceSynchronize() != cudaSuccess || ccl::variant_counters(tmp, true) != 0) return CCL_ERR_CUDA;
+    }
+    if (H > 0 && W > 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        const size_t need = ccl::variant_workspace_bytes(H, W);
+        void *ws = nullptr;
+        int cap = 0;
+        {
+            std::lock_guard<std::mutex> lk(g_mu);
+            DevBuf &b = g_scratch[{dev, s}];
+            if (b.bytes < need) {
+                if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+                st = grow(b, need);
+                if (st != CCL_OK) return st;
+            }
+            ws = b.ptr;
+            cap = g_cap;
+        }
+        if (ccl::launch_label_variant(img, H, W, pitch, connectivity, variant, labels, ws, s, cap) != 0)
+            return CCL_ERR_CUDA;
+    }
+    if (counters) {
+        if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+            ccl::variant_counters(counters, false) != 0)
+            return CCL_ERR_CUDA;
+    }
+    return CCL_OK;
+}
+
 ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,
                           int32_t *host_labels, void *stream) {
     ccl_status st = check_image_args(host_img, H, W, pitch, connectivity, host_labels);

@@ -143,6 +143,29 @@ __device__ __forceinline__ uint32_t band_ends(uint32_t A, uint32_t B) {
     return (A | B) & ~band_link<kConn8>(A, B);
 }
 
+// Coarse-labelling variants of Sec. 4.2: C2FL (0, the method), RC2FL (1,
+// coarse labelling along rows only), CC2FL (2, along columns only), NC2FL (3,
+// neither; the refinement does all the merging).  Along rows: the elements of
+// a band are its pieces (else every occupied column of a band is an element
+// of its own, and the links between neighbouring columns are refined).  Along
+// columns: an element takes the first element above it that it touches as
+// parent (else every contact with the band above is refined).
+template <bool kConn8, int kMode>
+struct Variant {
+    static constexpr bool kRow = kMode == 0 || kMode == 1;
+    static constexpr bool kCol = kMode == 0 || kMode == 2;
+    static constexpr int kCap = ((kConn8 && kRow) ? 16 : 32) * (kLH / 2);  // elements per lane tile
+};
+
+template <bool kConn8, bool kRow>
+__device__ __forceinline__ uint32_t elem_starts(uint32_t A, uint32_t B) {
+    return kRow ? band_starts<kConn8>(A, B) : (A | B);
+}
+template <bool kConn8, bool kRow>
+__device__ __forceinline__ uint32_t elem_ends(uint32_t A, uint32_t B) {
+    return kRow ? band_ends<kConn8>(A, B) : (A | B);
+}
+
 // Last column of the piece (run of `ends`' mask) holding column u.
 __device__ __forceinline__ int piece_end(uint32_t ends, int u) { return u + lobit(ends >> u); }
 
@@ -159,8 +182,10 @@ __device__ __forceinline__ int par_index(int id) {
 // entries, and links are only ever made on roots (by CAS), so the two never
 // overwrite each other.
 template <class G, int kCap>
-__device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t &rentry, int cap, int &err) {
+__device__ __forceinline__ int find_root(volatile uint16_t *par, int x, uint16_t &rentry, int cap, int &err,
+                                         unsigned *ops = nullptr) {
     for (int i = 0; i < cap; ++i) {
+        if (ops) ++ops[1];
         const uint16_t e = par[par_index<G, kCap>(x)];
         if (e & kRoot) { rentry = e; return x; }
         const uint16_t g = par[par_index<G, kCap>(e)];
@@ -192,10 +217,12 @@ __device__ __forceinline__ int find_root_ro(const volatile uint16_t *par, int x,
 // tile and no other thread reads or writes its entries yet: plain finds and
 // a plain store, the root with the larger key hung under the other.
 template <class G, int kCap>
-__device__ __forceinline__ void union_private(uint16_t *par, int a, int b, int cap, int &err) {
+__device__ __forceinline__ void union_private(uint16_t *par, int a, int b, int cap, int &err,
+                                              unsigned *ops = nullptr) {
     uint16_t ea, eb;
-    a = find_root<G, kCap>(par, a, ea, cap, err);
-    b = find_root<G, kCap>(par, b, eb, cap, err);
+    if (ops) ++ops[0];
+    a = find_root<G, kCap>(par, a, ea, cap, err, ops);
+    b = find_root<G, kCap>(par, b, eb, cap, err, ops);
     if (a == b) return;
     if ((ea & 0x7FFF) < (eb & 0x7FFF)) par[par_index<G, kCap>(b)] = (uint16_t)a;
     else par[par_index<G, kCap>(a)] = (uint16_t)b;
@@ -207,14 +234,16 @@ __device__ __forceinline__ void union_private(uint16_t *par, int a, int b, int c
 // changed meanwhile; the round repeats until no lane needs another, so the
 // warp stays converged between rounds.
 template <class G, int kCap>
-__device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int a, int b, int cap, int &err) {
+__device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int a, int b, int cap, int &err,
+                                                 unsigned *ops = nullptr) {
     volatile uint16_t *vp = par;
     bool pend = valid;
+    if (ops && valid) ++ops[0];
     for (int i = 0; __any_sync(kFull, pend); ++i) {
         if (pend) {
             uint16_t ea, eb;
-            a = find_root<G, kCap>(vp, a, ea, cap, err);
-            b = find_root<G, kCap>(vp, b, eb, cap, err);
+            a = find_root<G, kCap>(vp, a, ea, cap, err, ops);
+            b = find_root<G, kCap>(vp, b, eb, cap, err, ops);
             if (a == b || err) {
                 pend = false;
             } else {
@@ -222,6 +251,7 @@ __device__ __forceinline__ void union_block_sync(uint16_t *par, bool valid, int 
                     const int t = a; a = b; b = t;
                     const uint16_t u = ea; ea = eb; eb = u;
                 }
+                if (ops) ++ops[2];
                 const unsigned short old = atomicCAS(reinterpret_cast<unsigned short *>(par + par_index<G, kCap>(a)),
                                                      (unsigned short)ea, (unsigned short)b);
                 if (old == ea) pend = false;

@@ -67,6 +67,15 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap);
 
+// The coarse-labelling variants of Sec. 4.2 (mode 0 C2FL, 1 RC2FL, 2 CC2FL,
+// 3 NC2FL) with counters, on 512x64 blocks; scratch of
+// variant_workspace_bytes(H, W).  variant_counters reads the accumulated
+// merges, find steps and CAS attempts of step 1 (and clears them if asked).
+size_t variant_workspace_bytes(int H, int W);
+int launch_label_variant(const uint8_t *img, int H, int W, size_t pitch, int conn, int mode, int32_t *labels,
+                         void *ws, cudaStream_t stream, int cap);
+int variant_counters(unsigned long long *out, bool reset);
+
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
 

@@ -43,6 +43,9 @@
 namespace ccl {
 
 __device__ int g_device_error = 0;
+// Counters of the coarse-labelling variants (merges, find steps, CAS
+// attempts of step 1), accumulated by the counting instantiations only.
+__device__ unsigned long long g_variant_ops[3];
 
 // Per-block scratch regions, indexed by the global block (item) index; sized
 // for capacity, only the used parts are touched.
@@ -130,9 +133,9 @@ __device__ __forceinline__ bool local_union(uint16_t *lp, int a, int b, int cap,
 }
 
 // ---------------------------------------------------------------------------
-template <class G, bool kConn8>
+template <class G, int kCap_>
 struct LocalSmem {
-    static constexpr int kCap = Bands<kConn8>::kCap;
+    static constexpr int kCap = kCap_;
     static constexpr int kWords = kCap * G::kThreads / 32;  // bitmap words over all entries
     uint16_t par[kCap * G::kThreads];  // list entries, see ccl_block.cuh
     uint32_t mask[kLH][G::kThreads];   // row masks
@@ -175,11 +178,12 @@ struct HalfQueue {
     __device__ __forceinline__ uint4 bits() const { return make_uint4(q0, q1, q2, q3); }
 };
 
-template <class G, bool kConn8>
+template <class G, bool kConn8, int kMode, bool kCount>
 __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
-                                              LocalSmem<G, kConn8> &sm, int cap) {
+                                              LocalSmem<G, Variant<kConn8, kMode>::kCap> &sm, int cap) {
     using Bd = Bands<kConn8>;
-    constexpr int kCap = Bd::kCap;
+    using V = Variant<kConn8, kMode>;
+    constexpr int kCap = V::kCap;
     constexpr int R = Bd::kRows;
     constexpr int NB = Bd::kN;
     constexpr int T = G::kThreads;
@@ -197,9 +201,11 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     const int tx = t & (G::BLX - 1), ty = t >> G::kBLXLog2;
     const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
     int err = 0;
+    unsigned cnt[3] = {0u, 0u, 0u};
+    unsigned *const ops = kCount ? cnt : nullptr;
 
     if (t == 0) sm.err = 0;
-    for (int i = t; i < LocalSmem<G, kConn8>::kWords; i += T) sm.border[i] = 0u;
+    for (int i = t; i < LocalSmem<G, kCap>::kWords; i += T) sm.border[i] = 0u;
 
     // -- initialization: the lane tile's 8 rows as masks (all loads in flight
     // at once; pixels outside the image are background)
@@ -241,14 +247,27 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     int base_prev = 0, npieces = 0;
     {
         uint32_t pB = 0u, pS = 0u, pE = 0u;  // band above: lower row, piece starts, piece ends
+        // queue of a band's further contacts; a full queue (16 entries) is
+        // merged by its thread on the spot
+        int nq = 0;
+        const auto push = [&](int a, int b) {
+            if (nq == 16) {
+                for (int j = 0; j < 16; ++j) {
+                    const int q = sm.xq[j][t];
+                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err, ops);
+                }
+                nq = 0;
+            }
+            sm.xq[nq++][t] = (uint16_t)((a << 7) | b);
+        };
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1];
-            const uint32_t S0 = band_starts<kConn8>(A, Bm), E0 = band_ends<kConn8>(A, Bm);
+            const uint32_t S0 = elem_starts<kConn8, V::kRow>(A, Bm), E0 = elem_ends<kConn8, V::kRow>(A, Bm);
             uint32_t S = S0, E = E0;
             const int nk = __popc(S0);
             const int nmax = __reduce_max_sync(kFull, nk);
-            int nq = 0;
+            nq = 0;
             for (int i = 0; i < nmax; ++i) {
                 const int a0 = lobit(S | 0x80000000u), a1 = lobit(E | 0x80000000u);
                 S &= S - 1u;
@@ -261,31 +280,33 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const int u0 = lobit(P | 0x80000000u);
                 const int up = P ? base_prev + __popc(pS & upto(u0)) - 1 : 0;
                 const uint16_t ue = par[up * T + t];
-                const uint16_t ent = P ? ((ue & kRoot) ? (uint16_t)((t << 7) | up) : ue)
-                                       : (uint16_t)(kRoot | piece_key<G>(tx, ty, k, A, rb, a0));
+                const uint16_t ent = (V::kCol && P) ? ((ue & kRoot) ? (uint16_t)((t << 7) | up) : ue)
+                                                    : (uint16_t)(kRoot | piece_key<G>(tx, ty, k, A, rb, a0));
                 if (act) par[(npieces + i) * T + t] = ent;
-                uint32_t P2 = P ? (P & ~upto(piece_end(pE, u0))) : 0u;
                 // (a piece above is a further contact of at most one piece of
-                // the band, the leftmost that touches it; a full queue, which
-                // takes 16 of them, is merged by its thread on the spot)
+                // the band, the leftmost that touches it)
+                uint32_t P2 = P ? (V::kCol ? (P & ~upto(piece_end(pE, u0))) : P) : 0u;
                 while (P2) {
                     const int u = lobit(P2);
-                    if (nq == 16) {
-                        for (int j = 0; j < 16; ++j) {
-                            const int q = sm.xq[j][t];
-                            union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err);
-                        }
-                        nq = 0;
-                    }
-                    sm.xq[nq++][t] = (uint16_t)(((npieces + i) << 7) | (base_prev + __popc(pS & upto(u)) - 1));
+                    push(npieces + i, base_prev + __popc(pS & upto(u)) - 1);
                     P2 &= ~upto(piece_end(pE, u));
+                }
+            }
+            if (!V::kRow) {
+                // without coarse labelling along rows, the links between the
+                // band's occupied columns are refined like any other contact
+                uint32_t L = band_link<kConn8>(A, Bm);
+                for (; L; L &= L - 1u) {
+                    const int c = lobit(L);
+                    const int e = npieces + __popc(S0 & upto(c)) - 1;
+                    push(e + 1, e);
                 }
             }
             const int nqmax = __reduce_max_sync(kFull, nq);
             for (int j = 0; j < nqmax; ++j) {
                 if (j < nq) {
                     const int q = sm.xq[j][t];
-                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err);
+                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err, ops);
                 }
             }
             base_prev = npieces;
@@ -327,7 +348,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         for (int j = 0; j < m; ++j) {
             const bool v = j < nsq;
             const uint32_t q = v ? sq[j * T + t] : 0u;
-            union_block_sync<G, kCap>(par, v, (int)(q >> 16), (int)(q & 0xFFFFu), cap, err);
+            union_block_sync<G, kCap>(par, v, (int)(q >> 16), (int)(q & 0xFFFFu), cap, err, ops);
         }
         nsq = 0;
     };
@@ -343,8 +364,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             room(3);
             const uint32_t A = mrow[k * R], Bm = mrow[k * R + R - 1];
             const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl];
-            const int np = __popc(band_starts<kConn8>(A, Bm));
-            const int lnp = __popc(band_starts<kConn8>(lA, lB));
+            const int np = __popc(elem_starts<kConn8, V::kRow>(A, Bm));
+            const int lnp = __popc(elem_starts<kConn8, V::kRow>(lA, lB));
             const int me_first = (t << 7) | mb;
             const int l_last = (tl << 7) | (lbase + lnp - 1);
             // column 0 of my band k beside column 31 of the left band k
@@ -354,7 +375,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const uint32_t nA = mrow[(k + 1) * R];
                 const uint32_t lnA = sm.mask[(k + 1) * R][tl];
                 const int l_next_last =
-                    (tl << 7) | (lbase + lnp + __popc(band_starts<kConn8>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
+                    (tl << 7) | (lbase + lnp + __popc(elem_starts<kConn8, V::kRow>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
                 // lower row of my band k, column 0 ~ upper row of the left band k+1, column 31
                 seam(hasl && (Bm & 1u) && (lnA >> 31), me_first, l_next_last);
                 // upper row of my band k+1, column 0 ~ lower row of the left band k, column 31
@@ -365,12 +386,12 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         }
     }
     const uint32_t A0 = mrow[0];
-    const uint32_t S00 = band_starts<kConn8>(A0, mrow[R - 1]), E00 = band_ends<kConn8>(A0, mrow[R - 1]);
+    const uint32_t S00 = elem_starts<kConn8, V::kRow>(A0, mrow[R - 1]), E00 = elem_ends<kConn8, V::kRow>(A0, mrow[R - 1]);
     {
         const bool hasu = ty > 0;
         const int tu = hasu ? t - G::BLX : t;
         const uint32_t uA = sm.mask[kLH - R][tu], uB = sm.mask[kLH - 1][tu];
-        const uint32_t uS = band_starts<kConn8>(uA, uB), uE = band_ends<kConn8>(uA, uB);
+        const uint32_t uS = elem_starts<kConn8, V::kRow>(uA, uB), uE = elem_ends<kConn8, V::kRow>(uA, uB);
         const int ubase = sm.lastbase[tu];
         uint32_t S = hasu ? S00 : 0u;
         uint32_t E = hasu ? E00 : 0u;
@@ -397,7 +418,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const int tul = ul ? tu - 1 : t;
             const uint32_t ulB = sm.mask[kLH - 1][tul];
             seam(ul && (ulB >> 31), t << 7,
-                 (tul << 7) | (sm.lastbase[tul] + __popc(band_starts<kConn8>(sm.mask[kLH - 2][tul], ulB)) - 1));
+                 (tul << 7) | (sm.lastbase[tul] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - 2][tul], ulB)) - 1));
             const bool ur = hasu && tx + 1 < G::BLX && (A0 >> 31);
             const int tur = ur ? tu + 1 : t;
             seam(ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | (__popc(S00) - 1), (tur << 7) | sm.lastbase[tur]);
@@ -425,7 +446,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         atomicOr(&sm.border[bit >> 5], 1u << (bit & 31));
     };
     const uint32_t AL = mrow[kLH - R], BL = mrow[kLH - 1];
-    const uint32_t SL = band_starts<kConn8>(AL, BL), EL = band_ends<kConn8>(AL, BL);
+    const uint32_t SL = elem_starts<kConn8, V::kRow>(AL, BL), EL = elem_ends<kConn8, V::kRow>(AL, BL);
     if (ty == 0) {
         uint32_t S = S00, E = E00;
         for (int i = 0; S; ++i) {
@@ -449,7 +470,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 #pragma unroll
         for (int k = 0; k < NB; ++k) {
             const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
-            const int np = __popc(band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]));
+            const int np = __popc(elem_starts<kConn8, V::kRow>(mrow[k * R], mrow[k * R + R - 1]));
             if (tx == 0 && (OR & 1u)) mark((t << 7) | mb);
             if (tx == G::BLX - 1 && (OR >> 31)) mark((t << 7) | (mb + np - 1));
             mb += np;
@@ -533,7 +554,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         const uint32_t A = sm.mask[0][lt];
         uint16_t v = kBg;
         if ((A >> bit) & 1u)
-            v = border_slot(value_of((lt << 7) | (__popc(band_starts<kConn8>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
+            v = border_slot(value_of((lt << 7) | (__popc(elem_starts<kConn8, V::kRow>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
         Eb[G::kEdgeTop + c] = v;
         // bottom row: the last band of the lane tiles with ty == BLY - 1
         const int lb2 = (G::BLY - 1) * G::BLX + lt;
@@ -541,7 +562,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         v = kBg;
         if ((Bl >> bit) & 1u)
             v = border_slot(value_of(
-                (lb2 << 7) | (sm.lastbase[lb2] + __popc(band_starts<kConn8>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
+                (lb2 << 7) | (sm.lastbase[lb2] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
         Eb[G::kEdgeBottom + c] = v;
     }
     for (int i = t; i < 2 * G::kBH; i += T) {
@@ -554,8 +575,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         uint16_t v = kBg;
         if (right ? (m >> 31) : (m & 1u)) {
             int base = 0;
-            for (int j = 0; j < k; ++j) base += __popc(band_starts<kConn8>(sm.mask[j * R][lt], sm.mask[j * R + R - 1][lt]));
-            const int loc = right ? base + __popc(band_starts<kConn8>(sm.mask[k * R][lt], sm.mask[k * R + R - 1][lt])) - 1
+            for (int j = 0; j < k; ++j) base += __popc(elem_starts<kConn8, V::kRow>(sm.mask[j * R][lt], sm.mask[j * R + R - 1][lt]));
+            const int loc = right ? base + __popc(elem_starts<kConn8, V::kRow>(sm.mask[k * R][lt], sm.mask[k * R + R - 1][lt])) - 1
                                   : base;
             v = border_slot(value_of((lt << 7) | loc));
         }
@@ -581,6 +602,13 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         mo[1] = make_uint4(mrow[4], mrow[5], mrow[6], mrow[7]);
     }
     if (err) atomicOr(&sm.err, err);
+    if (kCount) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned v = __reduce_add_sync(kFull, cnt[k]);
+            if ((t & 31) == 0 && v) atomicAdd(&g_variant_ops[k], (unsigned long long)v);
+        }
+    }
     __syncthreads();
     if (t == 0) {
         s.nslots[b] = sm.nslots;
@@ -588,15 +616,16 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     }
 }
 
-template <class G, bool kConn8>
-__global__ void __launch_bounds__(G::kThreads, (kConn8 ? 1024 : 640) / G::kThreads) k_block_local(JobTable jt, Scratch s,
-                                                                                           int cap) {
+template <class G, bool kConn8, int kMode = 0, bool kCount = false>
+__global__ void __launch_bounds__(G::kThreads, (Variant<kConn8, kMode>::kCap == 64 ? 1024 : 640) / G::kThreads)
+    k_block_local(JobTable jt, Scratch s, int cap) {
+    using Sm = LocalSmem<G, Variant<kConn8, kMode>::kCap>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    LocalSmem<G, kConn8> &sm = *reinterpret_cast<LocalSmem<G, kConn8> *>(smem_raw);
+    Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 0, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
-        process_local<G, kConn8>(job, lb, gb, s, sm, cap);
+        process_local<G, kConn8, kMode, kCount>(job, lb, gb, s, sm, cap);
         __syncthreads();
     }
 }
@@ -765,7 +794,7 @@ struct WriteSmem {
 template <class G>
 __device__ __forceinline__ int runlab_index(int tx, int c) { return kLW * tx + (c ^ ((tx & 3) << 3)); }
 
-template <class G, bool kConn8>
+template <class G, bool kConn8, bool kRow>
 __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
                                               WriteSmem<G> &sm, int cap, uint32_t bound) {
     using Bd = Bands<kConn8>;
@@ -803,7 +832,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     int npieces = 0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
-        npieces += __popc(band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]));
+        npieces += __popc(elem_starts<kConn8, kRow>(mrow[k * R], mrow[k * R + R - 1]));
     }
     const int nchunks = (npieces + 7) >> 3;
     uint4 vq = nchunks > 0 ? vin[0] : make_uint4(0, 0, 0, 0);
@@ -814,7 +843,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         // each lane tile: one label per piece of its band k, at the piece start
-        uint32_t S = band_starts<kConn8>(mrow[k * R], mrow[k * R + R - 1]);
+        uint32_t S = elem_starts<kConn8, kRow>(mrow[k * R], mrow[k * R + R - 1]);
         while (S) {
             const int a0 = lobit(S);
             S &= S - 1u;
@@ -846,7 +875,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
             const uint32_t ma = sm.mask[k * R][ry * G::BLX + ctx];
             const uint32_t mbm = sm.mask[k * R + R - 1][ry * G::BLX + ctx];
             const uint32_t mo = ma | mbm;
-            const uint32_t SS = band_starts<kConn8>(ma, mbm);
+            const uint32_t SS = elem_starts<kConn8, kRow>(ma, mbm);
             int lab[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -876,13 +905,13 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     }
 }
 
-template <class G, bool kConn8>
+template <class G, bool kConn8, bool kRow = true>
 __global__ void __launch_bounds__(G::kThreads) k_block_write(JobTable jt, Scratch s, int cap, uint32_t bound) {
     __shared__ WriteSmem<G> sm;
     for (unsigned iter = 0; claim_item(jt, 2, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
-        process_write<G, kConn8>(job, lb, gb, s, sm, cap, bound);
+        process_write<G, kConn8, kRow>(job, lb, gb, s, sm, cap, bound);
         __syncthreads();
     }
 }
@@ -1055,7 +1084,7 @@ struct GeoLaunch {
 
 template <class G, bool kConn8>
 bool geo_launch_conn(int dev, GeoLaunch &g) {
-    const int bytes = (int)sizeof(LocalSmem<G, kConn8>);
+    const int bytes = (int)sizeof(LocalSmem<G, Variant<kConn8, 0>::kCap>);
     if (cudaFuncSetAttribute(k_block_local<G, kConn8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
         cudaSuccess)
         return false;
@@ -1106,13 +1135,15 @@ int launch_table(int conn, const JobTable &jt, unsigned grid_local, unsigned gri
                  const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream) {
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, true>), stream>>>(jt, s, local_cap);
+        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<true, 0>::kCap>), stream>>>(
+            jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<G, true><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
         ev = timing_mark(stream, ev, kKindMerge);
         k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     } else {
-        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, false>), stream>>>(jt, s, local_cap);
+        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<false, 0>::kCap>), stream>>>(
+            jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<G, false><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
         ev = timing_mark(stream, ev, kKindMerge);
@@ -1165,6 +1196,50 @@ int launch_batch(int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t cap
     return launch_table<G>(conn, jt, (unsigned)(gl.sms * gl.occ_local[c8]), (unsigned)(gl.sms * gl.occ_merge[c8]),
                            (unsigned)(gl.sms * gl.occ_write[c8]), carve<G>(ws, capacity), local_cap, global_cap,
                            bound, stream);
+}
+
+// One image through a coarse-labelling variant of step 1 (with its
+// counters), on 512x64 blocks; steps 2 and 3 as in the method.
+template <bool kConn8, int kMode>
+int launch_variant_t(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
+                     cudaStream_t stream, int cap) {
+    using G = G0;
+    using V = Variant<kConn8, kMode>;
+    const int bytes = (int)sizeof(LocalSmem<G, V::kCap>);
+    if (cudaFuncSetAttribute(k_block_local<G, kConn8, kMode, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             bytes) != cudaSuccess)
+        return -1;
+    JobTable jt{};
+    jt.single.img = img;
+    jt.single.labels = labels;
+    jt.single.pitch = pitch;
+    jt.single.H = H;
+    jt.single.W = W;
+    jt.single.nbx = (W + G::kBW - 1) / G::kBW;
+    jt.single.nby = (H + G::kBH - 1) / G::kBH;
+    jt.single.flags = ((((uintptr_t)img | pitch) & 15) == 0 ? kJobVecIn : 0u) |
+                      ((((uintptr_t)labels & 15) == 0 && (W & 3) == 0) ? kJobVecOut : 0u);
+    const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
+    jt.total = (unsigned)nb;
+    int local_cap, global_cap;
+    uint32_t bound;
+    caps_for<G>(nb, cap, local_cap, global_cap, bound);
+    const Scratch s = carve<G>(ws, nb);
+    k_block_local<G, kConn8, kMode, true><<<(unsigned)nb, G::kThreads, bytes, stream>>>(jt, s, local_cap);
+    k_block_merge<G, kConn8><<<(unsigned)nb, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
+    k_block_write<G, kConn8, V::kRow><<<(unsigned)nb, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <bool kConn8>
+int launch_variant_c(int mode, const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
+                     cudaStream_t stream, int cap) {
+    switch (mode) {
+        case 1: return launch_variant_t<kConn8, 1>(img, H, W, pitch, labels, ws, stream, cap);
+        case 2: return launch_variant_t<kConn8, 2>(img, H, W, pitch, labels, ws, stream, cap);
+        case 3: return launch_variant_t<kConn8, 3>(img, H, W, pitch, labels, ws, stream, cap);
+        default: return launch_variant_t<kConn8, 0>(img, H, W, pitch, labels, ws, stream, cap);
+    }
 }
 
 }  // namespace
@@ -1221,6 +1296,23 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
         case 2: return launch_batch<G2>(conn, hdr, jobs, ws, capacity, stream, cap);
         default: return launch_batch<G0>(conn, hdr, jobs, ws, capacity, stream, cap);
     }
+}
+
+size_t variant_workspace_bytes(int H, int W) { return geo_workspace_bytes(0, geo_blocks(0, H, W)); }
+
+int launch_label_variant(const uint8_t *img, int H, int W, size_t pitch, int conn, int mode, int32_t *labels,
+                         void *ws, cudaStream_t stream, int cap) {
+    return conn == 8 ? launch_variant_c<true>(mode, img, H, W, pitch, labels, ws, stream, cap)
+                     : launch_variant_c<false>(mode, img, H, W, pitch, labels, ws, stream, cap);
+}
+
+int variant_counters(unsigned long long *out, bool reset) {
+    if (cudaMemcpyFromSymbol(out, g_variant_ops, 3 * sizeof(unsigned long long)) != cudaSuccess) return -1;
+    if (reset) {
+        const unsigned long long zero[3] = {0, 0, 0};
+        if (cudaMemcpyToSymbol(g_variant_ops, zero, sizeof(zero)) != cudaSuccess) return -1;
+    }
+    return 0;
 }
 
 int read_and_clear_device_error(int *value) {

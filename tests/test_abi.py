@@ -91,3 +91,11 @@ def test_argument_checks_before_any_device_work(lib):
     assert g(dummy_in, 32, 32, 32, 8, dummy_out, None, 1 << 20, None) == ccl.CCL_ERR_INVALID_ARG
     assert g(dummy_in, 32, 32, 32, 8, dummy_out, 0x20000 + 8, 1 << 20, None) == ccl.CCL_ERR_INVALID_ARG
     assert g(dummy_in, 32, 32, 32, 8, dummy_out, 0x20000, 16, None) == ccl.CCL_ERR_INVALID_ARG
+
+
+def test_variant_argument_checks(lib):
+    # host-side checks only: a bad variant or connectivity is refused before
+    # anything is launched
+    assert lib.ccl_label_variant(None, 4, 4, 4, 8, 7, None, None, None) == ccl.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_variant(None, 4, 4, 4, 5, 0, None, None, None) == ccl.CCL_ERR_INVALID_ARG
+    assert lib.ccl_label_variant(None, 0, 4, 4, 8, 0, None, None, None) == ccl.CCL_OK
