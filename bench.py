@@ -20,6 +20,7 @@ The JSON line carries, besides the contract keys:
   extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
                 between repetitions) with its per-kernel breakdown; the
                 256-image uneven batch (batched graph vs plain launches); the
+                coarse-labelling variants of Sec. 4.2 (time, counters); the
                 serving stream at 2k/5k/10k requests/s (p50/p99, Gpixel/s).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
@@ -333,6 +334,10 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
 
+    # -- extra: the coarse-labelling variants of Sec. 4.2 (time and counters)
+    if rank == 0 and not args.no_extra:
+        line.setdefault("extra", {})["variants"] = bench_variants(torch, ccl)
+
     # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
     # frames through the continuous-batching server)
     if rank == 0 and not args.no_extra:
@@ -441,6 +446,52 @@ def bench_batched(torch, ccl, hbm_gbs):
             "plain_graph_ms": ms_pg, "plain_graph_gpixel_s": px / (ms_pg / 1e3) / 1e9,
             "batched_hbm_roofline_frac": px * BYTES_PER_PIXEL / (ms_b / 1e3) / (hbm_gbs * 1e9),
             "device_status": ccl.ccl_status_string(status)}
+
+
+def bench_variants(torch, ccl):
+    """Sec. 4.2's comparison of the coarse-to-fine strategy on random noise:
+    C2FL (the method), RC2FL (coarse labelling along rows only), CC2FL (along
+    columns only) and NC2FL (none).  Per variant: the median time of the three
+    kernels (CUDA events, 5 runs after 2 warm-ups) and the step-1 counters
+    (merges, root-walk steps, CAS attempts) per Mpixel; (a) sizes 256^2 to
+    4096^2 at density 0.5, 4-connectivity (the paper's), (b) densities 0.1 to
+    0.9 at 2048^2, both connectivities.  Every variant's labels are checked
+    equal to C2FL's."""
+    from paper_1712_09789_gb300 import synth
+
+    names = ccl.VARIANTS
+
+    def one(img, conn):
+        d = torch.from_numpy(img).cuda()
+        ref = ccl.ccl_label_variant(d, conn, 0)
+        row = {}
+        for v, name in enumerate(names):
+            out = torch.empty_like(ref)
+            for _ in range(2):
+                ccl.ccl_label_variant(d, conn, v, labels=out)
+            ts = []
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ccl.ccl_label_variant(d, conn, v, labels=out)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b) * 1e3)
+            _, cnt = ccl.ccl_label_variant(d, conn, v, labels=out, counters=True)
+            mpx = img.size / 1e6
+            row[name] = {"us": sorted(ts)[2], "merges_per_mpx": cnt["merges"] / mpx,
+                         "find_steps_per_mpx": cnt["find_steps"] / mpx, "atomics_per_mpx": cnt["atomics"] / mpx,
+                         "same_labels": bool(torch.equal(out, ref))}
+        return row
+
+    res = {"workload": "Bernoulli noise; (a) side 256..4096 at p=0.5, 4-conn; (b) p=0.1..0.9 at 2048^2, 4/8-conn",
+           "sizes": {}, "densities": {}}
+    for side in (256, 1024, 4096):
+        res["sizes"][str(side)] = one(synth.bernoulli(side, side, 0.5, 0), 4)
+    for conn in (4, 8):
+        for p in (0.1, 0.3, 0.5, 0.7, 0.9):
+            res["densities"][f"conn{conn}_p{p}"] = one(synth.bernoulli(2048, 2048, p, 0), conn)
+    return res
 
 
 def bench_serving(torch, ccl, seconds, rates=(2000, 5000, 10000), warm=0.5):
