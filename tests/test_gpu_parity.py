@@ -211,3 +211,31 @@ def test_iteration_cap_reports_timeout_without_hanging():
         ccl.ccl_debug_set_iteration_cap(0)
     assert ccl.ccl_get_device_status() == ccl.CCL_OK
     np.testing.assert_array_equal(ccl.ccl_label(dev, 8).cpu().numpy(), oracle.label(img, 8))
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("conn", (4, 8))
+def test_blocks_with_a_piece_per_column(conn):
+    """Under 4-connectivity a band whose columns meet only diagonally holds a
+    piece per column (32 per band, the most a lane tile can hold).
+    Checkerboard patches in a noise image put such blocks beside ordinary ones
+    into one call (twice in a row) and into one batch."""
+    import torch
+
+    g = np.random.default_rng(77)
+    img = (g.random((300, 2100)) < 0.5).astype(np.uint8)
+    y, x = np.mgrid[0:300, 0:2100]
+    cb = ((x + y) % 2 == 0).astype(np.uint8)
+    for y0, x0 in ((0, 0), (64, 600), (130, 1536), (250, 1900)):
+        img[y0:y0 + 70, x0:x0 + 300] = cb[y0:y0 + 70, x0:x0 + 300]
+    want = oracle.label(img, conn)
+    d = torch.from_numpy(img).cuda()
+    for _ in range(2):
+        got = ccl.ccl_label(d, conn).cpu().numpy()
+        assert ccl.ccl_get_device_status() == ccl.CCL_OK
+        np.testing.assert_array_equal(got, want)
+    pairs = [(d, torch.empty(img.shape, dtype=torch.int32, device="cuda")),
+             (torch.from_numpy(cb[:100, :700].copy()).cuda(), torch.empty((100, 700), dtype=torch.int32, device="cuda"))]
+    ccl.ccl_label_batched(pairs, conn, tile=0)
+    np.testing.assert_array_equal(pairs[0][1].cpu().numpy(), want)
+    np.testing.assert_array_equal(pairs[1][1].cpu().numpy(), oracle.label(cb[:100, :700], conn))
