@@ -127,3 +127,32 @@ def label_closure(img: np.ndarray, conn: int) -> np.ndarray:
                     lab[y][x] = best
                     changed = True
     return np.array(lab, dtype=np.int32).reshape(H, W)
+
+
+def component_stats(labels: np.ndarray) -> np.ndarray:
+    """Statistics of every component of a canonical label image, in increasing
+    label order (the use the paper motivates in Sec. 1: size and location of
+    each region).  One row per component:
+    ``label, area, x0, y0, x1, y1, sum_x, sum_y`` -- area is the pixel count,
+    (x0, y0)-(x1, y1) the inclusive bounding box, sum_x and sum_y the sums of
+    the pixel coordinates (centroid = sum / area).  Plain numpy on the
+    definition: every pixel with label l > 0 belongs to component l."""
+    labels = np.asarray(labels)
+    H, W = labels.shape
+    ys, xs = np.nonzero(labels)
+    lab = labels[ys, xs].astype(np.int64)
+    order = np.argsort(lab, kind="stable")
+    lab, ys, xs = lab[order], ys[order].astype(np.int64), xs[order].astype(np.int64)
+    if lab.size == 0:
+        return np.zeros((0, 8), dtype=np.int64)
+    uniq, first, area = np.unique(lab, return_index=True, return_counts=True)
+    out = np.zeros((uniq.size, 8), dtype=np.int64)
+    out[:, 0] = uniq
+    out[:, 1] = area
+    out[:, 2] = np.minimum.reduceat(xs, first)
+    out[:, 3] = np.minimum.reduceat(ys, first)
+    out[:, 4] = np.maximum.reduceat(xs, first)
+    out[:, 5] = np.maximum.reduceat(ys, first)
+    out[:, 6] = np.add.reduceat(xs, first)
+    out[:, 7] = np.add.reduceat(ys, first)
+    return out

@@ -243,3 +243,43 @@ def test_rejects_bad_arguments():
         oracle.label(np.zeros((3, 3), np.int32), 4)
     # empty images label to empty outputs
     assert oracle.label(np.zeros((0, 5), np.uint8), 4).shape == (0, 5)
+
+
+# -- component statistics (oracle.component_stats), pinned by closed forms and
+# by a per-component brute force
+def test_component_stats_closed_forms():
+    # one filled rectangle: area, box and coordinate sums in closed form
+    img = np.zeros((9, 13), np.uint8)
+    img[2:7, 3:11] = 1
+    st = oracle.component_stats(oracle.label(img, 8))
+    assert st.shape == (1, 8)
+    xs, ys = np.arange(3, 11), np.arange(2, 7)
+    assert st[0].tolist() == [1 + 2 * 13 + 3, 40, 3, 2, 10, 6, ys.size * xs.sum(), xs.size * ys.sum()]
+    # 4-connected checkerboard: every pixel its own component, label 1 + index
+    y, x = np.mgrid[0:5, 0:7]
+    cb = ((x + y) % 2 == 0).astype(np.uint8)
+    st = oracle.component_stats(oracle.label(cb, 4))
+    py, px = np.nonzero(cb)
+    assert st[:, 0].tolist() == (1 + px + py * 7).tolist()
+    assert (st[:, 1] == 1).all()
+    assert st[:, 2].tolist() == px.tolist() and st[:, 4].tolist() == px.tolist()
+    assert st[:, 3].tolist() == py.tolist() and st[:, 5].tolist() == py.tolist()
+    assert st[:, 6].tolist() == px.tolist() and st[:, 7].tolist() == py.tolist()
+    # empty image: no rows
+    assert oracle.component_stats(np.zeros((3, 3), np.int32)).shape == (0, 8)
+
+
+@pytest.mark.parametrize("conn", (4, 8))
+def test_component_stats_brute_force(conn):
+    g = np.random.default_rng(31)
+    img = (g.random((40, 57)) < 0.45).astype(np.uint8)
+    lab = oracle.label(img, conn)
+    st = oracle.component_stats(lab)
+    assert st[:, 1].sum() == int(img.astype(bool).sum())
+    for row in st:
+        yy, xx = np.nonzero(lab == row[0])
+        assert row[1] == yy.size
+        assert (row[2], row[3], row[4], row[5]) == (xx.min(), yy.min(), xx.max(), yy.max())
+        assert (row[6], row[7]) == (xx.sum(), yy.sum())
+        # the label is the component's smallest raster position plus one
+        assert row[0] == 1 + (yy * img.shape[1] + xx).min()
