@@ -263,6 +263,33 @@ size_t ccl_noalloc_max_workspace_bytes(void);
 ccl_status ccl_get_device_status(void *stream);
 
 /*
+ * Statistics of one component, as ccl_component_stats writes them: its
+ * label, its pixel count, its inclusive bounding box (x0, y0)-(x1, y1) and
+ * the sums of its pixels' coordinates (centroid = sum / area).  40 bytes.
+ */
+typedef struct {
+    int32_t label;
+    int32_t area;
+    int32_t x0, y0, x1, y1;
+    int64_t sum_x, sum_y;
+} ccl_component;
+
+/*
+ * Size and location of every region of a labelled image (the uses of
+ * labelling the paper names in Sec. 1).  `labels` is a device H x W int32
+ * image of canonical labels, as ccl_label writes them (row stride W).  The
+ * components are written to the device array `out` in increasing label
+ * order, at most `capacity` of them; `*count` (host) receives the number of
+ * components, which may exceed `capacity` (call again with more room).
+ * Synchronous on `stream`; library-owned scratch of 4 bytes per pixel.
+ * Errors: bad sizes or pointers -> CCL_ERR_INVALID_ARG; labels that are not
+ * canonical (a label that names no root) -> CCL_ERR_INVALID_ARG after the
+ * run, with *count set; H*W > 2^31-2 -> CCL_ERR_UNSUPPORTED.
+ */
+ccl_status ccl_component_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, int *count,
+                               void *stream);
+
+/*
  * Coarse-labelling variants of Sec. 4.2, for the paper's comparison of the
  * coarse-to-fine strategy: variant 0 is the method (C2FL, what ccl_label
  * computes), 1 keeps the coarse labelling along rows only (RC2FL), 2 along

@@ -77,6 +77,8 @@ _SIGS = {
     "ccl_label_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
                                      _c.c_void_p]),
     "ccl_noalloc_max_workspace_bytes": (_c.c_size_t, []),
+    "ccl_component_stats": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_void_p, _c.c_int,
+                                       _c.POINTER(_c.c_int), _c.c_void_p]),
     "ccl_label_variant": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_int, _c.c_void_p,
                                      _c.POINTER(_c.c_ulonglong), _c.c_void_p]),
     "ccl_label_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p]),
@@ -210,6 +212,35 @@ def ccl_label_variant(img, connectivity: int = 8, variant: int = 0, labels=None,
     if counters:
         return labels, {"merges": cnt[0], "find_steps": cnt[1], "atomics": cnt[2]}
     return labels
+
+
+# numpy layout of ``ccl_component`` (40 bytes)
+COMPONENT_DTYPE = [("label", "<i4"), ("area", "<i4"), ("x0", "<i4"), ("y0", "<i4"), ("x1", "<i4"), ("y1", "<i4"),
+                   ("sum_x", "<i8"), ("sum_y", "<i8")]
+
+
+def ccl_component_stats(labels, stream=None, capacity=None):
+    """Size and location of every component of a canonical label image on the
+    device (``ccl_component_stats``): a numpy structured array in label order
+    with fields label, area, x0, y0, x1, y1, sum_x, sum_y.  Without
+    ``capacity`` a first call counts the components."""
+    import numpy as np
+    import torch
+
+    if labels.dtype != torch.int32 or labels.dim() != 2 or not labels.is_cuda or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous 2D int32 CUDA tensor")
+    H, W = labels.shape
+    lib = load()
+    sp = _stream_ptr(stream, labels.device)
+    n = ctypes.c_int(0)
+    if capacity is None:
+        _check(lib.ccl_component_stats(labels.data_ptr(), H, W, None, 0, ctypes.byref(n), sp), "ccl_component_stats")
+        capacity = n.value
+    buf = torch.empty(max(1, capacity) * 40, dtype=torch.uint8, device=labels.device)
+    _check(lib.ccl_component_stats(labels.data_ptr(), H, W, buf.data_ptr(), capacity, ctypes.byref(n), sp),
+           "ccl_component_stats")
+    k = min(n.value, capacity)
+    return np.frombuffer(buf[: k * 40].cpu().numpy().tobytes(), dtype=np.dtype(COMPONENT_DTYPE))
 
 
 def ccl_noalloc_max_workspace_bytes() -> int:

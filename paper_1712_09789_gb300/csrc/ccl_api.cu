@@ -26,6 +26,7 @@ struct DevBuf {
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_scratch;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_img;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_lab;
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_stats;  // component statistics scratch
 
 ccl_status grow(DevBuf &b, size_t need) {
     if (b.bytes >= need) return CCL_OK;
@@ -186,6 +187,41 @@ ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int
             return CCL_ERR_CUDA;
     }
     return CCL_OK;
+}
+
+ccl_status ccl_component_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, int *count,
+                               void *stream) {
+    if (H < 0 || W < 0 || !count || capacity < 0 || (capacity > 0 && !out)) return CCL_ERR_INVALID_ARG;
+    if ((long long)H * (long long)W > 2147483646LL) return CCL_ERR_UNSUPPORTED;
+    *count = 0;
+    if (H == 0 || W == 0) return CCL_OK;
+    if (!labels) return CCL_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t ws_bytes = (ccl::stats_workspace_bytes(H, W) + 255) & ~(size_t)255;
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DevBuf &b = g_stats[{dev, s}];
+        if (b.bytes < ws_bytes + 256) {
+            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+            const ccl_status st = grow(b, ws_bytes + 256);
+            if (st != CCL_OK) return st;
+        }
+        ws = b.ptr;
+    }
+    // the last 256 bytes hold the component count and the count of bad pixels
+    uint32_t *tail = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + ws_bytes);
+    if (cudaMemsetAsync(tail, 0, 8, s) != cudaSuccess) return CCL_ERR_CUDA;
+    if (ccl::launch_stats(labels, H, W, out, capacity, ws, tail, reinterpret_cast<int *>(tail + 1), s) != 0)
+        return CCL_ERR_CUDA;
+    uint32_t host[2] = {0, 0};
+    if (cudaMemcpyAsync(host, tail, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CCL_ERR_CUDA;
+    *count = (int)host[0];
+    return host[1] ? CCL_ERR_INVALID_ARG : CCL_OK;
 }
 
 ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,

@@ -76,6 +76,13 @@ int launch_label_variant(const uint8_t *img, int H, int W, size_t pitch, int con
                          void *ws, cudaStream_t stream, int cap);
 int variant_counters(unsigned long long *out, bool reset);
 
+// Component statistics (ccl_stats.cu): scratch bytes for an H x W image, and
+// the enqueued pipeline; the component count lands in *count_dev and the
+// number of pixels whose label names no root in *bad_dev (added to).
+size_t stats_workspace_bytes(int H, int W);
+int launch_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, void *ws,
+                 uint32_t *count_dev, int *bad_dev, cudaStream_t stream);
+
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
 

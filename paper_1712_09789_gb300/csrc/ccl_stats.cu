@@ -1,0 +1,227 @@
+// ccl_stats.cu -- statistics of every component of a labelled image: area,
+// bounding box and coordinate sums (centroid = sum / area), the size and
+// location of each region that the paper gives as the use of labelling
+// (Sec. 1).
+//
+// Canonical labels make the components easy to index: a pixel is its
+// component's root when its label equals its own raster position plus one,
+// and the roots in raster order are the components in label order.
+//   k_stats_count       roots per chunk of 8192 consecutive pixels
+//   k_stats_scan        exclusive prefix over the chunk counts (one CTA)
+//   k_stats_index       dense index of every root (rootmap[p]), component
+//                       records initialised in label order
+//   k_stats_accumulate  tiles of 16 x 512 pixels: each pixel's component is
+//                       looked up and its statistics folded into a shared-
+//                       memory hash table, one global update per component
+//                       and tile afterwards (the large components would
+//                       otherwise meet in global atomics from every pixel)
+#include <climits>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "ccl_internal.h"
+
+namespace ccl {
+namespace {
+
+constexpr int kChunk = 8192;      // pixels per chunk (256 threads x 32)
+constexpr int kStatThreads = 256;
+constexpr int kTileH = 16, kTileW = 512;
+constexpr int kHash = 1024;       // hash slots per tile
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool is_root(const int32_t *labels, long long p) {
+    return labels[p] == (int32_t)(p + 1);
+}
+
+__global__ void __launch_bounds__(kStatThreads) k_stats_count(const int32_t *labels, long long n, uint32_t *counts) {
+    __shared__ uint32_t warp_sum[kStatThreads / 32];
+    const long long base = (long long)blockIdx.x * kChunk;
+    uint32_t c = 0;
+    for (int i = 0; i < kChunk / kStatThreads; ++i) {
+        const long long p = base + i * kStatThreads + threadIdx.x;
+        if (p < n && is_root(labels, p)) ++c;
+    }
+    c = __reduce_add_sync(0xFFFFFFFFu, c);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t s = 0;
+        for (int w = 0; w < kStatThreads / 32; ++w) s += warp_sum[w];
+        counts[blockIdx.x] = s;
+    }
+}
+
+// counts[0..nchunks) -> exclusive prefix in place; counts[nchunks] = total
+__global__ void __launch_bounds__(1024) k_stats_scan(uint32_t *counts, int nchunks) {
+    __shared__ uint32_t warp_sum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int off = 0; off < nchunks; off += 1024) {
+        const int i = off + (int)threadIdx.x;
+        const uint32_t v = i < nchunks ? counts[i] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += x;
+        }
+        if (lane == 31) warp_sum[w] = incl;
+        __syncthreads();
+        uint32_t before = carry;
+        for (int k = 0; k < w; ++k) before += warp_sum[k];
+        if (i < nchunks) counts[i] = before + incl - v;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = before + incl;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) counts[nchunks] = carry;
+}
+
+__global__ void __launch_bounds__(kStatThreads) k_stats_index(const int32_t *labels, long long n,
+                                                               const uint32_t *base, uint32_t *rootmap,
+                                                               ccl_component *out, int capacity) {
+    __shared__ uint32_t warp_cnt[kStatThreads / 32];
+    const long long start = (long long)blockIdx.x * kChunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t next = base[blockIdx.x];  // dense index of the chunk's next root (same in every thread)
+    for (int i = 0; i < kChunk / kStatThreads; ++i) {
+        const long long p = start + i * kStatThreads + threadIdx.x;
+        const bool r = p < n && is_root(labels, p);
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, r);
+        if (lane == 0) warp_cnt[w] = __popc(m);
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+        for (int k = 0; k < kStatThreads / 32; ++k) {
+            const uint32_t c = warp_cnt[k];
+            if (k < w) before += c;
+            total += c;
+        }
+        if (r) {
+            const uint32_t idx = next + before + __popc(m & ((1u << lane) - 1u));
+            rootmap[p] = idx;
+            if ((int)idx < capacity) {
+                ccl_component c;
+                c.label = (int32_t)(p + 1);
+                c.area = 0;
+                c.x0 = INT_MAX;
+                c.y0 = INT_MAX;
+                c.x1 = -1;
+                c.y1 = -1;
+                c.sum_x = 0;
+                c.sum_y = 0;
+                out[idx] = c;
+            }
+        }
+        next += total;
+        __syncthreads();
+    }
+}
+
+struct StatSmem {
+    uint32_t key[kHash];
+    int32_t area[kHash], x0[kHash], y0[kHash], x1[kHash], y1[kHash];
+    unsigned long long sx[kHash], sy[kHash];
+};
+
+__device__ __forceinline__ void fold_global(ccl_component *out, uint32_t k, int a, int x0, int y0, int x1, int y1,
+                                            unsigned long long sx, unsigned long long sy) {
+    ccl_component &c = out[k];
+    atomicAdd(&c.area, a);
+    atomicMin(&c.x0, x0);
+    atomicMin(&c.y0, y0);
+    atomicMax(&c.x1, x1);
+    atomicMax(&c.y1, y1);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_x), sx);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_y), sy);
+}
+
+__global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t *labels, int H, int W,
+                                                                    const uint32_t *rootmap, const uint32_t *counts,
+                                                                    int nchunks, ccl_component *out, int capacity,
+                                                                    int *bad) {
+    __shared__ StatSmem sm;
+    for (int i = threadIdx.x; i < kHash; i += kStatThreads) {
+        sm.key[i] = kEmpty;
+        sm.area[i] = 0;
+        sm.x0[i] = INT_MAX;
+        sm.y0[i] = INT_MAX;
+        sm.x1[i] = -1;
+        sm.y1[i] = -1;
+        sm.sx[i] = 0;
+        sm.sy[i] = 0;
+    }
+    __syncthreads();
+    const uint32_t ncomp = counts[nchunks];
+    const uint32_t lim = ncomp < (uint32_t)capacity ? ncomp : (uint32_t)capacity;
+    const long long n = (long long)H * W;
+    const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;
+    int nbad = 0;
+    for (int i = threadIdx.x; i < kTileH * kTileW; i += kStatThreads) {
+        const int x = tx0 + (i % kTileW), y = ty0 + i / kTileW;
+        if (x >= W || y >= H) continue;
+        const int32_t l = labels[(long long)y * W + x];
+        if (l == 0) continue;
+        // a label must name a root of the image (canonical labels); anything
+        // else is counted and skipped
+        if (l < 0 || (long long)l > n || !is_root(labels, (long long)l - 1)) {
+            ++nbad;
+            continue;
+        }
+        const uint32_t k = rootmap[l - 1];
+        if (k >= lim) continue;
+        uint32_t h = (k * 2654435761u) >> 22;  // 10-bit hash
+        bool done = false;
+        for (int probe = 0; probe < 16 && !done; ++probe, h = (h + 1) & (kHash - 1)) {
+            uint32_t cur = sm.key[h];
+            if (cur == kEmpty) cur = atomicCAS(&sm.key[h], kEmpty, k);
+            if (cur == kEmpty || cur == k) {
+                atomicAdd(&sm.area[h], 1);
+                atomicMin(&sm.x0[h], x);
+                atomicMin(&sm.y0[h], y);
+                atomicMax(&sm.x1[h], x);
+                atomicMax(&sm.y1[h], y);
+                atomicAdd(&sm.sx[h], (unsigned long long)x);
+                atomicAdd(&sm.sy[h], (unsigned long long)y);
+                done = true;
+            }
+        }
+        if (!done) fold_global(out, k, 1, x, y, x, y, (unsigned long long)x, (unsigned long long)y);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHash; i += kStatThreads)
+        if (sm.key[i] != kEmpty)
+            fold_global(out, sm.key[i], sm.area[i], sm.x0[i], sm.y0[i], sm.x1[i], sm.y1[i], sm.sx[i], sm.sy[i]);
+    if (nbad) atomicAdd(bad, nbad);
+}
+
+}  // namespace
+
+size_t stats_workspace_bytes(int H, int W) {
+    const long long n = (long long)H * W;
+    const long long nchunks = (n + kChunk - 1) / kChunk;
+    return (size_t)((n * 4 + 255) & ~255LL) + (size_t)((nchunks + 1 + 1) * 4 + 255);
+}
+
+int launch_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, void *ws,
+                 uint32_t *count_dev, int *bad_dev, cudaStream_t stream) {
+    const long long n = (long long)H * W;
+    const int nchunks = (int)((n + kChunk - 1) / kChunk);
+    uint32_t *rootmap = static_cast<uint32_t *>(ws);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + ((n * 4 + 255) & ~255LL));
+    k_stats_count<<<nchunks, kStatThreads, 0, stream>>>(labels, n, counts);
+    k_stats_scan<<<1, 1024, 0, stream>>>(counts, nchunks);
+    k_stats_index<<<nchunks, kStatThreads, 0, stream>>>(labels, n, counts, rootmap, out, capacity);
+    const dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
+    k_stats_accumulate<<<grid, kStatThreads, 0, stream>>>(labels, H, W, rootmap, counts, nchunks, out, capacity,
+                                                         bad_dev);
+    if (cudaMemcpyAsync(count_dev, counts + nchunks, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) !=
+        cudaSuccess)
+        return -1;
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace ccl

@@ -99,3 +99,12 @@ def test_variant_argument_checks(lib):
     assert lib.ccl_label_variant(None, 4, 4, 4, 8, 7, None, None, None) == ccl.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_variant(None, 4, 4, 4, 5, 0, None, None, None) == ccl.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_variant(None, 0, 4, 4, 8, 0, None, None, None) == ccl.CCL_OK
+
+
+def test_component_stats_argument_checks(lib):
+    n = ctypes.c_int(-1)
+    assert lib.ccl_component_stats(None, -1, 4, None, 0, ctypes.byref(n), None) == ccl.CCL_ERR_INVALID_ARG
+    assert lib.ccl_component_stats(None, 4, 4, None, 3, ctypes.byref(n), None) == ccl.CCL_ERR_INVALID_ARG
+    assert lib.ccl_component_stats(None, 4, 4, None, 0, None, None) == ccl.CCL_ERR_INVALID_ARG
+    assert lib.ccl_component_stats(None, 65536, 32768, None, 0, ctypes.byref(n), None) == ccl.CCL_ERR_UNSUPPORTED
+    assert lib.ccl_component_stats(None, 0, 4, None, 0, ctypes.byref(n), None) == ccl.CCL_OK and n.value == 0
