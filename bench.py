@@ -20,8 +20,9 @@ The JSON line carries, besides the contract keys:
   extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
                 between repetitions) with its per-kernel breakdown; the
                 256-image uneven batch (batched graph vs plain launches); the
-                coarse-labelling variants of Sec. 4.2 (time, counters); the
-                serving stream at 2k/5k/10k requests/s (p50/p99, Gpixel/s).
+                coarse-labelling variants of Sec. 4.2 (time, counters);
+                component statistics of the 8192^2 labels; the serving stream
+                at 2k/5k/10k requests/s (p50/p99, Gpixel/s).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 """
@@ -338,6 +339,10 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line.setdefault("extra", {})["variants"] = bench_variants(torch, ccl)
 
+    # -- extra: component statistics of the 8192^2 labels
+    if rank == 0 and not args.no_extra:
+        line.setdefault("extra", {})["component_stats"] = bench_stats(torch, ccl)
+
     # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
     # frames through the continuous-batching server)
     if rank == 0 and not args.no_extra:
@@ -491,6 +496,40 @@ def bench_variants(torch, ccl):
     for conn in (4, 8):
         for p in (0.1, 0.3, 0.5, 0.7, 0.9):
             res["densities"][f"conn{conn}_p{p}"] = one(synth.bernoulli(2048, 2048, p, 0), conn)
+    return res
+
+
+def bench_stats(torch, ccl):
+    """Component statistics (area, bounding box, coordinate sums) of the
+    8192x8192 Bernoulli(0.5) labels, both connectivities: one synchronous
+    ccl_component_stats call per repetition with the records left on the
+    device; median of 5 after 2 warm-ups (host clock around the call, which
+    returns after its stream has finished)."""
+    import ctypes
+
+    from paper_1712_09789_gb300 import synth
+
+    lib = ccl.load()
+    img = torch.from_numpy(synth.bernoulli(8192, 8192, 0.5, 0)).cuda()
+    res = {"workload": "8192x8192 Bernoulli p=0.5 seed 0 labels"}
+    for conn in (8, 4):
+        lab = ccl.ccl_label(img, conn)
+        n = ctypes.c_int(0)
+        sp = torch.cuda.current_stream().cuda_stream
+        lib.ccl_component_stats(lab.data_ptr(), 8192, 8192, None, 0, ctypes.byref(n), sp)
+        buf = torch.empty(max(1, n.value) * 40, dtype=torch.uint8, device="cuda")
+        ts = []
+        for i in range(7):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = lib.ccl_component_stats(lab.data_ptr(), 8192, 8192, buf.data_ptr(), n.value, ctypes.byref(n), sp)
+            t1 = time.perf_counter()
+            if st != ccl.CCL_OK:
+                raise RuntimeError(f"ccl_component_stats: {ccl.ccl_status_string(st)}")
+            if i >= 2:
+                ts.append((t1 - t0) * 1e3)
+        ms = sorted(ts)[2]
+        res[f"conn{conn}"] = {"components": n.value, "ms": ms, "gpixel_s": 8192 * 8192 / (ms / 1e3) / 1e9}
     return res
 
 
