@@ -17,6 +17,12 @@ Three independent routes to that result:
 * ``label_bfs``      -- breadth-first flood fill in raster order, plain C.
 * ``label_closure``  -- pure Python: repeated min-propagation over the
   adjacency until nothing changes.  Slow; for images of a few hundred pixels.
+
+3D volumes (the 2D/3D problem statement of Sec. 1) follow the same rule one
+dimension up: voxel (x, y, z) of a ``(D, H, W)`` array has raster position
+``x + y*W + z*W*H``; 6- or 26-connectivity.  ``label3d_two_pass`` and
+``label3d_bfs`` (C) and ``label3d_closure`` (pure Python) mirror the 2D
+routines.
 """
 from __future__ import annotations
 
@@ -53,6 +59,11 @@ def _load():
                 fn = getattr(lib, name)
                 fn.restype = ctypes.c_int
                 fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                               ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
+            for name in ("ccl_oracle3d_two_pass", "ccl_oracle3d_bfs"):
+                fn = getattr(lib, name)
+                fn.restype = ctypes.c_int
+                fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                ctypes.c_int64, ctypes.c_int, ctypes.c_void_p]
             _lib = lib
     return _lib
@@ -127,6 +138,85 @@ def label_closure(img: np.ndarray, conn: int) -> np.ndarray:
                     lab[y][x] = best
                     changed = True
     return np.array(lab, dtype=np.int32).reshape(H, W)
+
+
+def _call3d(name: str, vol: np.ndarray, conn: int) -> np.ndarray:
+    vol = np.asarray(vol)
+    if vol.ndim != 3 or vol.dtype != np.uint8:
+        raise ValueError("volume must be a 3D uint8 array")
+    if conn not in (6, 26):
+        raise ValueError("connectivity must be 6 or 26")
+    D, H, W = vol.shape
+
+    # the C routines take a row pitch and a slice stride of H * pitch
+    # (numpy may report any stride for a dimension of extent 1)
+    def fits(v):
+        s0, s1, s2 = v.strides
+        if W > 1 and s2 != 1:
+            return False
+        if H > 1:
+            return s1 >= W and (D == 1 or s0 == s1 * H)
+        return D == 1 or s0 >= W
+
+    if not fits(vol):
+        vol = np.ascontiguousarray(vol)
+    pitch = vol.strides[1] if H > 1 else (vol.strides[0] if D > 1 else W)
+    out = np.empty((D, H, W), dtype=np.int32)
+    if D == 0 or H == 0 or W == 0:
+        return out
+    rc = getattr(_load(), name)(vol.ctypes.data, D, H, W, pitch, conn, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError(f"{name} failed with status {rc}")
+    return out
+
+
+def label3d_two_pass(vol: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels of a volume by raster two-pass union-find (C)."""
+    return _call3d("ccl_oracle3d_two_pass", vol, conn)
+
+
+def label3d_bfs(vol: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels of a volume by raster-order breadth-first flood fill (C)."""
+    return _call3d("ccl_oracle3d_bfs", vol, conn)
+
+
+def label3d(vol: np.ndarray, conn: int) -> np.ndarray:
+    """The oracle's answer for a volume: the two-pass union-find labels."""
+    return label3d_two_pass(vol, conn)
+
+
+def label3d_closure(vol: np.ndarray, conn: int) -> np.ndarray:
+    """Canonical labels of a volume by min-propagation to a fixed point (pure
+    Python; volumes of a few hundred voxels)."""
+    vol = np.asarray(vol)
+    D, H, W = vol.shape
+    if conn not in (6, 26):
+        raise ValueError("connectivity must be 6 or 26")
+    nbrs = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+            if (dx, dy, dz) != (0, 0, 0) and (conn == 26 or abs(dx) + abs(dy) + abs(dz) == 1)]
+    fg = vol != 0
+    lab = {}
+    for z in range(D):
+        for y in range(H):
+            for x in range(W):
+                if fg[z, y, x]:
+                    lab[(x, y, z)] = x + y * W + z * W * H + 1
+    changed = True
+    while changed:
+        changed = False
+        for (x, y, z), v in list(lab.items()):
+            best = v
+            for dx, dy, dz in nbrs:
+                w = lab.get((x + dx, y + dy, z + dz))
+                if w is not None and w < best:
+                    best = w
+            if best != v:
+                lab[(x, y, z)] = best
+                changed = True
+    out = np.zeros((D, H, W), dtype=np.int32)
+    for (x, y, z), v in lab.items():
+        out[z, y, x] = v
+    return out
 
 
 def component_stats(labels: np.ndarray) -> np.ndarray:

@@ -1,5 +1,6 @@
 /*
- * CPU oracle for connected-components labelling of a 2D binary image.
+ * CPU oracle for connected-components labelling of a 2D binary image (and,
+ * at the end of the file, of a 3D binary volume).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the library path may include, link or
  * call this file; only the tests, the package smoke check and the CPU
@@ -145,6 +146,130 @@ int ccl_oracle_bfs(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
                     if (!is_fg(img, pitch, nx, ny) || labels[n] != 0) continue;
                     labels[n] = lab;
                     queue[tail++] = (int32_t)n;
+                }
+            }
+        }
+    }
+    free(queue);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * 3D volumes.  The task the paper sets out (Sec. 1) is a unique ID per
+ * connected region of a 2D or 3D image; its method is worked out in 2D.  The
+ * volume extension reads the pixel model of Sec. 3 one dimension up:
+ *   - voxel V(x,y,z) has raster position x + y*W + z*W*H; the INPUT has a
+ *     row stride of `pitch` bytes and a slice stride of H*pitch bytes;
+ *   - adjacency: 6-connectivity (|dx|+|dy|+|dz| == 1) or 26-connectivity
+ *     (max(|dx|,|dy|,|dz|) == 1);
+ *   - every voxel of a component C gets 1 + min over C of the raster
+ *     position; background gets 0.
+ * Same status codes as the 2D routines; D*H*W must stay below 2^31 - 1.
+ */
+static int args3_ok(int64_t D, int64_t H, int64_t W, int64_t pitch, int conn)
+{
+    if (D < 0 || H < 0 || W < 0) return 0;
+    if (D > 0 && H > 0 && W > 0 && pitch < W) return 0;
+    if (conn != 6 && conn != 26) return 0;
+    if (D * H * W > (int64_t)2147483646) return 0;
+    return 1;
+}
+
+static int is_fg3(const uint8_t *img, int64_t H, int64_t pitch, int64_t x, int64_t y, int64_t z)
+{
+    return img[(z * H + y) * pitch + x] != 0;
+}
+
+/* Is the offset (dx,dy,dz) a neighbour under `conn`? */
+static int is_nbr3(int conn, int dx, int dy, int dz)
+{
+    int a = (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz);
+    if (a == 0) return 0;
+    return conn == 26 || a == 1;
+}
+
+int ccl_oracle3d_two_pass(const uint8_t *img, int64_t D, int64_t H, int64_t W, int64_t pitch,
+                          int conn, int32_t *labels)
+{
+    if (!args3_ok(D, H, W, pitch, conn)) return 1;
+    int64_t N = D * H * W;
+    if (N == 0) return 0;
+    int32_t *parent = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    if (!parent) return 2;
+
+    /* Pass 1 in raster order (x fastest, then y, then z): each foreground
+     * voxel starts as its own tree and is joined with every foreground
+     * neighbour that comes earlier in that order, i.e. the neighbours in the
+     * previous slice, in the previous row of the same slice, and to the left. */
+    for (int64_t z = 0; z < D; ++z) {
+        for (int64_t y = 0; y < H; ++y) {
+            for (int64_t x = 0; x < W; ++x) {
+                int32_t p = (int32_t)((z * H + y) * W + x);
+                if (!is_fg3(img, H, pitch, x, y, z)) {
+                    parent[p] = -1;
+                    continue;
+                }
+                parent[p] = p;
+                for (int dz = -1; dz <= 0; ++dz) {
+                    for (int dy = -1; dy <= 1; ++dy) {
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            int earlier = dz < 0 || (dy < 0) || (dy == 0 && dx < 0);
+                            if (!earlier || !is_nbr3(conn, dx, dy, dz)) continue;
+                            int64_t nx = x + dx, ny = y + dy, nz = z + dz;
+                            if (nx < 0 || ny < 0 || nz < 0 || nx >= W || ny >= H) continue;
+                            if (!is_fg3(img, H, pitch, nx, ny, nz)) continue;
+                            uf_union(parent, p, (int32_t)((nz * H + ny) * W + nx));
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    /* Pass 2: each foreground voxel takes 1 + its root. */
+    for (int64_t p = 0; p < N; ++p)
+        labels[p] = parent[p] < 0 ? 0 : 1 + uf_find(parent, (int32_t)p);
+
+    free(parent);
+    return 0;
+}
+
+int ccl_oracle3d_bfs(const uint8_t *img, int64_t D, int64_t H, int64_t W, int64_t pitch,
+                     int conn, int32_t *labels)
+{
+    if (!args3_ok(D, H, W, pitch, conn)) return 1;
+    int64_t N = D * H * W;
+    if (N == 0) return 0;
+    int32_t *queue = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    if (!queue) return 2;
+    for (int64_t p = 0; p < N; ++p) labels[p] = 0;
+
+    for (int64_t z0 = 0; z0 < D; ++z0) {
+        for (int64_t y0 = 0; y0 < H; ++y0) {
+            for (int64_t x0 = 0; x0 < W; ++x0) {
+                int64_t seed = (z0 * H + y0) * W + x0;
+                if (!is_fg3(img, H, pitch, x0, y0, z0) || labels[seed] != 0) continue;
+                /* the first voxel of its component in raster order */
+                int32_t lab = (int32_t)(seed + 1);
+                int64_t head = 0, tail = 0;
+                labels[seed] = lab;
+                queue[tail++] = (int32_t)seed;
+                while (head < tail) {
+                    int64_t q = queue[head++];
+                    int64_t qx = q % W, qy = (q / W) % H, qz = q / (W * H);
+                    for (int dz = -1; dz <= 1; ++dz) {
+                        for (int dy = -1; dy <= 1; ++dy) {
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                if (!is_nbr3(conn, dx, dy, dz)) continue;
+                                int64_t nx = qx + dx, ny = qy + dy, nz = qz + dz;
+                                if (nx < 0 || ny < 0 || nz < 0 || nx >= W || ny >= H || nz >= D) continue;
+                                int64_t n = (nz * H + ny) * W + nx;
+                                if (!is_fg3(img, H, pitch, nx, ny, nz) || labels[n] != 0) continue;
+                                labels[n] = lab;
+                                queue[tail++] = (int32_t)n;
+                            }
+                        }
+                    }
                 }
             }
         }

@@ -21,6 +21,9 @@ natural/texture/artifact images from 512x512 to 4096x4096):
 * ``smoothed``       Gaussian-smoothed white noise thresholded at a quantile.
 * ``batch_uneven``   256 images of uneven size for the batched path.
 * ``serving_frames`` a stream of translated smoothed-noise frames.
+* ``bernoulli3d``, ``smoothed3d``, ``shells``, ``comb3d``: volumes
+  ``[D][H][W]`` for the 3D extension (noise, blobs, concentric cube shells,
+  a comb per slice joined through the slices between them).
 """
 from __future__ import annotations
 
@@ -194,3 +197,49 @@ def poisson_arrivals(rate_hz: float, duration_s: float, seed: int) -> np.ndarray
     n = int(rate_hz * duration_s * 1.2) + 16
     t = np.cumsum(g.exponential(1.0 / rate_hz, size=n))
     return t[t < duration_s]
+
+
+# --- volumes ----------------------------------------------------------------
+# 3D inputs are ``uint8`` arrays ``[D][H][W]`` (slice, row, column).
+
+def bernoulli3d(D: int, H: int, W: int, p: float, seed: int) -> np.ndarray:
+    """I.i.d. foreground voxels with probability ``p``; drawn slice by slice
+    from one generator (the same stream as a single ``(D, H, W)`` draw)."""
+    g = rng(seed)
+    out = np.empty((D, H, W), dtype=np.uint8)
+    for z in range(D):
+        out[z] = g.random((H, W)) < p
+    return out
+
+
+def smoothed3d(D: int, H: int, W: int, sigma: float, density: float, seed: int) -> np.ndarray:
+    """White noise smoothed by a separable Gaussian along all three axes
+    (periodic edges), thresholded so that about ``density`` is foreground."""
+    from scipy.ndimage import gaussian_filter1d
+
+    f = rng(seed).standard_normal((D, H, W))
+    for ax in range(3):
+        f = gaussian_filter1d(f, sigma, axis=ax, mode="wrap")
+    t = np.quantile(f, 1.0 - density)
+    return (f > t).astype(np.uint8)
+
+
+def shells(N: int) -> np.ndarray:
+    """Concentric 1-voxel cube shells around voxel (N//2, N//2, N//2) at
+    Chebyshev radius 0, 3, 6, ..., each drawn only if it lies inside the
+    volume: ``ring_count(N)`` components under both connectivities."""
+    c = N // 2
+    rmax = min(c, N - 1 - c)
+    zs, ys, xs = np.ogrid[:N, :N, :N]
+    d = np.maximum(np.maximum(np.abs(xs - c), np.abs(ys - c)), np.abs(zs - c))
+    return ((d % 3 == 0) & (d <= rmax - rmax % 3)).astype(np.uint8)
+
+
+def comb3d(D: int, H: int, W: int) -> np.ndarray:
+    """Even slices hold the serpentine ``comb(H, W)``; each odd slice holds the
+    single voxel (x=0, y=0), which joins the combs above and below it.  One
+    component under both connectivities, crossing every block face."""
+    out = np.zeros((D, H, W), dtype=np.uint8)
+    out[0::2] = comb(H, W)
+    out[1::2, 0, 0] = 1
+    return out

@@ -41,7 +41,7 @@ MUTATIONS = {
 }
 
 
-def _build_variant(tmp_path, name, subs):
+def _build_variant(tmp_path, name, subs, symbol="ccl_oracle_two_pass"):
     text = open(SRC).read()
     for sub in subs:
         old, new = sub[0], sub[1]
@@ -53,10 +53,10 @@ def _build_variant(tmp_path, name, subs):
     c.write_text(text)
     subprocess.check_call(["gcc", "-O1", "-std=c11", "-shared", "-fPIC", str(c), "-o", str(so)])
     lib = ctypes.CDLL(str(so))
-    fn = lib.ccl_oracle_two_pass
+    fn = getattr(lib, symbol)
     fn.restype = ctypes.c_int
-    fn.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
-                   ctypes.c_int, ctypes.c_void_p]
+    nsizes = 4 if symbol.startswith("ccl_oracle3d") else 3
+    fn.argtypes = [ctypes.c_void_p] + [ctypes.c_int64] * nsizes + [ctypes.c_int, ctypes.c_void_p]
     return fn
 
 
@@ -97,5 +97,66 @@ def test_planted_mistake_is_caught(tmp_path, name):
     ok = _battery_passes(fn)
     if name == "no_mutation":
         assert ok, "the unmodified oracle must pass its own battery"
+    else:
+        assert not ok, f"planted mistake '{name}' went unnoticed"
+
+
+# --- the volume routine -------------------------------------------------------------
+
+MUTATIONS3 = {
+    # every planted mistake keeps the routine inside its buffers: it drops or
+    # misplaces links and reads, it never follows an unset parent
+    "no_mutation": [],
+    "previous_slice_skips_the_next_row": [
+        ("int earlier = dz < 0 || (dy < 0) || (dy == 0 && dx < 0);",
+         "int earlier = (dz < 0 && dy <= 0) || (dy < 0) || (dy == 0 && dx < 0);")],
+    "left_link_only_across_slices": [
+        ("int earlier = dz < 0 || (dy < 0) || (dy == 0 && dx < 0);",
+         "int earlier = dz < 0 || (dy < 0) || (dy == 0 && dx < 0 && dz < 0);")],
+    "eighteen_for_twenty_six": [
+        ("return conn == 26 || a == 1;", "return (conn == 26 && a <= 2) || a == 1;")],
+    "six_without_slice_links": [
+        ("return conn == 26 || a == 1;", "return conn == 26 || (a == 1 && dz == 0);")],
+    "slice_stride_not_scaled_by_pitch": [
+        ("return img[(z * H + y) * pitch + x] != 0;", "return img[z * H + y * pitch + x] != 0;")],
+    "label_without_plus_one": [
+        ("labels[p] = parent[p] < 0 ? 0 : 1 + uf_find(parent, (int32_t)p);",
+         "labels[p] = parent[p] < 0 ? 0 : uf_find(parent, (int32_t)p);")],
+}
+
+
+def _run3(fn, vol, conn):
+    D, H, W = vol.shape
+    pitch = vol.strides[1]
+    assert vol.strides[0] == pitch * H
+    out = np.empty((D, H, W), np.int32)
+    assert fn(vol.ctypes.data, D, H, W, pitch, conn, out.ctypes.data) == 0
+    return out
+
+
+def _battery3_passes(fn):
+    for conn in (6, 26):
+        for shape in ((2, 2, 2), (2, 2, 3), (2, 3, 2)):
+            n = shape[0] * shape[1] * shape[2]
+            for code in range(2 ** n):
+                vol = np.array([(code >> i) & 1 for i in range(n)], np.uint8).reshape(shape)
+                if not np.array_equal(_run3(fn, vol, conn), oracle.label3d_closure(vol, conn)):
+                    return False
+    g = np.random.default_rng(4)
+    base = (g.random((4, 5, 13)) < 0.45).astype(np.uint8)
+    padded = np.ones((4, 5, 16), np.uint8)
+    padded[:, :, :13] = base
+    for conn in (6, 26):
+        if not np.array_equal(_run3(fn, padded[:, :, :13], conn), oracle.label3d_closure(base, conn)):
+            return False
+    return True
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS3))
+def test_planted_mistake_in_volume_routine_is_caught(tmp_path, name):
+    fn = _build_variant(tmp_path, "v3_" + name, MUTATIONS3[name], symbol="ccl_oracle3d_two_pass")
+    ok = _battery3_passes(fn)
+    if name == "no_mutation":
+        assert ok, "the unmodified volume routine must pass its own battery"
     else:
         assert not ok, f"planted mistake '{name}' went unnoticed"
