@@ -304,6 +304,30 @@ ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int
                              int32_t *labels, unsigned long long *counters, void *stream);
 
 /*
+ * Label a 3D binary volume (Sec. 1 poses the task for 2D and 3D images; the
+ * three steps of Sec. 3 are applied to blocks of 32 x 16 x 16 voxels).
+ *   img          device, u8; voxel (x, y, z) at img[(z * H + y) * pitch + x]
+ *                (row stride pitch, slice stride H * pitch); nonzero =
+ *                foreground.
+ *   D, H, W      slices, rows, columns.
+ *   pitch        input row stride in bytes, >= W.
+ *   connectivity 6 (face neighbours) or 26 (face, edge and corner neighbours).
+ *   labels       device, int32 [D][H][W] dense, written in full: 0 for
+ *                background, else 1 + the smallest raster position
+ *                x + y*W + z*W*H of the voxel's component.
+ *   stream       cudaStream_t; the call is stream-ordered and asynchronous.
+ * Uses a library-owned scratch buffer per (device, stream) of 5 KB per block,
+ * grown on demand (a cudaMalloc; call once outside stream capture before
+ * capturing).  Returns CCL_ERR_INVALID_ARG for NULL pointers, negative sizes,
+ * pitch < W, connectivity not in {6,26} or overlapping img/labels;
+ * CCL_ERR_UNSUPPORTED when D*H*W > 2^31 - 2; CCL_ERR_OUT_OF_MEMORY when the
+ * scratch cannot grow; CCL_ERR_CUDA when a launch fails.  Iteration caps are
+ * reported by ccl_get_device_status().
+ */
+ccl_status ccl_label_3d(const uint8_t *img, int D, int H, int W, size_t pitch, int connectivity,
+                        int32_t *labels, void *stream);
+
+/*
  * Test hook for failure detection: caps every find/union loop in the kernels
  * at `cap` iterations (cap <= 0 restores the default, which no valid input
  * can reach).  A low cap makes the loops give up, set the device error word

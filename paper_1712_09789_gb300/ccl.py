@@ -81,6 +81,8 @@ _SIGS = {
                                        _c.POINTER(_c.c_int), _c.c_void_p]),
     "ccl_label_variant": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_int, _c.c_void_p,
                                      _c.POINTER(_c.c_ulonglong), _c.c_void_p]),
+    "ccl_label_3d": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
+                                _c.c_void_p]),
     "ccl_label_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p]),
     "ccl_label_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_int, _c.c_void_p]),
     "ccl_autotune_batched": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.c_void_p,
@@ -191,6 +193,38 @@ def ccl_label_noalloc(img, connectivity: int = 8, labels=None, stream=None):
     st = load().ccl_label_noalloc(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                                   _stream_ptr(stream, img.device))
     _check(st, "ccl_label_noalloc")
+    return labels
+
+
+def ccl_label_3d(vol, connectivity: int = 26, labels=None, stream=None):
+    """Canonical labels of a device volume (``ccl_label_3d``): ``vol`` is a 3D
+    ``torch.uint8`` CUDA tensor ``[D][H][W]`` with contiguous rows and a slice
+    stride of H row strides; ``labels`` a contiguous int32 ``[D][H][W]``
+    tensor (allocated when None).  Returns ``labels``."""
+    import torch
+
+    if not isinstance(vol, torch.Tensor) or vol.dtype != torch.uint8 or vol.dim() != 3:
+        raise ValueError("volume must be a 3D torch.uint8 tensor")
+    if not vol.is_cuda:
+        raise ValueError("volume must be a CUDA tensor")
+    D, H, W = vol.shape
+    # numpy-style strides of extent-1 dimensions carry no meaning
+    if W > 1 and vol.stride(2) != 1:
+        raise ValueError("volume rows must be contiguous (stride(2) == 1)")
+    if H > 1:
+        pitch = vol.stride(1)
+        if D > 1 and vol.stride(0) != pitch * H:
+            raise ValueError("the slice stride must be H times the row stride")
+    else:
+        pitch = vol.stride(0) if D > 1 else W
+    if labels is None:
+        labels = torch.empty((D, H, W), dtype=torch.int32, device=vol.device)
+    elif (labels.dtype != torch.int32 or tuple(labels.shape) != (D, H, W) or not labels.is_contiguous()
+          or labels.device != vol.device):
+        raise ValueError("labels must be a contiguous int32 tensor of the volume's shape and device")
+    st = load().ccl_label_3d(vol.data_ptr(), D, H, W, pitch, connectivity, labels.data_ptr(),
+                             _stream_ptr(stream, vol.device))
+    _check(st, "ccl_label_3d")
     return labels
 
 

@@ -27,6 +27,7 @@ std::map<std::pair<int, cudaStream_t>, DevBuf> g_scratch;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_img;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_lab;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_stats;  // component statistics scratch
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_volume; // face records of the 3D labelling
 
 ccl_status grow(DevBuf &b, size_t need) {
     if (b.bytes >= need) return CCL_OK;
@@ -275,9 +276,45 @@ const char *ccl_debug_kernel_name(int kind) { return ccl::kernel_kind_name(kind)
 
 ccl_status ccl_get_device_status(void *stream) {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CCL_ERR_CUDA;
-    int v = 0;
+    int v = 0, vv = 0;
     if (ccl::read_and_clear_device_error(&v) != 0) return CCL_ERR_CUDA;
-    return v ? CCL_ERR_DEVICE_TIMEOUT : CCL_OK;
+    if (ccl::read_and_clear_volume_error(&vv) != 0) return CCL_ERR_CUDA;
+    return (v | vv) ? CCL_ERR_DEVICE_TIMEOUT : CCL_OK;
+}
+
+ccl_status ccl_label_3d(const uint8_t *img, int D, int H, int W, size_t pitch, int connectivity, int32_t *labels,
+                        void *stream) {
+    if (D < 0 || H < 0 || W < 0) return CCL_ERR_INVALID_ARG;
+    if (connectivity != 6 && connectivity != 26) return CCL_ERR_INVALID_ARG;
+    if (D == 0 || H == 0 || W == 0) return CCL_OK;
+    if (!img || !labels) return CCL_ERR_INVALID_ARG;
+    if (pitch < (size_t)W) return CCL_ERR_INVALID_ARG;
+    const long long n = (long long)D * (long long)H * (long long)W;
+    if (n > 2147483646LL) return CCL_ERR_UNSUPPORTED;
+    // the input span and the output span must not overlap
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(img);
+    const uintptr_t i1 = i0 + (size_t)((long long)D * H - 1) * pitch + (size_t)W;
+    const uintptr_t o0 = reinterpret_cast<uintptr_t>(labels);
+    const uintptr_t o1 = o0 + (size_t)n * sizeof(int32_t);
+    if (i0 < o1 && o0 < i1) return CCL_ERR_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t need = ccl::volume_workspace_bytes(D, H, W);
+    void *ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        DevBuf &b = g_volume[{dev, s}];
+        if (b.bytes < need) {
+            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+            const ccl_status st = grow(b, need);
+            if (st != CCL_OK) return st;
+        }
+        ws = b.ptr;
+    }
+    if (ccl::launch_volume(img, D, H, W, pitch, connectivity, labels, ws, s, current_cap()) != 0)
+        return CCL_ERR_CUDA;
+    return CCL_OK;
 }
 
 }  // extern "C"

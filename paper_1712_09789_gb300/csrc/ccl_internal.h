@@ -83,8 +83,16 @@ size_t stats_workspace_bytes(int H, int W);
 int launch_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, void *ws,
                  uint32_t *count_dev, int *bad_dev, cudaStream_t stream);
 
+// 3D volumes (ccl_volume.cu): scratch bytes (face records) for a D x H x W
+// volume, and the enqueued labelling (row stride pitch, slice stride
+// H * pitch; connectivity 6 or 26).  Returns 0, or -1 when a launch failed.
+size_t volume_workspace_bytes(int D, int H, int W);
+int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
+                  cudaStream_t stream, int cap);
+
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
+int read_and_clear_volume_error(int *value);
 
 // Argument checks and iteration cap of the C ABI, for entry points that live
 // in other translation units (same rules as ccl_label()).

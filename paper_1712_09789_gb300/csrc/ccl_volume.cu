@@ -1,0 +1,495 @@
+// ccl_volume.cu -- connected components of a 3D binary volume.
+//
+// Sec. 1 states the labelling task for 2D and 3D images; the paper works the
+// method out in 2D.  This is the same coarse-to-fine structure one dimension
+// up, on blocks of 32 x 16 x 16 voxels (one CTA, one thread per 32-voxel row
+// held as a bit mask):
+//   k_vol_local  step 1 (Sec. 3.1): rows become runs; each run is linked to
+//                the runs it touches in the earlier rows of its block (the
+//                row above, the row in the slice before, and under
+//                26-connectivity the two diagonal rows of the slice before,
+//                with x widened by one voxel) by a shared-memory union-find
+//                whose links go from the larger block position to the
+//                smaller, so a root is its component's first voxel in raster
+//                order.  Roots of components that reach a block face get a
+//                forest entry in `labels` (own position + 1), and the local
+//                root of every face voxel goes to a compact face record.
+//   k_vol_merge  step 2 (Sec. 3.2): every voxel pair across a block face is
+//                joined in the global forest (lock-free atomicMin union);
+//                a pair that crosses several faces is taken by the z face,
+//                else the y face, else the x face, so each pair is seen once.
+//   k_vol_write  step 3 (Sec. 3.3): the block's runs are recomputed from the
+//                volume, each root's final label is found (border roots by a
+//                walk of the global forest), and every voxel of the block is
+//                written once, as whole 128-byte rows.
+// Labels: 1 + min raster position x + y*W + z*W*H of the component, 0 for
+// background.  The forest lives in `labels` at border-root positions only;
+// the write-out overwrites such an entry with its final value, which is still
+// a pointer to the same tree's root, so concurrent walks stay valid.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "ccl_block.cuh"
+#include "ccl_internal.h"
+
+namespace ccl {
+namespace {
+
+constexpr int kVX = 32, kVY = 16, kVZ = 16;  // block: voxels along x, y, z
+constexpr int kVRows = kVY * kVZ;            // rows of 32 voxels per block
+constexpr int kVThreads = kVRows;            // one thread per row
+constexpr int kVIds = kVRows * kVX;          // ids: row * 32 + x (row = z * kVY + y)
+constexpr uint16_t kNoRoot = 0xFFFF;         // face record of a background voxel
+constexpr uint32_t kFinal = 0x80000000u;     // root entry holding its final label
+// face records per block, u16 local root ids: x faces [side][row],
+// y faces [side][z][x], z faces [side][y][x]
+constexpr int kFX = 2 * kVRows;
+constexpr int kFYLo = kFX, kFYHi = kFX + kVZ * kVX;
+constexpr int kFZLo = kFX + 2 * kVZ * kVX, kFZHi = kFZLo + kVY * kVX;
+constexpr int kFaceEntries = kFZHi + kVY * kVX;
+static_assert(kVIds <= 0x8000, "ids must fit the face records");
+static_assert((kFaceEntries * 2) % 16 == 0, "face records stay 16-byte aligned");
+
+__device__ int g_volume_error = 0;
+
+struct VolArgs {
+    const uint8_t *img;
+    int32_t *labels;
+    uint16_t *faces;
+    unsigned long long pitch;
+    int D, H, W;
+    int n;  // voxels, D * H * W
+    int nbx, nby, nbz;
+    int vec_in;
+    int local_cap, global_cap;
+};
+
+struct VolSmem {
+    uint32_t mask[kVRows];    // row masks (bit x = voxel x of the row)
+    uint32_t border[kVRows];  // bit x of row r: id r*32+x is the root of a component on a block face
+    uint32_t par[kVIds];      // union-find entries, by slot(id); used at run starts only
+};
+
+// Storage slot of an id: rows keep their 32 entries, rotated by the row so
+// that threads on different rows touching the same column use other banks.
+__device__ __forceinline__ int slot(int id) { return (id & ~31) | ((id + (id >> 5)) & 31); }
+
+// Last voxel of the run of m that holds voxel b.
+__device__ __forceinline__ int run_end(uint32_t m, int b) {
+    const uint32_t z = ~m & (~0u << b);
+    return z ? lobit(z) - 1 : 31;
+}
+
+__device__ __forceinline__ long long vpos(const VolArgs &a, int x, int y, int z) {
+    return (long long)x + (long long)a.W * ((long long)y + (long long)a.H * z);
+}
+
+__device__ __forceinline__ int v_find(volatile uint32_t *par, int x, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        const int p = (int)par[slot(x)];
+        if (p == x) return x;
+        const int q = (int)par[slot(p)];
+        if (q == p) return p;
+        par[slot(x)] = (uint32_t)q;  // halving: an ancestor, never loses a link
+        x = q;
+    }
+    err |= kErrLocalCap;
+    return x;
+}
+
+// Root of x without writing: used once the unions are done, while other
+// threads store roots into their own entries (a halving store here could put
+// a non-root ancestor back over such a root).
+__device__ __forceinline__ int v_find_ro(const volatile uint32_t *par, int x, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        const int p = (int)par[slot(x)];
+        if (p == x) return x;
+        x = p;
+    }
+    err |= kErrLocalCap;
+    return x;
+}
+
+// Joins the sets of ids a and b; the larger root is hung under the smaller.
+__device__ void v_union(uint32_t *par, int a, int b, int cap, int &err) {
+    volatile uint32_t *vp = par;
+    for (int i = 0; i < cap; ++i) {
+        a = v_find(vp, a, cap, err);
+        b = v_find(vp, b, cap, err);
+        if (a == b || err) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = (int)atomicMin(par + slot(a), (uint32_t)b);
+        if (old == a) return;
+        a = old;  // a gained a parent meanwhile: join that one instead
+    }
+    err |= kErrLocalCap;
+}
+
+// Global forest in `labels`: the entry of a border root holds parent + 1.
+// A parent outside the volume can only come from an entry that a capped run
+// left unset; the walk then stops with the cap error instead of reading it.
+__device__ int vg_find(int32_t *lab, int n, int g, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        const int p = __ldcg(lab + g) - 1;
+        if (p == g) return g;
+        if ((unsigned)p >= (unsigned)n) break;
+        const int q = __ldcg(lab + p) - 1;
+        if (q == p) return p;
+        if ((unsigned)q >= (unsigned)n) break;
+        __stcg(lab + g, q + 1);
+        g = q;
+    }
+    err |= kErrGlobalCap;
+    return g;
+}
+
+__device__ void vg_union(int32_t *lab, int n, int a, int b, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        a = vg_find(lab, n, a, cap, err);
+        b = vg_find(lab, n, b, cap, err);
+        if (a == b || err) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(lab + a, b + 1) - 1;
+        if (old == a) return;
+        if ((unsigned)old >= (unsigned)n) break;
+        a = old;
+    }
+    err |= kErrGlobalCap;
+}
+
+__device__ int vg_find_ro(const int32_t *lab, int n, int g, int cap, int &err) {
+    for (int i = 0; i < cap; ++i) {
+        const int p = __ldcg(lab + g) - 1;
+        if (p == g) return g;
+        if ((unsigned)p >= (unsigned)n) break;
+        g = p;
+    }
+    err |= kErrGlobalCap;
+    return g;
+}
+
+// Links every run of row r (mask m, run starts st) to the runs of the earlier
+// row n that it touches (x widened by one voxel under 26-connectivity).
+template <bool k26>
+__device__ __forceinline__ void link_rows(VolSmem &sm, int r, uint32_t m, uint32_t st, int n, int cap, int &err) {
+    const uint32_t mn = sm.mask[n];
+    if (!(m & touch_range<k26>(mn))) return;
+    const uint32_t sn = mn & ~(mn << 1);
+    for (uint32_t t = st; t; t &= t - 1) {
+        const int s = lobit(t);
+        uint32_t c = mn & touch_range<k26>(run_bits(s, run_end(m, s)));
+        while (c) {
+            const int b = lobit(c);
+            v_union(sm.par, r * kVX + s, n * kVX + hibit(sn & upto(b)), cap, err);
+            const int ne = run_end(mn, b);
+            c = ne == 31 ? 0u : c & (~0u << (ne + 1));
+        }
+    }
+}
+
+// Step 1 inside the block (bx, by, bz): masks, runs, unions, compression and
+// the border-root marks.  Ends with a barrier; the thread's row mask is
+// returned.
+template <bool k26>
+__device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int bz, int &err) {
+    const int r = threadIdx.x, y = r % kVY, z = r / kVY;
+    const int gx0 = bx * kVX, gy = by * kVY + y, gz = bz * kVZ + z;
+    uint32_t m = 0;
+    if (gy < a.H && gz < a.D) {
+        const uint8_t *p = a.img + ((size_t)gz * a.H + gy) * a.pitch + gx0;
+        if (a.vec_in && gx0 + kVX <= a.W) {
+            const uint4 lo = ldg_nc16(p), hi = ldg_nc16(p + 16);
+            m = nz16(lo) | (nz16(hi) << 16);
+        } else {
+            const int n = a.W - gx0 < kVX ? a.W - gx0 : kVX;
+            for (int i = 0; i < n; ++i) m |= (uint32_t)(__ldg(p + i) != 0) << i;
+        }
+    }
+    sm.mask[r] = m;
+    sm.border[r] = 0;
+    const uint32_t st = m & ~(m << 1);
+    for (uint32_t t = st; t; t &= t - 1) {
+        const int id = r * kVX + lobit(t);
+        sm.par[slot(id)] = (uint32_t)id;
+    }
+    __syncthreads();
+
+    if (m) {
+        if (y > 0) link_rows<k26>(sm, r, m, st, r - 1, a.local_cap, err);
+        if (z > 0) {
+            link_rows<k26>(sm, r, m, st, r - kVY, a.local_cap, err);
+            if (k26) {
+                if (y > 0) link_rows<k26>(sm, r, m, st, r - kVY - 1, a.local_cap, err);
+                if (y < kVY - 1) link_rows<k26>(sm, r, m, st, r - kVY + 1, a.local_cap, err);
+            }
+        }
+    }
+    __syncthreads();
+
+    for (uint32_t t = st; t; t &= t - 1) {
+        const int id = r * kVX + lobit(t);
+        sm.par[slot(id)] = (uint32_t)v_find_ro(sm.par, id, a.local_cap, err);
+    }
+    __syncthreads();
+
+    // faces that have a neighbouring block: whole rows on y/z faces, the
+    // first and last voxel of every row on x faces
+    const bool face_row = (y == 0 && by > 0) || (y == kVY - 1 && by < a.nby - 1) || (z == 0 && bz > 0) ||
+                          (z == kVZ - 1 && bz < a.nbz - 1);
+    uint32_t fm = m & (face_row ? ~0u : ((bx > 0 ? 1u : 0u) | (bx < a.nbx - 1 ? 0x80000000u : 0u)));
+    while (fm) {
+        const int b = lobit(fm);
+        const int root = (int)sm.par[slot(r * kVX + hibit(st & upto(b)))];
+        atomicOr(&sm.border[root / kVX], 1u << (root % kVX));
+        const int e = run_end(m, b);
+        fm = e == 31 ? 0u : fm & (~0u << (e + 1));
+    }
+    __syncthreads();
+    return m;
+}
+
+__device__ __forceinline__ void block_coords(const VolArgs &a, int &bx, int &by, int &bz) {
+    const int b = blockIdx.x;
+    bx = b % a.nbx;
+    by = (b / a.nbx) % a.nby;
+    bz = b / (a.nbx * a.nby);
+}
+
+template <bool k26>
+__global__ void __launch_bounds__(kVThreads) k_vol_local(VolArgs a) {
+    __shared__ VolSmem sm;
+    int bx, by, bz;
+    block_coords(a, bx, by, bz);
+    int err = 0;
+    const uint32_t m = vol_local<k26>(sm, a, bx, by, bz, err);
+    const int r = threadIdx.x, y = r % kVY, z = r / kVY;
+    const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
+
+    // forest entries of the border roots on the own row
+    for (uint32_t t = sm.border[r]; t; t &= t - 1) {
+        const long long g = vpos(a, gx0 + lobit(t), gy0 + y, gz0 + z);
+        a.labels[g] = (int32_t)(g + 1);
+    }
+
+    // face records (only faces that have a neighbouring block are read)
+    uint16_t *f = a.faces + (size_t)blockIdx.x * kFaceEntries;
+    const uint32_t st = m & ~(m << 1);
+    if (bx > 0) f[r] = (m & 1u) ? (uint16_t)sm.par[slot(r * kVX)] : kNoRoot;
+    if (bx < a.nbx - 1) f[kVRows + r] = (m >> 31) ? (uint16_t)sm.par[slot(r * kVX + hibit(st))] : kNoRoot;
+    for (int e = r; e < 4 * kVY * kVX; e += kVThreads) {
+        const int face = e / (kVY * kVX), i = e % (kVY * kVX), u = i / kVX, x = i % kVX;
+        bool need;
+        int row;
+        switch (face) {
+            case 0: need = by > 0; row = u * kVY; break;                          // y = 0, u = z
+            case 1: need = by < a.nby - 1; row = u * kVY + kVY - 1; break;        // y = last
+            case 2: need = bz > 0; row = u; break;                                // z = 0, u = y
+            default: need = bz < a.nbz - 1; row = (kVZ - 1) * kVY + u; break;     // z = last
+        }
+        if (!need) continue;
+        const uint32_t mr = sm.mask[row];
+        uint16_t v = kNoRoot;
+        if ((mr >> x) & 1u) {
+            const uint32_t sr = mr & ~(mr << 1);
+            v = (uint16_t)sm.par[slot(row * kVX + hibit(sr & upto(x)))];
+        }
+        f[kFX + e] = v;
+    }
+    if (err) atomicOr(&g_volume_error, err);
+}
+
+// Position of local id `id` of block (bx, by, bz).
+__device__ __forceinline__ int id_pos(const VolArgs &a, int bx, int by, int bz, int id) {
+    const int row = id / kVX;
+    return (int)vpos(a, bx * kVX + id % kVX, by * kVY + row % kVY, bz * kVZ + row / kVY);
+}
+
+template <bool k26>
+__global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
+    int bx, by, bz;
+    block_coords(a, bx, by, bz);
+    const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
+    const uint16_t *own = a.faces + (size_t)blockIdx.x * kFaceEntries;
+    constexpr int kR = k26 ? 1 : 0;
+    int err = 0;
+    int last_q = -1, last_p = -1;
+    auto join = [&](int q, int p) {
+        if (q == last_q && p == last_p) return;
+        last_q = q;
+        last_p = p;
+        vg_union(a.labels, a.n, q, p, a.global_cap, err);
+    };
+    // z face: own slice 0 against the last slice of the blocks below
+    if (bz > 0) {
+        for (int e = threadIdx.x; e < kVY * kVX; e += kVThreads) {
+            const int q = own[kFZLo + e];
+            if (q == kNoRoot) continue;
+            const int gx = gx0 + e % kVX, gy = gy0 + e / kVX;
+            const int qg = id_pos(a, bx, by, bz, q);
+            for (int dy = -kR; dy <= kR; ++dy) {
+                for (int dx = -kR; dx <= kR; ++dx) {
+                    const int nx = gx + dx, ny = gy + dy;
+                    if (nx < 0 || ny < 0 || nx >= a.W || ny >= a.H) continue;
+                    const int nbx = nx / kVX, nby = ny / kVY;
+                    const uint16_t *nf = a.faces + (size_t)(((bz - 1) * a.nby + nby) * a.nbx + nbx) * kFaceEntries;
+                    const int p = nf[kFZHi + (ny % kVY) * kVX + nx % kVX];
+                    if (p != kNoRoot) join(qg, id_pos(a, nbx, nby, bz - 1, p));
+                }
+            }
+        }
+    }
+    // y face: own row y = 0 against row y = last of the blocks in front, in
+    // the same z block
+    if (by > 0) {
+        for (int e = threadIdx.x; e < kVZ * kVX; e += kVThreads) {
+            const int q = own[kFYLo + e];
+            if (q == kNoRoot) continue;
+            const int z = e / kVX, gx = gx0 + e % kVX;
+            const int qg = id_pos(a, bx, by, bz, q);
+            for (int dz = -kR; dz <= kR; ++dz) {
+                const int zz = z + dz;
+                if (zz < 0 || zz >= kVZ || gz0 + zz >= a.D) continue;
+                for (int dx = -kR; dx <= kR; ++dx) {
+                    const int nx = gx + dx;
+                    if (nx < 0 || nx >= a.W) continue;
+                    const int nbx = nx / kVX;
+                    const uint16_t *nf = a.faces + (size_t)((bz * a.nby + by - 1) * a.nbx + nbx) * kFaceEntries;
+                    const int p = nf[kFYHi + zz * kVX + nx % kVX];
+                    if (p != kNoRoot) join(qg, id_pos(a, nbx, by - 1, bz, p));
+                }
+            }
+        }
+    }
+    // x face: own first voxels against the last voxels of the block to the
+    // left, in the same y and z block
+    if (bx > 0) {
+        const uint16_t *nf = a.faces + (size_t)(blockIdx.x - 1) * kFaceEntries;
+        for (int r = threadIdx.x; r < kVRows; r += kVThreads) {
+            const int q = own[r];
+            if (q == kNoRoot) continue;
+            const int y = r % kVY, z = r / kVY;
+            const int qg = id_pos(a, bx, by, bz, q);
+            for (int dz = -kR; dz <= kR; ++dz) {
+                const int zz = z + dz;
+                if (zz < 0 || zz >= kVZ || gz0 + zz >= a.D) continue;
+                for (int dy = -kR; dy <= kR; ++dy) {
+                    const int yy = y + dy;
+                    if (yy < 0 || yy >= kVY || gy0 + yy >= a.H) continue;
+                    const int p = nf[kVRows + zz * kVY + yy];
+                    if (p != kNoRoot) join(qg, id_pos(a, bx - 1, by, bz, p));
+                }
+            }
+        }
+    }
+    if (err) atomicOr(&g_volume_error, err);
+}
+
+template <bool k26>
+__global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
+    __shared__ VolSmem sm;
+    int bx, by, bz;
+    block_coords(a, bx, by, bz);
+    int err = 0;
+    const uint32_t m = vol_local<k26>(sm, a, bx, by, bz, err);
+    const int r = threadIdx.x;
+    const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
+
+    // final label of every root of the own row (only this thread touches
+    // these entries now)
+    const uint32_t st = m & ~(m << 1);
+    const uint32_t br = sm.border[r];
+    for (uint32_t t = st; t; t &= t - 1) {
+        const int s = lobit(t), id = r * kVX + s;
+        if ((int)sm.par[slot(id)] != id) continue;
+        const int g = (int)vpos(a, gx0 + s, gy0 + r % kVY, gz0 + r / kVY);
+        const int root = ((br >> s) & 1u) ? vg_find_ro(a.labels, a.n, g, a.global_cap, err) : g;
+        sm.par[slot(id)] = kFinal | (uint32_t)(root + 1);
+    }
+    __syncthreads();
+
+    // whole rows, one warp per row, lane = x
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int gx = gx0 + lane;
+    for (int row = warp; row < kVRows; row += kVThreads / 32) {
+        const int gy = gy0 + row % kVY, gz = gz0 + row / kVY;
+        if (gy >= a.H || gz >= a.D) continue;
+        if (gx >= a.W) continue;
+        const uint32_t mr = sm.mask[row];
+        int32_t v = 0;
+        if ((mr >> lane) & 1u) {
+            const uint32_t sr = mr & ~(mr << 1);
+            const uint32_t e = sm.par[slot(row * kVX + hibit(sr & upto(lane)))];
+            v = (int32_t)((e & kFinal) ? e & ~kFinal : sm.par[slot((int)e)] & ~kFinal);
+        }
+        __stcs(a.labels + vpos(a, gx, gy, gz), v);
+    }
+    if (err) atomicOr(&g_volume_error, err);
+}
+
+void volume_grid(int D, int H, int W, int &nbx, int &nby, int &nbz) {
+    nbx = (W + kVX - 1) / kVX;
+    nby = (H + kVY - 1) / kVY;
+    nbz = (D + kVZ - 1) / kVZ;
+}
+
+}  // namespace
+
+size_t volume_workspace_bytes(int D, int H, int W) {
+    int nbx, nby, nbz;
+    volume_grid(D, H, W, nbx, nby, nbz);
+    const size_t bytes = (size_t)nbx * nby * nbz * kFaceEntries * sizeof(uint16_t);
+    return (bytes + 255) & ~(size_t)255;
+}
+
+int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
+                  cudaStream_t stream, int cap) {
+    VolArgs a;
+    a.img = img;
+    a.labels = labels;
+    a.faces = static_cast<uint16_t *>(ws);
+    a.pitch = pitch;
+    a.D = D;
+    a.H = H;
+    a.W = W;
+    a.n = (int)((long long)D * H * W);
+    volume_grid(D, H, W, a.nbx, a.nby, a.nbz);
+    a.vec_in = (pitch % 16 == 0) && (reinterpret_cast<uintptr_t>(img) % 16 == 0);
+    // a find walks a strictly decreasing chain and a union retry strictly
+    // lowers its node, so neither can take more steps than there are nodes
+    const long long n = (long long)D * H * W;
+    a.local_cap = cap > 0 ? cap : kVIds + 16;
+    a.global_cap = cap > 0 ? cap : (int)(n + 16 < (1LL << 30) ? n + 16 : (1LL << 30));
+    const unsigned blocks = (unsigned)((long long)a.nbx * a.nby * a.nbz);
+    if (conn == 26) {
+        k_vol_local<true><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_merge<true><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<true><<<blocks, kVThreads, 0, stream>>>(a);
+    } else {
+        k_vol_local<false><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_merge<false><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<false><<<blocks, kVThreads, 0, stream>>>(a);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int read_and_clear_volume_error(int *value) {
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_volume_error, sizeof(int)) != cudaSuccess) return -1;
+    if (v) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_volume_error, &zero, sizeof(int)) != cudaSuccess) return -1;
+    }
+    *value = v;
+    return 0;
+}
+
+}  // namespace ccl

@@ -108,3 +108,20 @@ def test_component_stats_argument_checks(lib):
     assert lib.ccl_component_stats(None, 4, 4, None, 0, None, None) == ccl.CCL_ERR_INVALID_ARG
     assert lib.ccl_component_stats(None, 65536, 32768, None, 0, ctypes.byref(n), None) == ccl.CCL_ERR_UNSUPPORTED
     assert lib.ccl_component_stats(None, 0, 4, None, 0, ctypes.byref(n), None) == ccl.CCL_OK and n.value == 0
+
+
+def test_volume_argument_checks(lib):
+    # host-side checks only: every case below returns before a launch
+    f = lib.ccl_label_3d
+    vin, vout = 0x100000, 0x40000000
+    for conn in (4, 8, 18, 0):
+        assert f(vin, 2, 2, 2, 2, conn, vout, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(vin, -1, 2, 2, 2, 6, vout, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(vin, 2, 2, -2, 2, 26, vout, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(None, 0, 5, 5, 5, 6, None, None) == ccl.CCL_OK
+    assert f(None, 5, 5, 0, 5, 26, None, None) == ccl.CCL_OK
+    assert f(None, 2, 2, 2, 2, 6, vout, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(vin, 2, 2, 2, 2, 6, None, None) == ccl.CCL_ERR_INVALID_ARG
+    assert f(vin, 2, 2, 4, 3, 6, vout, None) == ccl.CCL_ERR_INVALID_ARG          # pitch < W
+    assert f(vin, 2048, 1024, 1024, 1024, 6, vout, None) == ccl.CCL_ERR_UNSUPPORTED
+    assert f(vin, 4, 4, 4, 4, 26, vin + 8, None) == ccl.CCL_ERR_INVALID_ARG     # overlapping buffers
