@@ -159,37 +159,63 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t
     const uint32_t lim = ncomp < (uint32_t)capacity ? ncomp : (uint32_t)capacity;
     const long long n = (long long)H * W;
     const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;
+    const int lane = threadIdx.x & 31;
     int nbad = 0;
+    // the lanes of a warp read 32 neighbouring pixels of a row; lanes of one
+    // component are folded first (one shared-memory update per component and
+    // warp step), the coordinate sums in 32 bits when no 32 coordinates can
+    // overflow them
+    const bool warp_sums = W <= (1 << 26) && H <= (1 << 26);
     for (int i = threadIdx.x; i < kTileH * kTileW; i += kStatThreads) {
         const int x = tx0 + (i % kTileW), y = ty0 + i / kTileW;
-        if (x >= W || y >= H) continue;
-        const int32_t l = labels[(long long)y * W + x];
-        if (l == 0) continue;
-        // a label must name a root of the image (canonical labels); anything
-        // else is counted and skipped
-        if (l < 0 || (long long)l > n || !is_root(labels, (long long)l - 1)) {
-            ++nbad;
-            continue;
+        uint32_t k = kEmpty;
+        if (x < W && y < H) {
+            const int32_t l = labels[(long long)y * W + x];
+            if (l != 0) {
+                // a label must name a root of the image (canonical labels);
+                // anything else is counted and skipped
+                if (l < 0 || (long long)l > n || !is_root(labels, (long long)l - 1)) {
+                    ++nbad;
+                } else {
+                    k = rootmap[l - 1];
+                    if (k >= lim) k = kEmpty;
+                }
+            }
         }
-        const uint32_t k = rootmap[l - 1];
-        if (k >= lim) continue;
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
+        if (k == kEmpty) continue;
+        const int a = __popc(peers);
+        const int gx0 = (int)__reduce_min_sync(peers, (unsigned)x), gx1 = (int)__reduce_max_sync(peers, (unsigned)x);
+        const int gy0 = (int)__reduce_min_sync(peers, (unsigned)y), gy1 = (int)__reduce_max_sync(peers, (unsigned)y);
+        unsigned long long gsx = (unsigned long long)x, gsy = (unsigned long long)y;
+        if (warp_sums) {
+            gsx = __reduce_add_sync(peers, (unsigned)x);
+            gsy = __reduce_add_sync(peers, (unsigned)y);
+        }
+        const bool leader = lane == __ffs(peers) - 1;
+        // without warp sums every lane adds its own coordinates
+        if (!leader && warp_sums) continue;
+        const int aa = leader ? a : 0;
         uint32_t h = (k * 2654435761u) >> 22;  // 10-bit hash
         bool done = false;
         for (int probe = 0; probe < 16 && !done; ++probe, h = (h + 1) & (kHash - 1)) {
             uint32_t cur = sm.key[h];
             if (cur == kEmpty) cur = atomicCAS(&sm.key[h], kEmpty, k);
             if (cur == kEmpty || cur == k) {
-                atomicAdd(&sm.area[h], 1);
-                atomicMin(&sm.x0[h], x);
-                atomicMin(&sm.y0[h], y);
-                atomicMax(&sm.x1[h], x);
-                atomicMax(&sm.y1[h], y);
-                atomicAdd(&sm.sx[h], (unsigned long long)x);
-                atomicAdd(&sm.sy[h], (unsigned long long)y);
+                if (aa) atomicAdd(&sm.area[h], aa);
+                if (leader) {
+                    atomicMin(&sm.x0[h], gx0);
+                    atomicMin(&sm.y0[h], gy0);
+                    atomicMax(&sm.x1[h], gx1);
+                    atomicMax(&sm.y1[h], gy1);
+                }
+                atomicAdd(&sm.sx[h], gsx);
+                atomicAdd(&sm.sy[h], gsy);
                 done = true;
             }
         }
-        if (!done) fold_global(out, k, 1, x, y, x, y, (unsigned long long)x, (unsigned long long)y);
+        if (!done) fold_global(out, k, aa, leader ? gx0 : INT_MAX, leader ? gy0 : INT_MAX, leader ? gx1 : -1,
+                               leader ? gy1 : -1, gsx, gsy);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < kHash; i += kStatThreads)
