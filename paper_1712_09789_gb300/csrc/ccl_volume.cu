@@ -42,6 +42,8 @@ constexpr int kVThreads = kVRows;            // one thread per row
 constexpr int kVIds = kVRows * kVX;          // ids: row * 32 + x (row = z * kVY + y)
 constexpr uint16_t kNoRoot = 0xFFFF;         // face record of a background voxel
 constexpr uint32_t kFinal = 0x80000000u;     // root entry holding its final label
+constexpr int kPairHash = 2048;              // root pairs remembered per CTA in the merge
+constexpr unsigned long long kNoPair = ~0ull;
 // face records per block, u16 local root ids: x faces [side][row],
 // y faces [side][z][x], z faces [side][y][x]
 constexpr int kFX = 2 * kVRows;
@@ -177,10 +179,15 @@ __device__ int vg_find_ro(const int32_t *lab, int n, int g, int cap, int &err) {
     return g;
 }
 
-// Links every run of row r (mask m, run starts st) to the runs of the earlier
-// row n that it touches (x widened by one voxel under 26-connectivity).
+// Contacts of the runs of row r (mask m, run starts st) with the runs of the
+// earlier row n (x widened by one voxel under 26-connectivity), visited per
+// run in increasing x.  Coarse labelling: the first contact of a run (over
+// the neighbour rows in a fixed order) became its parent before any union,
+// so it is skipped here (bit s of `first` marks run s as past it); every
+// later contact is joined by a union.
 template <bool k26>
-__device__ __forceinline__ void link_rows(VolSmem &sm, int r, uint32_t m, uint32_t st, int n, int cap, int &err) {
+__device__ __forceinline__ void link_rows(VolSmem &sm, int r, uint32_t m, uint32_t st, int n, uint32_t &first,
+                                          int cap, int &err) {
     const uint32_t mn = sm.mask[n];
     if (!(m & touch_range<k26>(mn))) return;
     const uint32_t sn = mn & ~(mn << 1);
@@ -189,11 +196,47 @@ __device__ __forceinline__ void link_rows(VolSmem &sm, int r, uint32_t m, uint32
         uint32_t c = mn & touch_range<k26>(run_bits(s, run_end(m, s)));
         while (c) {
             const int b = lobit(c);
-            v_union(sm.par, r * kVX + s, n * kVX + hibit(sn & upto(b)), cap, err);
+            if (first & (1u << s)) v_union(sm.par, r * kVX + s, n * kVX + hibit(sn & upto(b)), cap, err);
+            first |= 1u << s;
             const int ne = run_end(mn, b);
             c = ne == 31 ? 0u : c & (~0u << (ne + 1));
         }
     }
+}
+
+// The earlier rows a run can touch, in the order they are visited: the row
+// above, the row in the slice before, and under 26-connectivity the two
+// diagonal rows of the slice before.  Bit k of the returned mask says that
+// neighbour k exists inside the block.
+__device__ __forceinline__ constexpr int nb_off(int k) {
+    return k == 0 ? -1 : k == 1 ? -kVY : k == 2 ? -kVY - 1 : -kVY + 1;
+}
+template <bool k26>
+__device__ __forceinline__ uint32_t earlier_rows(int y, int z) {
+    uint32_t v = 0;
+    if (y > 0) v |= 1u;
+    if (z > 0) {
+        v |= 2u;
+        if (k26 && y > 0) v |= 4u;
+        if (k26 && y < kVY - 1) v |= 8u;
+    }
+    return v;
+}
+
+// First contact of run s of row r among the earlier rows, in the order
+// link_rows visits them; -1 when the run touches none.
+template <bool k26>
+__device__ __forceinline__ int first_contact(const VolSmem &sm, int r, uint32_t m, int s, uint32_t nbv) {
+    const uint32_t w = touch_range<k26>(run_bits(s, run_end(m, s)));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        if (!(nbv & (1u << k))) continue;
+        const int n = r + nb_off(k);
+        const uint32_t mn = sm.mask[n];
+        const uint32_t c = mn & w;
+        if (c) return n * kVX + hibit(mn & ~(mn << 1) & upto(lobit(c)));
+    }
+    return -1;
 }
 
 // Step 1 inside the block (bx, by, bz): masks, runs, unions, compression and
@@ -217,21 +260,25 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
     sm.mask[r] = m;
     sm.border[r] = 0;
     const uint32_t st = m & ~(m << 1);
+    const uint32_t nbv = earlier_rows<k26>(y, z);
+    __syncthreads();
+
+    // coarse labelling: each run takes its first contact (a run of an
+    // earlier row, hence a smaller id) as parent, or itself; only the own
+    // entries are written, so no atomics are needed
     for (uint32_t t = st; t; t &= t - 1) {
-        const int id = r * kVX + lobit(t);
-        sm.par[slot(id)] = (uint32_t)id;
+        const int s = lobit(t), id = r * kVX + s;
+        const int f = first_contact<k26>(sm, r, m, s, nbv);
+        sm.par[slot(id)] = (uint32_t)(f >= 0 ? f : id);
     }
     __syncthreads();
 
+    // refinement: the remaining contacts by union
     if (m) {
-        if (y > 0) link_rows<k26>(sm, r, m, st, r - 1, a.local_cap, err);
-        if (z > 0) {
-            link_rows<k26>(sm, r, m, st, r - kVY, a.local_cap, err);
-            if (k26) {
-                if (y > 0) link_rows<k26>(sm, r, m, st, r - kVY - 1, a.local_cap, err);
-                if (y < kVY - 1) link_rows<k26>(sm, r, m, st, r - kVY + 1, a.local_cap, err);
-            }
-        }
+        uint32_t first = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (nbv & (1u << k)) link_rows<k26>(sm, r, m, st, r + nb_off(k), first, a.local_cap, err);
     }
     __syncthreads();
 
@@ -320,12 +367,25 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
     const uint16_t *own = a.faces + (size_t)blockIdx.x * kFaceEntries;
     constexpr int kR = k26 ? 1 : 0;
+    // pairs of roots already joined by this CTA: most face voxels of a
+    // component repeat the pair of their neighbours
+    __shared__ unsigned long long seen[kPairHash];
+    for (int i = threadIdx.x; i < kPairHash; i += kVThreads) seen[i] = kNoPair;
+    __syncthreads();
     int err = 0;
     int last_q = -1, last_p = -1;
     auto join = [&](int q, int p) {
         if (q == last_q && p == last_p) return;
         last_q = q;
         last_p = p;
+        const unsigned long long key = ((unsigned long long)(unsigned)q << 32) | (unsigned)p;
+        unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kPairHash - 1);
+        for (int i = 0; i < 16; ++i, h = (h + 1) & (kPairHash - 1)) {
+            unsigned long long cur = ((volatile unsigned long long *)seen)[h];
+            if (cur == kNoPair) cur = atomicCAS(&seen[h], kNoPair, key);
+            if (cur == key) return;      // joined by another thread of the CTA
+            if (cur == kNoPair) break;   // claimed: this thread joins it
+        }
         vg_union(a.labels, a.n, q, p, a.global_cap, err);
     };
     // z face: own slice 0 against the last slice of the blocks below
