@@ -4,24 +4,26 @@
 // method out in 2D.  This is the same coarse-to-fine structure one dimension
 // up, on blocks of 32 x 16 x 16 voxels (one CTA, one thread per 32-voxel row
 // held as a bit mask):
-//   k_vol_local  step 1 (Sec. 3.1): rows become runs; each run is linked to
-//                the runs it touches in the earlier rows of its block (the
-//                row above, the row in the slice before, and under
+//   k_vol_local  step 1 (Sec. 3.1): rows become runs.  Coarse labelling
+//                gives each run its first contact in an earlier row of the
+//                block (the row above, the row in the slice before, and under
 //                26-connectivity the two diagonal rows of the slice before,
-//                with x widened by one voxel) by a shared-memory union-find
-//                whose links go from the larger block position to the
-//                smaller, so a root is its component's first voxel in raster
-//                order.  Roots of components that reach a block face get a
-//                forest entry in `labels` (own position + 1), and the local
-//                root of every face voxel goes to a compact face record.
+//                with x widened by one voxel) as parent; the other contacts
+//                are joined by a shared-memory union-find whose links go from
+//                the larger block position to the smaller, so a root is its
+//                component's first voxel in raster order.  Roots of
+//                components that reach a block face get a forest entry in
+//                `labels` (own position + 1), and every voxel's local root
+//                goes to a root record (2 bytes per voxel).
 //   k_vol_merge  step 2 (Sec. 3.2): every voxel pair across a block face is
-//                joined in the global forest (lock-free atomicMin union);
-//                a pair that crosses several faces is taken by the z face,
-//                else the y face, else the x face, so each pair is seen once.
-//   k_vol_write  step 3 (Sec. 3.3): the block's runs are recomputed from the
-//                volume, each root's final label is found (border roots by a
-//                walk of the global forest), and every voxel of the block is
-//                written once, as whole 128-byte rows.
+//                joined in the global forest (lock-free atomicMin union, the
+//                pairs of roots deduplicated per CTA); a pair that crosses
+//                several faces is taken by the z face, else the y face, else
+//                the x face, so each pair is seen once.
+//   k_vol_write  step 3 (Sec. 3.3): each block root's final label is found
+//                (border roots by a walk of the global forest) and every voxel
+//                of the block is written once from its root record, as whole
+//                128-byte rows.
 // Labels: 1 + min raster position x + y*W + z*W*H of the component, 0 for
 // background.  The forest lives in `labels` at border-root positions only;
 // the write-out overwrites such an entry with its final value, which is still
@@ -41,24 +43,22 @@ constexpr int kVRows = kVY * kVZ;            // rows of 32 voxels per block
 constexpr int kVThreads = kVRows;            // one thread per row
 constexpr int kVIds = kVRows * kVX;          // ids: row * 32 + x (row = z * kVY + y)
 constexpr uint16_t kNoRoot = 0xFFFF;         // face record of a background voxel
-constexpr uint32_t kFinal = 0x80000000u;     // root entry holding its final label
 constexpr int kPairHash = 2048;              // root pairs remembered per CTA in the merge
 constexpr unsigned long long kNoPair = ~0ull;
-// face records per block, u16 local root ids: x faces [side][row],
-// y faces [side][z][x], z faces [side][y][x]
-constexpr int kFX = 2 * kVRows;
-constexpr int kFYLo = kFX, kFYHi = kFX + kVZ * kVX;
-constexpr int kFZLo = kFX + 2 * kVZ * kVX, kFZHi = kFZLo + kVY * kVX;
-constexpr int kFaceEntries = kFZHi + kVY * kVX;
-static_assert(kVIds <= 0x8000, "ids must fit the face records");
-static_assert((kFaceEntries * 2) % 16 == 0, "face records stay 16-byte aligned");
+// Root records: per block, one u16 per voxel slot (row * 32 + x), block
+// after block: the local root id of the voxel, with kBorderBit set when that
+// root's component reaches a block face; kNoRoot for background.
+constexpr uint16_t kBorderBit = 0x8000;
+constexpr uint16_t kIdMask = 0x7FFF;
+static_assert(kVIds <= kIdMask, "ids must fit the root records");
+static_assert((kVIds * 2) % 16 == 0, "root records stay 16-byte aligned per block");
 
 __device__ int g_volume_error = 0;
 
 struct VolArgs {
     const uint8_t *img;
     int32_t *labels;
-    uint16_t *faces;
+    uint16_t *roots;  // root records, kVIds per block
     unsigned long long pitch;
     int D, H, W;
     int n;  // voxels, D * H * W
@@ -327,29 +327,18 @@ __global__ void __launch_bounds__(kVThreads) k_vol_local(VolArgs a) {
         a.labels[g] = (int32_t)(g + 1);
     }
 
-    // face records (only faces that have a neighbouring block are read)
-    uint16_t *f = a.faces + (size_t)blockIdx.x * kFaceEntries;
-    const uint32_t st = m & ~(m << 1);
-    if (bx > 0) f[r] = (m & 1u) ? (uint16_t)sm.par[slot(r * kVX)] : kNoRoot;
-    if (bx < a.nbx - 1) f[kVRows + r] = (m >> 31) ? (uint16_t)sm.par[slot(r * kVX + hibit(st))] : kNoRoot;
-    for (int e = r; e < 4 * kVY * kVX; e += kVThreads) {
-        const int face = e / (kVY * kVX), i = e % (kVY * kVX), u = i / kVX, x = i % kVX;
-        bool need;
-        int row;
-        switch (face) {
-            case 0: need = by > 0; row = u * kVY; break;                          // y = 0, u = z
-            case 1: need = by < a.nby - 1; row = u * kVY + kVY - 1; break;        // y = last
-            case 2: need = bz > 0; row = u; break;                                // z = 0, u = y
-            default: need = bz < a.nbz - 1; row = (kVZ - 1) * kVY + u; break;     // z = last
-        }
-        if (!need) continue;
+    // root records of the block, one warp per row (64-byte stores)
+    uint16_t *rec = a.roots + (size_t)blockIdx.x * kVIds;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    for (int row = warp; row < kVRows; row += kVThreads / 32) {
         const uint32_t mr = sm.mask[row];
         uint16_t v = kNoRoot;
-        if ((mr >> x) & 1u) {
+        if ((mr >> lane) & 1u) {
             const uint32_t sr = mr & ~(mr << 1);
-            v = (uint16_t)sm.par[slot(row * kVX + hibit(sr & upto(x)))];
+            const int root = (int)sm.par[slot(row * kVX + hibit(sr & upto(lane)))];
+            v = (uint16_t)(root | (((sm.border[root / kVX] >> (root % kVX)) & 1u) ? kBorderBit : 0));
         }
-        f[kFX + e] = v;
+        rec[row * kVX + lane] = v;
     }
     if (err) atomicOr(&g_volume_error, err);
 }
@@ -365,7 +354,7 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
-    const uint16_t *own = a.faces + (size_t)blockIdx.x * kFaceEntries;
+    const uint16_t *own = a.roots + (size_t)blockIdx.x * kVIds;
     constexpr int kR = k26 ? 1 : 0;
     // pairs of roots already joined by this CTA: most face voxels of a
     // component repeat the pair of their neighbours
@@ -391,8 +380,8 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     // z face: own slice 0 against the last slice of the blocks below
     if (bz > 0) {
         for (int e = threadIdx.x; e < kVY * kVX; e += kVThreads) {
-            const int q = own[kFZLo + e];
-            if (q == kNoRoot) continue;
+            const int q = own[e] & kIdMask;  // slice 0: row = y, e = y * 32 + x
+            if (q == kIdMask) continue;
             const int gx = gx0 + e % kVX, gy = gy0 + e / kVX;
             const int qg = id_pos(a, bx, by, bz, q);
             for (int dy = -kR; dy <= kR; ++dy) {
@@ -400,9 +389,9 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
                     const int nx = gx + dx, ny = gy + dy;
                     if (nx < 0 || ny < 0 || nx >= a.W || ny >= a.H) continue;
                     const int nbx = nx / kVX, nby = ny / kVY;
-                    const uint16_t *nf = a.faces + (size_t)(((bz - 1) * a.nby + nby) * a.nbx + nbx) * kFaceEntries;
-                    const int p = nf[kFZHi + (ny % kVY) * kVX + nx % kVX];
-                    if (p != kNoRoot) join(qg, id_pos(a, nbx, nby, bz - 1, p));
+                    const uint16_t *nr = a.roots + (size_t)(((bz - 1) * a.nby + nby) * a.nbx + nbx) * kVIds;
+                    const int p = nr[((kVZ - 1) * kVY + ny % kVY) * kVX + nx % kVX] & kIdMask;
+                    if (p != kIdMask) join(qg, id_pos(a, nbx, nby, bz - 1, p));
                 }
             }
         }
@@ -411,9 +400,9 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     // the same z block
     if (by > 0) {
         for (int e = threadIdx.x; e < kVZ * kVX; e += kVThreads) {
-            const int q = own[kFYLo + e];
-            if (q == kNoRoot) continue;
             const int z = e / kVX, gx = gx0 + e % kVX;
+            const int q = own[z * kVY * kVX + e % kVX] & kIdMask;  // row y = 0 of slice z
+            if (q == kIdMask) continue;
             const int qg = id_pos(a, bx, by, bz, q);
             for (int dz = -kR; dz <= kR; ++dz) {
                 const int zz = z + dz;
@@ -422,9 +411,9 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
                     const int nx = gx + dx;
                     if (nx < 0 || nx >= a.W) continue;
                     const int nbx = nx / kVX;
-                    const uint16_t *nf = a.faces + (size_t)((bz * a.nby + by - 1) * a.nbx + nbx) * kFaceEntries;
-                    const int p = nf[kFYHi + zz * kVX + nx % kVX];
-                    if (p != kNoRoot) join(qg, id_pos(a, nbx, by - 1, bz, p));
+                    const uint16_t *nr = a.roots + (size_t)((bz * a.nby + by - 1) * a.nbx + nbx) * kVIds;
+                    const int p = nr[(zz * kVY + kVY - 1) * kVX + nx % kVX] & kIdMask;
+                    if (p != kIdMask) join(qg, id_pos(a, nbx, by - 1, bz, p));
                 }
             }
         }
@@ -432,10 +421,10 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     // x face: own first voxels against the last voxels of the block to the
     // left, in the same y and z block
     if (bx > 0) {
-        const uint16_t *nf = a.faces + (size_t)(blockIdx.x - 1) * kFaceEntries;
+        const uint16_t *nr = a.roots + (size_t)(blockIdx.x - 1) * kVIds;
         for (int r = threadIdx.x; r < kVRows; r += kVThreads) {
-            const int q = own[r];
-            if (q == kNoRoot) continue;
+            const int q = own[r * kVX] & kIdMask;  // voxel x = 0 of row r
+            if (q == kIdMask) continue;
             const int y = r % kVY, z = r / kVY;
             const int qg = id_pos(a, bx, by, bz, q);
             for (int dz = -kR; dz <= kR; ++dz) {
@@ -444,8 +433,8 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
                 for (int dy = -kR; dy <= kR; ++dy) {
                     const int yy = y + dy;
                     if (yy < 0 || yy >= kVY || gy0 + yy >= a.H) continue;
-                    const int p = nf[kVRows + zz * kVY + yy];
-                    if (p != kNoRoot) join(qg, id_pos(a, bx - 1, by, bz, p));
+                    const int p = nr[(zz * kVY + yy) * kVX + kVX - 1] & kIdMask;  // voxel x = 31
+                    if (p != kIdMask) join(qg, id_pos(a, bx - 1, by, bz, p));
                 }
             }
         }
@@ -453,26 +442,35 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     if (err) atomicOr(&g_volume_error, err);
 }
 
-template <bool k26>
+// Step 3 from the root records: every block root that is a voxel of the
+// own row gets its final label (border roots by a walk of the global
+// forest), then every voxel of the block is written once.
 __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
-    __shared__ VolSmem sm;
+    __shared__ uint32_t fin[kVIds];  // final label by root id
     int bx, by, bz;
     block_coords(a, bx, by, bz);
-    int err = 0;
-    const uint32_t m = vol_local<k26>(sm, a, bx, by, bz, err);
-    const int r = threadIdx.x;
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
-
-    // final label of every root of the own row (only this thread touches
-    // these entries now)
-    const uint32_t st = m & ~(m << 1);
-    const uint32_t br = sm.border[r];
-    for (uint32_t t = st; t; t &= t - 1) {
-        const int s = lobit(t), id = r * kVX + s;
-        if ((int)sm.par[slot(id)] != id) continue;
-        const int g = (int)vpos(a, gx0 + s, gy0 + r % kVY, gz0 + r / kVY);
-        const int root = ((br >> s) & 1u) ? vg_find_ro(a.labels, a.n, g, a.global_cap, err) : g;
-        sm.par[slot(id)] = kFinal | (uint32_t)(root + 1);
+    const uint16_t *rec = a.roots + (size_t)blockIdx.x * kVIds;
+    int err = 0;
+    {
+        const int r = threadIdx.x, gy = gy0 + r % kVY, gz = gz0 + r / kVY;
+        if (gy < a.H && gz < a.D) {
+            const uint4 *row = reinterpret_cast<const uint4 *>(rec + r * kVX);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 w = __ldcs(row + c);
+                const uint32_t h[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int x = c * 8 + k;
+                    const int v = (int)((h[k / 2] >> (16 * (k % 2))) & 0xFFFFu);
+                    if (v == kNoRoot || (v & kIdMask) != r * kVX + x) continue;
+                    const int g = (int)vpos(a, gx0 + x, gy, gz);
+                    const int root = (v & kBorderBit) ? vg_find_ro(a.labels, a.n, g, a.global_cap, err) : g;
+                    fin[v & kIdMask] = (uint32_t)(root + 1);
+                }
+            }
+        }
     }
     __syncthreads();
 
@@ -483,14 +481,8 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
         const int gy = gy0 + row % kVY, gz = gz0 + row / kVY;
         if (gy >= a.H || gz >= a.D) continue;
         if (gx >= a.W) continue;
-        const uint32_t mr = sm.mask[row];
-        int32_t v = 0;
-        if ((mr >> lane) & 1u) {
-            const uint32_t sr = mr & ~(mr << 1);
-            const uint32_t e = sm.par[slot(row * kVX + hibit(sr & upto(lane)))];
-            v = (int32_t)((e & kFinal) ? e & ~kFinal : sm.par[slot((int)e)] & ~kFinal);
-        }
-        __stcs(a.labels + vpos(a, gx, gy, gz), v);
+        const int v = rec[row * kVX + lane];
+        __stcs(a.labels + vpos(a, gx, gy, gz), v == kNoRoot ? 0 : (int32_t)fin[v & kIdMask]);
     }
     if (err) atomicOr(&g_volume_error, err);
 }
@@ -506,7 +498,7 @@ void volume_grid(int D, int H, int W, int &nbx, int &nby, int &nbz) {
 size_t volume_workspace_bytes(int D, int H, int W) {
     int nbx, nby, nbz;
     volume_grid(D, H, W, nbx, nby, nbz);
-    const size_t bytes = (size_t)nbx * nby * nbz * kFaceEntries * sizeof(uint16_t);
+    const size_t bytes = (size_t)nbx * nby * nbz * kVIds * sizeof(uint16_t);
     return (bytes + 255) & ~(size_t)255;
 }
 
@@ -515,7 +507,7 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     VolArgs a;
     a.img = img;
     a.labels = labels;
-    a.faces = static_cast<uint16_t *>(ws);
+    a.roots = static_cast<uint16_t *>(ws);
     a.pitch = pitch;
     a.D = D;
     a.H = H;
@@ -532,11 +524,11 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     if (conn == 26) {
         k_vol_local<true><<<blocks, kVThreads, 0, stream>>>(a);
         k_vol_merge<true><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<true><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<<<blocks, kVThreads, 0, stream>>>(a);
     } else {
         k_vol_local<false><<<blocks, kVThreads, 0, stream>>>(a);
         k_vol_merge<false><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<false><<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<<<blocks, kVThreads, 0, stream>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
