@@ -59,6 +59,7 @@ struct VolArgs {
     const uint8_t *img;
     int32_t *labels;
     uint16_t *roots;  // root records, kVIds per block
+    uint16_t *xface;  // the root records of x = 0 and x = 31, [block][2][row]
     unsigned long long pitch;
     int D, H, W;
     int n;  // voxels, D * H * W
@@ -239,6 +240,21 @@ __device__ __forceinline__ int first_contact(const VolSmem &sm, int r, uint32_t 
     return -1;
 }
 
+// Row (y, z) of the volume over the block's 32 columns from gx0, as a bit
+// mask; rows outside the volume are empty.
+__device__ __forceinline__ uint32_t row_mask(const VolArgs &a, int gx0, int gy, int gz) {
+    if (gy < 0 || gz < 0 || gy >= a.H || gz >= a.D) return 0u;
+    const uint8_t *p = a.img + ((size_t)gz * a.H + gy) * a.pitch + gx0;
+    if (a.vec_in && gx0 + kVX <= a.W) {
+        const uint4 lo = ldg_nc16(p), hi = ldg_nc16(p + 16);
+        return nz16(lo) | (nz16(hi) << 16);
+    }
+    uint32_t m = 0;
+    const int n = a.W - gx0 < kVX ? a.W - gx0 : kVX;
+    for (int i = 0; i < n; ++i) m |= (uint32_t)(__ldg(p + i) != 0) << i;
+    return m;
+}
+
 // Step 1 inside the block (bx, by, bz): masks, runs, unions, compression and
 // the border-root marks.  Ends with a barrier; the thread's row mask is
 // returned.
@@ -246,16 +262,27 @@ template <bool k26>
 __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int bz, int &err) {
     const int r = threadIdx.x, y = r % kVY, z = r / kVY;
     const int gx0 = bx * kVX, gy = by * kVY + y, gz = bz * kVZ + z;
-    uint32_t m = 0;
-    if (gy < a.H && gz < a.D) {
-        const uint8_t *p = a.img + ((size_t)gz * a.H + gy) * a.pitch + gx0;
-        if (a.vec_in && gx0 + kVX <= a.W) {
-            const uint4 lo = ldg_nc16(p), hi = ldg_nc16(p + 16);
-            m = nz16(lo) | (nz16(hi) << 16);
-        } else {
-            const int n = a.W - gx0 < kVX ? a.W - gx0 : kVX;
-            for (int i = 0; i < n; ++i) m |= (uint32_t)(__ldg(p + i) != 0) << i;
-        }
+    const uint32_t m = row_mask(a, gx0, gy, gz);
+
+    // Voxels of this row that touch a foreground voxel of a neighbouring
+    // block across a y or z face: the rows across the face (under
+    // 26-connectivity the three rows at dz or dy in -1..1, widened by one
+    // voxel, with the voxels beyond the block's x range taken as
+    // foreground).  Only their components need a forest entry.  The x faces
+    // are taken as touching wherever the edge voxel is foreground.
+    uint32_t across = 0;
+    {
+        constexpr int kR = k26 ? 1 : 0;
+        const auto widen = [](uint32_t h) { return k26 ? (h | (h << 1) | (h >> 1) | 0x80000001u) : h; };
+        if (m && y == 0 && by > 0)
+            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy - 1, gz + d));
+        if (m && y == kVY - 1 && by < a.nby - 1)
+            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + 1, gz + d));
+        if (m && z == 0 && bz > 0)
+            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + d, gz - 1));
+        if (m && z == kVZ - 1 && bz < a.nbz - 1)
+            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + d, gz + 1));
+        across |= (bx > 0 ? 1u : 0u) | (bx < a.nbx - 1 ? 0x80000000u : 0u);
     }
     sm.mask[r] = m;
     sm.border[r] = 0;
@@ -288,11 +315,8 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
     }
     __syncthreads();
 
-    // faces that have a neighbouring block: whole rows on y/z faces, the
-    // first and last voxel of every row on x faces
-    const bool face_row = (y == 0 && by > 0) || (y == kVY - 1 && by < a.nby - 1) || (z == 0 && bz > 0) ||
-                          (z == kVZ - 1 && bz < a.nbz - 1);
-    uint32_t fm = m & (face_row ? ~0u : ((bx > 0 ? 1u : 0u) | (bx < a.nbx - 1 ? 0x80000000u : 0u)));
+    // roots of the components with a voxel that touches a neighbouring block
+    uint32_t fm = m & across;
     while (fm) {
         const int b = lobit(fm);
         const int root = (int)sm.par[slot(r * kVX + hibit(st & upto(b)))];
@@ -339,6 +363,10 @@ __global__ void __launch_bounds__(kVThreads) k_vol_local(VolArgs a) {
             v = (uint16_t)(root | (((sm.border[root / kVX] >> (root % kVX)) & 1u) ? kBorderBit : 0));
         }
         rec[row * kVX + lane] = v;
+        // the x faces once more, packed: the merge reads them per row
+        uint16_t *xf = a.xface + (size_t)blockIdx.x * 2 * kVRows;
+        if (lane == 0) xf[row] = v;
+        if (lane == kVX - 1) xf[kVRows + row] = v;
     }
     if (err) atomicOr(&g_volume_error, err);
 }
@@ -421,9 +449,10 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     // x face: own first voxels against the last voxels of the block to the
     // left, in the same y and z block
     if (bx > 0) {
-        const uint16_t *nr = a.roots + (size_t)(blockIdx.x - 1) * kVIds;
+        const uint16_t *ox = a.xface + (size_t)blockIdx.x * 2 * kVRows;
+        const uint16_t *nx = a.xface + (size_t)(blockIdx.x - 1) * 2 * kVRows;
         for (int r = threadIdx.x; r < kVRows; r += kVThreads) {
-            const int q = own[r * kVX] & kIdMask;  // voxel x = 0 of row r
+            const int q = ox[r] & kIdMask;  // voxel x = 0 of row r
             if (q == kIdMask) continue;
             const int y = r % kVY, z = r / kVY;
             const int qg = id_pos(a, bx, by, bz, q);
@@ -433,7 +462,7 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
                 for (int dy = -kR; dy <= kR; ++dy) {
                     const int yy = y + dy;
                     if (yy < 0 || yy >= kVY || gy0 + yy >= a.H) continue;
-                    const int p = nr[(zz * kVY + yy) * kVX + kVX - 1] & kIdMask;  // voxel x = 31
+                    const int p = nx[kVRows + zz * kVY + yy] & kIdMask;  // voxel x = 31
                     if (p != kIdMask) join(qg, id_pos(a, bx - 1, by, bz, p));
                 }
             }
@@ -446,19 +475,28 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
 // own row gets its final label (border roots by a walk of the global
 // forest), then every voxel of the block is written once.
 __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
-    __shared__ uint32_t fin[kVIds];  // final label by root id
+    constexpr int kWalks = 1024;      // marked roots walked by the whole CTA
+    __shared__ uint32_t fin[kVIds];   // final label by root id
+    __shared__ uint16_t walk[kWalks]; // marked roots of the block
+    __shared__ int nwalk;
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
     const uint16_t *rec = a.roots + (size_t)blockIdx.x * kVIds;
     int err = 0;
+    if (threadIdx.x == 0) nwalk = 0;
+    __syncthreads();
+    // roots of the own row: unmarked ones are final at once, marked ones are
+    // listed so that the forest walks (chains of dependent loads) spread
+    // over all threads; a full list leaves the rest to the thread that found
+    // them
     {
         const int r = threadIdx.x, gy = gy0 + r % kVY, gz = gz0 + r / kVY;
         if (gy < a.H && gz < a.D) {
             const uint4 *row = reinterpret_cast<const uint4 *>(rec + r * kVX);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                const uint4 w = __ldcs(row + c);
+                const uint4 w = __ldg(row + c);  // read again below: keep it in L2
                 const uint32_t h[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -466,10 +504,24 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
                     const int v = (int)((h[k / 2] >> (16 * (k % 2))) & 0xFFFFu);
                     if (v == kNoRoot || (v & kIdMask) != r * kVX + x) continue;
                     const int g = (int)vpos(a, gx0 + x, gy, gz);
-                    const int root = (v & kBorderBit) ? vg_find_ro(a.labels, a.n, g, a.global_cap, err) : g;
-                    fin[v & kIdMask] = (uint32_t)(root + 1);
+                    if (!(v & kBorderBit)) {
+                        fin[v & kIdMask] = (uint32_t)(g + 1);
+                        continue;
+                    }
+                    const int i = atomicAdd(&nwalk, 1);
+                    if (i < kWalks) walk[i] = (uint16_t)(v & kIdMask);
+                    else fin[v & kIdMask] = (uint32_t)(vg_find_ro(a.labels, a.n, g, a.global_cap, err) + 1);
                 }
             }
+        }
+    }
+    __syncthreads();
+    {
+        const int n = nwalk < kWalks ? nwalk : kWalks;
+        for (int i = threadIdx.x; i < n; i += kVThreads) {
+            const int id = walk[i];
+            const int g = id_pos(a, bx, by, bz, id);
+            fin[id] = (uint32_t)(vg_find_ro(a.labels, a.n, g, a.global_cap, err) + 1);
         }
     }
     __syncthreads();
@@ -498,7 +550,7 @@ void volume_grid(int D, int H, int W, int &nbx, int &nby, int &nbz) {
 size_t volume_workspace_bytes(int D, int H, int W) {
     int nbx, nby, nbz;
     volume_grid(D, H, W, nbx, nby, nbz);
-    const size_t bytes = (size_t)nbx * nby * nbz * kVIds * sizeof(uint16_t);
+    const size_t bytes = (size_t)nbx * nby * nbz * (kVIds + 2 * kVRows) * sizeof(uint16_t);
     return (bytes + 255) & ~(size_t)255;
 }
 
@@ -514,6 +566,7 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     a.W = W;
     a.n = (int)((long long)D * H * W);
     volume_grid(D, H, W, a.nbx, a.nby, a.nbz);
+    a.xface = a.roots + (size_t)a.nbx * a.nby * a.nbz * kVIds;
     a.vec_in = (pitch % 16 == 0) && (reinterpret_cast<uintptr_t>(img) % 16 == 0);
     // a find walks a strictly decreasing chain and a union retry strictly
     // lowers its node, so neither can take more steps than there are nodes
