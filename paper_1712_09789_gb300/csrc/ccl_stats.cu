@@ -10,11 +10,12 @@
 //   k_stats_scan        exclusive prefix over the chunk counts (one CTA)
 //   k_stats_index       dense index of every root (rootmap[p]), component
 //                       records initialised in label order
-//   k_stats_accumulate  tiles of 16 x 512 pixels: each pixel's component is
+//   k_stats_accumulate  tiles of 32 x 256 pixels: each pixel's component is
 //                       looked up and its statistics folded into a shared-
 //                       memory hash table, one global update per component
 //                       and tile afterwards (the large components would
-//                       otherwise meet in global atomics from every pixel)
+//                       otherwise meet in global atomics from every pixel);
+//                       a component inside one tile gets plain stores
 #include <climits>
 #include <cstdint>
 
@@ -27,7 +28,7 @@ namespace {
 
 constexpr int kChunk = 8192;      // pixels per chunk (256 threads x 32)
 constexpr int kStatThreads = 256;
-constexpr int kTileH = 16, kTileW = 512;
+constexpr int kTileH = 32, kTileW = 256;
 constexpr int kHash = 1024;       // hash slots per tile
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
@@ -121,22 +122,27 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_index(const int32_t *lab
     }
 }
 
+// Per-tile statistics in tile coordinates (x - tx0, y - ty0): every field
+// fits 32 bits (a tile has 8192 pixels of coordinates below 256), so all
+// shared-memory updates are native 32-bit atomics.
 struct StatSmem {
     uint32_t key[kHash];
     int32_t area[kHash], x0[kHash], y0[kHash], x1[kHash], y1[kHash];
-    unsigned long long sx[kHash], sy[kHash];
+    uint32_t sx[kHash], sy[kHash];
 };
 
-__device__ __forceinline__ void fold_global(ccl_component *out, uint32_t k, int a, int x0, int y0, int x1, int y1,
-                                            unsigned long long sx, unsigned long long sy) {
+// Adds a tile's share of a component (tile coordinates from tx0, ty0) to its
+// record.
+__device__ __forceinline__ void fold_global(ccl_component *out, uint32_t k, int tx0, int ty0, int a, int x0, int y0,
+                                            int x1, int y1, uint32_t sx, uint32_t sy) {
     ccl_component &c = out[k];
     atomicAdd(&c.area, a);
-    atomicMin(&c.x0, x0);
-    atomicMin(&c.y0, y0);
-    atomicMax(&c.x1, x1);
-    atomicMax(&c.y1, y1);
-    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_x), sx);
-    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_y), sy);
+    atomicMin(&c.x0, tx0 + x0);
+    atomicMin(&c.y0, ty0 + y0);
+    atomicMax(&c.x1, tx0 + x1);
+    atomicMax(&c.y1, ty0 + y1);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_x), (unsigned long long)sx + (unsigned long long)a * tx0);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&c.sum_y), (unsigned long long)sy + (unsigned long long)a * ty0);
 }
 
 __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t *labels, int H, int W,
@@ -161,13 +167,12 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t
     const int tx0 = blockIdx.x * kTileW, ty0 = blockIdx.y * kTileH;
     const int lane = threadIdx.x & 31;
     int nbad = 0;
-    // the lanes of a warp read 32 neighbouring pixels of a row; lanes of one
-    // component are folded first (one shared-memory update per component and
-    // warp step), the coordinate sums in 32 bits when no 32 coordinates can
-    // overflow them
-    const bool warp_sums = W <= (1 << 26) && H <= (1 << 26);
+    // the lanes of a warp read 32 neighbouring pixels of a row; the lanes of
+    // one component are folded first, so each component takes one
+    // shared-memory update per warp step
     for (int i = threadIdx.x; i < kTileH * kTileW; i += kStatThreads) {
-        const int x = tx0 + (i % kTileW), y = ty0 + i / kTileW;
+        const int rx = i % kTileW, ry = i / kTileW;
+        const int x = tx0 + rx, y = ty0 + ry;
         uint32_t k = kEmpty;
         if (x < W && y < H) {
             const int32_t l = labels[(long long)y * W + x];
@@ -184,43 +189,55 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t
         }
         const unsigned peers = __match_any_sync(0xFFFFFFFFu, k);
         if (k == kEmpty) continue;
+        // every lane of the group (all of `peers`) takes part in the
+        // reductions; then the lowest lane updates for the whole group
         const int a = __popc(peers);
-        const int gx0 = (int)__reduce_min_sync(peers, (unsigned)x), gx1 = (int)__reduce_max_sync(peers, (unsigned)x);
-        const int gy0 = (int)__reduce_min_sync(peers, (unsigned)y), gy1 = (int)__reduce_max_sync(peers, (unsigned)y);
-        unsigned long long gsx = (unsigned long long)x, gsy = (unsigned long long)y;
-        if (warp_sums) {
-            gsx = __reduce_add_sync(peers, (unsigned)x);
-            gsy = __reduce_add_sync(peers, (unsigned)y);
-        }
-        const bool leader = lane == __ffs(peers) - 1;
-        // without warp sums every lane adds its own coordinates
-        if (!leader && warp_sums) continue;
-        const int aa = leader ? a : 0;
+        const int gx0 = (int)__reduce_min_sync(peers, (unsigned)rx), gx1 = (int)__reduce_max_sync(peers, (unsigned)rx);
+        const int gy0 = (int)__reduce_min_sync(peers, (unsigned)ry), gy1 = (int)__reduce_max_sync(peers, (unsigned)ry);
+        const uint32_t gsx = __reduce_add_sync(peers, (unsigned)rx), gsy = __reduce_add_sync(peers, (unsigned)ry);
+        if (lane != __ffs(peers) - 1) continue;
         uint32_t h = (k * 2654435761u) >> 22;  // 10-bit hash
         bool done = false;
         for (int probe = 0; probe < 16 && !done; ++probe, h = (h + 1) & (kHash - 1)) {
             uint32_t cur = sm.key[h];
             if (cur == kEmpty) cur = atomicCAS(&sm.key[h], kEmpty, k);
             if (cur == kEmpty || cur == k) {
-                if (aa) atomicAdd(&sm.area[h], aa);
-                if (leader) {
-                    atomicMin(&sm.x0[h], gx0);
-                    atomicMin(&sm.y0[h], gy0);
-                    atomicMax(&sm.x1[h], gx1);
-                    atomicMax(&sm.y1[h], gy1);
-                }
+                atomicAdd(&sm.area[h], a);
+                atomicMin(&sm.x0[h], gx0);
+                atomicMin(&sm.y0[h], gy0);
+                atomicMax(&sm.x1[h], gx1);
+                atomicMax(&sm.y1[h], gy1);
                 atomicAdd(&sm.sx[h], gsx);
                 atomicAdd(&sm.sy[h], gsy);
                 done = true;
             }
         }
-        if (!done) fold_global(out, k, aa, leader ? gx0 : INT_MAX, leader ? gy0 : INT_MAX, leader ? gx1 : -1,
-                               leader ? gy1 : -1, gsx, gsy);
+        if (!done) fold_global(out, k, tx0, ty0, a, gx0, gy0, gx1, gy1, gsx, gsy);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < kHash; i += kStatThreads)
-        if (sm.key[i] != kEmpty)
-            fold_global(out, sm.key[i], sm.area[i], sm.x0[i], sm.y0[i], sm.x1[i], sm.y1[i], sm.sx[i], sm.sy[i]);
+    // a component that reaches no tile edge shared with another tile lies in
+    // this tile alone: its record is final and takes plain stores
+    const int lastx = kTileW - 1, lasty = kTileH - 1;
+    const bool right = tx0 + kTileW < W, below = ty0 + kTileH < H;
+    for (int i = threadIdx.x; i < kHash; i += kStatThreads) {
+        const uint32_t k = sm.key[i];
+        if (k == kEmpty) continue;
+        const int a = sm.area[i];
+        const bool alone = !(sm.x0[i] == 0 && tx0 > 0) && !(sm.y0[i] == 0 && ty0 > 0) &&
+                           !(sm.x1[i] == lastx && right) && !(sm.y1[i] == lasty && below);
+        if (alone) {
+            ccl_component &c = out[k];
+            c.area = a;
+            c.x0 = tx0 + sm.x0[i];
+            c.y0 = ty0 + sm.y0[i];
+            c.x1 = tx0 + sm.x1[i];
+            c.y1 = ty0 + sm.y1[i];
+            c.sum_x = (int64_t)sm.sx[i] + (int64_t)a * tx0;
+            c.sum_y = (int64_t)sm.sy[i] + (int64_t)a * ty0;
+        } else {
+            fold_global(out, k, tx0, ty0, a, sm.x0[i], sm.y0[i], sm.x1[i], sm.y1[i], sm.sx[i], sm.sy[i]);
+        }
+    }
     if (nbad) atomicAdd(bad, nbad);
 }
 
