@@ -255,6 +255,126 @@ __device__ __forceinline__ uint32_t row_mask(const VolArgs &a, int gx0, int gy, 
     return m;
 }
 
+// 26-connectivity works on bundles of 2 x 2 rows: (2Y, 2Z), (2Y+1, 2Z),
+// (2Y, 2Z+1), (2Y+1, 2Z+1).  Every voxel of a bundle column touches every
+// voxel of the same and the two neighbouring columns of the bundle (|dx|,
+// |dy|, |dz| <= 1), so the components inside a bundle are the runs of the OR
+// of its four rows ("pieces"), found by bit operations.  A piece is named by
+// its first voxel in raster order: the first of the four rows it occupies
+// (they are in increasing id order), first column there.  A piece name is a
+// voxel id, so the union-find over pieces keeps the order of voxel ids.
+struct Bundle {
+    uint32_t m0, m1, m2, m3;  // rows r0, r0 + 1, r0 + kVY, r0 + kVY + 1
+    int r0;
+};
+
+__device__ __forceinline__ int bundle_row0(int r) { return (r / kVY & ~1) * kVY + (r % kVY & ~1); }
+
+__device__ __forceinline__ Bundle load_bundle(const VolSmem &sm, int r0) {
+    return {sm.mask[r0], sm.mask[r0 + 1], sm.mask[r0 + kVY], sm.mask[r0 + kVY + 1], r0};
+}
+
+__device__ __forceinline__ uint32_t bundle_or(const Bundle &b) { return b.m0 | b.m1 | b.m2 | b.m3; }
+
+__device__ __forceinline__ int piece_key(const Bundle &b, int s, int e) {
+    const uint32_t rb = run_bits(s, e);
+    if (b.m0 & rb) return b.r0 * kVX + lobit(b.m0 & rb);
+    if (b.m1 & rb) return (b.r0 + 1) * kVX + lobit(b.m1 & rb);
+    if (b.m2 & rb) return (b.r0 + kVY) * kVX + lobit(b.m2 & rb);
+    return (b.r0 + kVY + 1) * kVX + lobit(b.m3 & rb);
+}
+
+// Name of the piece that holds voxel x (x must be in the bundle's OR).
+__device__ __forceinline__ int piece_key_at(const Bundle &b, int x) {
+    const uint32_t o = bundle_or(b);
+    return piece_key(b, hibit(o & ~(o << 1) & upto(x)), run_end(o, x));
+}
+
+// The earlier bundles a bundle (Y, Z) can touch, in the order they are
+// visited, and which rows of each side face the other:
+//   0: (Y-1, Z)    own rows y = 2Y      vs its rows y = 2Y-1
+//   1: (Y, Z-1)    own rows z = 2Z      vs its rows z = 2Z-1
+//   2: (Y-1, Z-1)  own row (2Y, 2Z)     vs its row (2Y-1, 2Z-1)
+//   3: (Y+1, Z-1)  own row (2Y+1, 2Z)   vs its row (2Y+2, 2Z-1)
+__device__ __forceinline__ int bundle_nb_off(int k) {
+    return k == 0 ? -2 : k == 1 ? -2 * kVY : k == 2 ? -2 * kVY - 2 : -2 * kVY + 2;
+}
+__device__ __forceinline__ uint32_t bundle_own_face(const Bundle &b, int k) {
+    return k == 0 ? (b.m0 | b.m2) : k == 1 ? (b.m0 | b.m1) : k == 2 ? b.m0 : b.m1;
+}
+__device__ __forceinline__ uint32_t bundle_nb_face(const Bundle &n, int k) {
+    return k == 0 ? (n.m1 | n.m3) : k == 1 ? (n.m2 | n.m3) : k == 2 ? n.m3 : n.m2;
+}
+
+// Root of voxel x of row r once the block's lists are compressed.
+template <bool k26>
+__device__ __forceinline__ int voxel_root(const VolSmem &sm, int r, int x) {
+    if (k26) return (int)sm.par[slot(piece_key_at(load_bundle(sm, bundle_row0(r)), x))];
+    const uint32_t mr = sm.mask[r];
+    return (int)sm.par[slot(r * kVX + hibit(mr & ~(mr << 1) & upto(x)))];
+}
+
+// Step 1 for 26-connectivity on the block's 64 bundles (threads 0..63):
+// coarse labelling (each piece takes its first contact in an earlier bundle
+// as parent when that piece has the smaller name), refinement (every contact
+// joined by union) and compression.  Ends with a barrier.
+__device__ void bundle_labelling(VolSmem &sm, const VolArgs &a, int &err) {
+    constexpr int kBY = kVY / 2, kBZ = kVZ / 2;
+    const int t = threadIdx.x;
+    const bool mine = t < kBY * kBZ;
+    const int Y = t % kBY, Z = t / kBY;
+    const int r0 = 2 * Z * kVY + 2 * Y;
+    Bundle b = {0u, 0u, 0u, 0u, 0};
+    uint32_t o = 0, starts = 0, nbv = 0;
+    if (mine) {
+        b = load_bundle(sm, r0);
+        o = bundle_or(b);
+        starts = o & ~(o << 1);
+        nbv = (Y > 0 ? 1u : 0u) | (Z > 0 ? 2u : 0u) | (Y > 0 && Z > 0 ? 4u : 0u) | (Y < kBY - 1 && Z > 0 ? 8u : 0u);
+    }
+    for (uint32_t q = starts; q; q &= q - 1) {
+        const int s = lobit(q), e = run_end(o, s);
+        const int key = piece_key(b, s, e);
+        int parent = key;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (parent != key || !(nbv & (1u << k))) continue;
+            const Bundle n = load_bundle(sm, r0 + bundle_nb_off(k));
+            const uint32_t c = touch_range<true>(bundle_own_face(b, k) & run_bits(s, e)) & bundle_nb_face(n, k);
+            if (c) {
+                const int nk = piece_key_at(n, lobit(c));
+                if (nk < key) parent = nk;
+            }
+        }
+        sm.par[slot(key)] = (uint32_t)parent;
+    }
+    __syncthreads();
+    for (uint32_t q = starts; q; q &= q - 1) {
+        const int s = lobit(q), e = run_end(o, s);
+        const int key = piece_key(b, s, e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (!(nbv & (1u << k))) continue;
+            const Bundle n = load_bundle(sm, r0 + bundle_nb_off(k));
+            const uint32_t no = bundle_or(n);
+            uint32_t c = touch_range<true>(bundle_own_face(b, k) & run_bits(s, e)) & bundle_nb_face(n, k);
+            while (c) {
+                const int bit = lobit(c);
+                v_union(sm.par, key, piece_key_at(n, bit), a.local_cap, err);
+                const int ne = run_end(no, bit);
+                c = ne == 31 ? 0u : c & (~0u << (ne + 1));
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t q = starts; q; q &= q - 1) {
+        const int s = lobit(q);
+        const int key = piece_key(b, s, run_end(o, s));
+        sm.par[slot(key)] = (uint32_t)v_find_ro(sm.par, key, a.local_cap, err);
+    }
+    __syncthreads();
+}
+
 // Step 1 inside the block (bx, by, bz): masks, runs, unions, compression and
 // the border-root marks.  Ends with a barrier; the thread's row mask is
 // returned.
@@ -286,40 +406,44 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
     }
     sm.mask[r] = m;
     sm.border[r] = 0;
-    const uint32_t st = m & ~(m << 1);
-    const uint32_t nbv = earlier_rows<k26>(y, z);
     __syncthreads();
 
-    // coarse labelling: each run takes its first contact (a run of an
-    // earlier row, hence a smaller id) as parent, or itself; only the own
-    // entries are written, so no atomics are needed
-    for (uint32_t t = st; t; t &= t - 1) {
-        const int s = lobit(t), id = r * kVX + s;
-        const int f = first_contact<k26>(sm, r, m, s, nbv);
-        sm.par[slot(id)] = (uint32_t)(f >= 0 ? f : id);
-    }
-    __syncthreads();
+    if (k26) {
+        bundle_labelling(sm, a, err);
+    } else {
+        const uint32_t st = m & ~(m << 1);
+        const uint32_t nbv = earlier_rows<k26>(y, z);
+        // coarse labelling: each run takes its first contact (a run of an
+        // earlier row, hence a smaller id) as parent, or itself; only the
+        // own entries are written, so no atomics are needed
+        for (uint32_t t = st; t; t &= t - 1) {
+            const int s = lobit(t), id = r * kVX + s;
+            const int f = first_contact<k26>(sm, r, m, s, nbv);
+            sm.par[slot(id)] = (uint32_t)(f >= 0 ? f : id);
+        }
+        __syncthreads();
 
-    // refinement: the remaining contacts by union
-    if (m) {
-        uint32_t first = 0;
+        // refinement: the remaining contacts by union
+        if (m) {
+            uint32_t first = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (nbv & (1u << k)) link_rows<k26>(sm, r, m, st, r + nb_off(k), first, a.local_cap, err);
-    }
-    __syncthreads();
+            for (int k = 0; k < 4; ++k)
+                if (nbv & (1u << k)) link_rows<k26>(sm, r, m, st, r + nb_off(k), first, a.local_cap, err);
+        }
+        __syncthreads();
 
-    for (uint32_t t = st; t; t &= t - 1) {
-        const int id = r * kVX + lobit(t);
-        sm.par[slot(id)] = (uint32_t)v_find_ro(sm.par, id, a.local_cap, err);
+        for (uint32_t t = st; t; t &= t - 1) {
+            const int id = r * kVX + lobit(t);
+            sm.par[slot(id)] = (uint32_t)v_find_ro(sm.par, id, a.local_cap, err);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // roots of the components with a voxel that touches a neighbouring block
     uint32_t fm = m & across;
     while (fm) {
         const int b = lobit(fm);
-        const int root = (int)sm.par[slot(r * kVX + hibit(st & upto(b)))];
+        const int root = voxel_root<k26>(sm, r, b);
         atomicOr(&sm.border[root / kVX], 1u << (root % kVX));
         const int e = run_end(m, b);
         fm = e == 31 ? 0u : fm & (~0u << (e + 1));
@@ -358,8 +482,7 @@ __global__ void __launch_bounds__(kVThreads) k_vol_local(VolArgs a) {
         const uint32_t mr = sm.mask[row];
         uint16_t v = kNoRoot;
         if ((mr >> lane) & 1u) {
-            const uint32_t sr = mr & ~(mr << 1);
-            const int root = (int)sm.par[slot(row * kVX + hibit(sr & upto(lane)))];
+            const int root = voxel_root<k26>(sm, row, lane);
             v = (uint16_t)(root | (((sm.border[root / kVX] >> (root % kVX)) & 1u) ? kBorderBit : 0));
         }
         rec[row * kVX + lane] = v;
