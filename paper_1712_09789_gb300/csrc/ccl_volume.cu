@@ -4,17 +4,20 @@
 // method out in 2D.  This is the same coarse-to-fine structure one dimension
 // up, on blocks of 32 x 16 x 16 voxels (one CTA, one thread per 32-voxel row
 // held as a bit mask):
-//   k_vol_local  step 1 (Sec. 3.1): rows become runs.  Coarse labelling
-//                gives each run its first contact in an earlier row of the
-//                block (the row above, the row in the slice before, and under
-//                26-connectivity the two diagonal rows of the slice before,
-//                with x widened by one voxel) as parent; the other contacts
+//   k_vol_local  step 1 (Sec. 3.1).  Under 6-connectivity the elements are
+//                the runs of each row; coarse labelling gives each run its
+//                first contact in an earlier row of the block (the row above,
+//                the row in the slice before) as parent.  Under
+//                26-connectivity the elements are the pieces of 2 x 2 row
+//                bundles (runs of the OR of four rows, see Bundle), linked to
+//                the four earlier bundles the same way.  The other contacts
 //                are joined by a shared-memory union-find whose links go from
 //                the larger block position to the smaller, so a root is its
 //                component's first voxel in raster order.  Roots of
-//                components that reach a block face get a forest entry in
-//                `labels` (own position + 1), and every voxel's local root
-//                goes to a root record (2 bytes per voxel).
+//                components that touch a neighbouring block's foreground get
+//                a forest entry in `labels` (own position + 1), and every
+//                voxel's local root goes to a root record (2 bytes per
+//                voxel).
 //   k_vol_merge  step 2 (Sec. 3.2): every voxel pair across a block face is
 //                joined in the global forest (lock-free atomicMin union, the
 //                pairs of roots deduplicated per CTA); a pair that crosses
