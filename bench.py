@@ -342,7 +342,7 @@ def run_ours(args):
 
     # -- extra: the uneven 256-image batch, batched graph vs plain launches
     if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
+        line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs, cpu=not args.no_cpu)
 
     # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
     # frames through the continuous-batching server); it runs before the
@@ -404,7 +404,51 @@ def bench_8192(torch, ccl, hbm_gbs):
             "kernels_mean_us": {k: (t / n * 1e3 if n else None) for k, (t, n) in kt.items()}}
 
 
-def bench_batched(torch, ccl, hbm_gbs):
+def _oracle_batch_task(task):
+    """Worker of oracle_all_cores: labels one image of the batch, read from
+    the memory-mapped batch file, with the CPU oracle."""
+    import numpy as np
+
+    import oracle
+
+    path, off, H, W, conn = task
+    img = np.memmap(path, dtype=np.uint8, mode="r", offset=off, shape=(H, W))
+    oracle.label(np.asarray(img), conn)
+    return H * W
+
+
+def oracle_all_cores(imgs, conn):
+    """The CPU oracle over a whole batch, one image per task on every host
+    core (spawned worker processes; the batch is shared through a
+    memory-mapped file, so the timed region holds labelling only)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "batch.u8")
+        tasks, off = [], 0
+        with open(path, "wb") as f:
+            for im in imgs:
+                f.write(np.ascontiguousarray(im).tobytes())
+                tasks.append((path, off, im.shape[0], im.shape[1], conn))
+                off += im.size
+        # a worker that cannot start makes the executor raise, not wait
+        with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn")) as pool:
+            list(pool.map(_oracle_batch_task, tasks[:cores]))  # every worker loads the oracle
+            t0 = time.perf_counter()
+            px = sum(pool.map(_oracle_batch_task, tasks))
+            dt = time.perf_counter() - t0
+    return {"value": px / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": f"all {len(imgs)} images of the batch, one image per task"}
+
+
+def bench_batched(torch, ccl, hbm_gbs, cpu=True):
     """256 images with H, W uniform in [64, 2048], density uniform in
     [0.2, 0.8] (half Bernoulli, half sigma=4 smoothed noise), 8-connectivity:
     one ccl_label_batched call (autotuned block shape, graph replay) against
@@ -455,13 +499,19 @@ def bench_batched(torch, ccl, hbm_gbs):
             ccl.ccl_label_ws(img, ws, 8, labels=lab)
     ms_pg = timed(graph.replay)
     status = ccl.ccl_get_device_status()
-    return {"workload": "256 images, H,W ~ U[64,2048], density ~ U[0.2,0.8], 8-connectivity",
-            "pixels": px, "tile": ccl.ccl_tile_names()[tile],
-            "batched_ms": ms_b, "batched_gpixel_s": px / (ms_b / 1e3) / 1e9,
-            "plain_ms": ms_p, "plain_gpixel_s": px / (ms_p / 1e3) / 1e9,
-            "plain_graph_ms": ms_pg, "plain_graph_gpixel_s": px / (ms_pg / 1e3) / 1e9,
-            "batched_hbm_roofline_frac": px * BYTES_PER_PIXEL / (ms_b / 1e3) / (hbm_gbs * 1e9),
-            "device_status": ccl.ccl_status_string(status)}
+    res = {"workload": "256 images, H,W ~ U[64,2048], density ~ U[0.2,0.8], 8-connectivity",
+           "pixels": px, "tile": ccl.ccl_tile_names()[tile],
+           "batched_ms": ms_b, "batched_gpixel_s": px / (ms_b / 1e3) / 1e9,
+           "plain_ms": ms_p, "plain_gpixel_s": px / (ms_p / 1e3) / 1e9,
+           "plain_graph_ms": ms_pg, "plain_graph_gpixel_s": px / (ms_pg / 1e3) / 1e9,
+           "batched_hbm_roofline_frac": px * BYTES_PER_PIXEL / (ms_b / 1e3) / (hbm_gbs * 1e9),
+           "device_status": ccl.ccl_status_string(status)}
+    if cpu:
+        try:
+            res["cpu_oracle_all_cores"] = oracle_all_cores(imgs, 8)
+        except Exception as exc:  # the CPU baseline must not cost the GPU numbers
+            res["cpu_oracle_all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"}
+    return res
 
 
 def bench_variants(torch, ccl):
