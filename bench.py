@@ -18,11 +18,14 @@ The JSON line carries, besides the contract keys:
                 copies inside the timed region);
   clocks        SM clocks and throttle reasons sampled during the timed region;
   extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
-                between repetitions) with its per-kernel breakdown; the
-                256-image uneven batch (batched graph vs plain launches); the
-                coarse-labelling variants of Sec. 4.2 (time, counters);
-                component statistics of the 8192^2 labels; the serving stream
-                at 2k/5k/10k requests/s (p50/p99, Gpixel/s).
+                between repetitions) with its per-kernel breakdown; single
+                512^2 and 4096^2 images, L2 flushed and warm (min, median,
+                mean, stdev); the 256-image uneven batch (batched graph vs
+                plain launches, and the CPU oracle over the batch on every
+                host core); the serving stream at 2k/5k/10k requests/s
+                (p50/p99, Gpixel/s); the coarse-labelling variants of
+                Sec. 4.2 (time, counters); component statistics of the
+                8192^2 labels; 512^3 volumes (6/26-connectivity).
 
 ``--impl reference`` times the CPU oracle instead (the reference arm).
 """
@@ -340,6 +343,11 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line["extra"] = bench_8192(torch, ccl, hbm_gbs)
 
+    # -- extra: single 512x512 and 4096x4096 images, L2 flushed and warm
+    if rank == 0 and not args.no_extra:
+        line["extra"]["single_512"] = bench_single(torch, ccl, 512, hbm_gbs)
+        line["extra"]["single_4096"] = bench_single(torch, ccl, 4096, hbm_gbs)
+
     # -- extra: the uneven 256-image batch, batched graph vs plain launches
     if rank == 0 and not args.no_extra:
         line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs, cpu=not args.no_cpu)
@@ -371,6 +379,39 @@ def run_ours(args):
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def bench_single(torch, ccl, N, hbm_gbs, reps=100, warm=10):
+    """One N x N Bernoulli(0.5) image (seed 0), 8-connectivity, plain
+    ccl_label: CUDA events around each call after `warm` warm-up calls,
+    `reps` repetitions with L2 flushed before each (a 512 MB write) and
+    `reps` without (inputs warm in L2).  min / median / mean / stdev in us."""
+    from paper_1712_09789_gb300 import synth
+
+    img = torch.from_numpy(synth.bernoulli(N, N, 0.5, 0)).cuda()
+    out = torch.empty((N, N), dtype=torch.int32, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(warm):
+        ccl.ccl_label(img, 8, labels=out)
+    res = {"workload": f"{N}x{N} Bernoulli p=0.5 seed 0, 8-connectivity, plain path"}
+    for mode in ("cold", "warm"):
+        ts = []
+        for _ in range(reps):
+            if mode == "cold":
+                flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ccl.ccl_label(img, 8, labels=out)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) * 1e3)
+        med = statistics.median(ts)
+        res[mode] = {"min_us": min(ts), "median_us": med, "mean_us": statistics.fmean(ts),
+                     "stdev_us": statistics.stdev(ts), "gpixel_s": N * N / (med / 1e6) / 1e9,
+                     "hbm_roofline_frac": N * N * BYTES_PER_PIXEL / (med / 1e6) / (hbm_gbs * 1e9)}
+    if ccl.ccl_get_device_status() != ccl.CCL_OK:
+        raise RuntimeError("single-image labelling reported a device error")
+    return res
 
 
 def bench_8192(torch, ccl, hbm_gbs):
