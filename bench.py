@@ -350,7 +350,7 @@ def run_ours(args):
 
     # -- extra: the uneven 256-image batch, batched graph vs plain launches
     if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs, cpu=not args.no_cpu)
+        line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
 
     # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
     # frames through the continuous-batching server); it runs before the
@@ -371,6 +371,17 @@ def run_ours(args):
     if rank == 0 and not args.no_extra:
         line.setdefault("extra", {})["volume_512"] = bench_volume(torch, ccl, hbm_gbs)
 
+    # -- the CPU oracle over the whole uneven batch on every host core (after
+    # the GPU extras: its worker processes load the host)
+    if rank == 0 and world == 1 and not args.no_extra and not args.no_cpu:
+        from paper_1712_09789_gb300 import synth
+
+        try:
+            cores = oracle_all_cores(synth.batch_uneven(256, seed=0), 8)
+        except Exception as exc:  # the CPU baseline must not cost the GPU numbers
+            cores = {"unavailable": f"{type(exc).__name__}: {exc}"}
+        line["extra"]["batched_256"]["cpu_oracle_all_cores"] = cores
+
     # -- CPU oracle on a bounded sample, rank 0 at N = 1 only
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = bench_cpu(host, work, outs)
@@ -382,33 +393,51 @@ def run_ours(args):
 
 
 def bench_single(torch, ccl, N, hbm_gbs, reps=100, warm=10):
-    """One N x N Bernoulli(0.5) image (seed 0), 8-connectivity, plain
-    ccl_label: CUDA events around each call after `warm` warm-up calls,
-    `reps` repetitions with L2 flushed before each (a 512 MB write) and
-    `reps` without (inputs warm in L2).  min / median / mean / stdev in us."""
+    """One N x N Bernoulli(0.5) image (seed 0), 8-connectivity, plain path.
+    Device time: the call (``ccl_label_ws`` with caller-owned scratch)
+    captured once in a CUDA graph and replayed, CUDA events around each
+    replay, `reps` repetitions with L2 flushed before each (a 512 MB write)
+    and `reps` without, after `warm` warm-ups; min / median / mean / stdev in
+    us.  Call time: the same through ``ccl_label`` from Python, one call
+    between events, host launch work included (what a caller that waits for
+    every image sees)."""
     from paper_1712_09789_gb300 import synth
 
     img = torch.from_numpy(synth.bernoulli(N, N, 0.5, 0)).cuda()
     out = torch.empty((N, N), dtype=torch.int32, device="cuda")
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    for _ in range(warm):
-        ccl.ccl_label(img, 8, labels=out)
-    res = {"workload": f"{N}x{N} Bernoulli p=0.5 seed 0, 8-connectivity, plain path"}
-    for mode in ("cold", "warm"):
+    ws = torch.empty(ccl.ccl_workspace_size(N, N, 8), dtype=torch.uint8, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warm):
+            ccl.ccl_label_ws(img, ws, 8, labels=out)
+    torch.cuda.current_stream().wait_stream(side)
+    with torch.cuda.graph(graph):
+        ccl.ccl_label_ws(img, ws, 8, labels=out)
+
+    def stats(fn, cold):
         ts = []
         for _ in range(reps):
-            if mode == "cold":
+            if cold:
                 flush.fill_(1)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            ccl.ccl_label(img, 8, labels=out)
+            fn()
             b.record()
             b.synchronize()
             ts.append(a.elapsed_time(b) * 1e3)
         med = statistics.median(ts)
-        res[mode] = {"min_us": min(ts), "median_us": med, "mean_us": statistics.fmean(ts),
-                     "stdev_us": statistics.stdev(ts), "gpixel_s": N * N / (med / 1e6) / 1e9,
-                     "hbm_roofline_frac": N * N * BYTES_PER_PIXEL / (med / 1e6) / (hbm_gbs * 1e9)}
+        return {"min_us": min(ts), "median_us": med, "mean_us": statistics.fmean(ts),
+                "stdev_us": statistics.stdev(ts), "gpixel_s": N * N / (med / 1e6) / 1e9,
+                "hbm_roofline_frac": N * N * BYTES_PER_PIXEL / (med / 1e6) / (hbm_gbs * 1e9)}
+
+    for _ in range(warm):
+        graph.replay()
+    res = {"workload": f"{N}x{N} Bernoulli p=0.5 seed 0, 8-connectivity, plain path",
+           "device_cold": stats(graph.replay, True), "device_warm": stats(graph.replay, False),
+           "call_cold": stats(lambda: ccl.ccl_label(img, 8, labels=out), True)}
     if ccl.ccl_get_device_status() != ccl.CCL_OK:
         raise RuntimeError("single-image labelling reported a device error")
     return res
@@ -489,7 +518,7 @@ def oracle_all_cores(imgs, conn):
             "sample": f"all {len(imgs)} images of the batch, one image per task"}
 
 
-def bench_batched(torch, ccl, hbm_gbs, cpu=True):
+def bench_batched(torch, ccl, hbm_gbs):
     """256 images with H, W uniform in [64, 2048], density uniform in
     [0.2, 0.8] (half Bernoulli, half sigma=4 smoothed noise), 8-connectivity:
     one ccl_label_batched call (autotuned block shape, graph replay) against
@@ -547,11 +576,6 @@ def bench_batched(torch, ccl, hbm_gbs, cpu=True):
            "plain_graph_ms": ms_pg, "plain_graph_gpixel_s": px / (ms_pg / 1e3) / 1e9,
            "batched_hbm_roofline_frac": px * BYTES_PER_PIXEL / (ms_b / 1e3) / (hbm_gbs * 1e9),
            "device_status": ccl.ccl_status_string(status)}
-    if cpu:
-        try:
-            res["cpu_oracle_all_cores"] = oracle_all_cores(imgs, 8)
-        except Exception as exc:  # the CPU baseline must not cost the GPU numbers
-            res["cpu_oracle_all_cores"] = {"unavailable": f"{type(exc).__name__}: {exc}"}
     return res
 
 
