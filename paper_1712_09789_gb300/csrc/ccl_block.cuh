@@ -1,7 +1,9 @@
 // ccl_block.cuh -- device building blocks of the block-based labeller.
 //
-// Geometry.  A CTA owns a block of (32 * BLX) x (8 * BLY) pixels and has one
-// thread per lane tile of 32 columns x 8 rows (tx = t % BLX, ty = t / BLX).
+// Geometry.  A CTA owns a block of (32 * BLX) x (kLH * BLY) pixels and has one
+// thread per lane tile of 32 columns x kLH rows (tx = t % BLX, ty = t / BLX).
+// Short lane tiles keep each thread's chain of dependent steps short, so a
+// mid-size image still puts enough warps on every SM.
 // A thread holds each row of its lane tile as a 32-bit mask (bit c = column
 // c).  The block shape (BLX, BLY) is a template parameter so that the batched
 // path can pick it per workload.
@@ -17,13 +19,15 @@
 // work shrinks.  Pieces are numbered per lane tile in band order, then column
 // order, which is recomputable from the masks by a popcount.
 //
-// Label-equivalence lists.  Piece `loc` of thread t has the id (t << 7) | loc
+// Label-equivalence lists.  Piece `loc` of thread t has the id
+// (t << kLocBits) | loc
 // and one 16-bit entry in shared memory: a root holds kRoot | key, key being
 // the block raster position (row * block width + column) of the smallest
 // pixel of its list; any other entry holds the id of its parent.  Links go
 // from the larger key to the smaller (Sec. 3.1.3 and 3.2), so the root of a
 // component carries the component's smallest block raster position.  Entry of
-// id i lives at par[(i & 127) * threads + (i >> 7)], so 32 lanes touching
+// id i lives at par[(i & (capacity - 1)) * threads + (i >> kLocBits)], so 32
+// lanes touching
 // their own piece loc hit 32 consecutive half-words.
 #pragma once
 
@@ -33,8 +37,10 @@
 namespace ccl {
 
 constexpr int kLW = 32;                 // lane tile width (bits of a row mask)
-constexpr int kLH = 8;                  // lane tile height (rows of a thread)
+constexpr int kLH = 4;                  // lane tile height (rows of a thread)
 constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile: at most 32 per two-row band
+constexpr int kLocBits = 6;             // piece index bits of a piece id (thread << kLocBits | piece)
+static_assert(kPieceCapMax <= (1 << kLocBits), "piece indices must fit their bits");
 constexpr int kVChunksMax = kPieceCapMax / 8;  // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
 constexpr uint16_t kBorderRoot = 0x4000;  // entry of a root once its border slot is known: kBorderRoot | slot
@@ -65,10 +71,10 @@ struct Geo {
     static constexpr int kEdgeLeft = 2 * kBW;
     static constexpr int kEdgeRight = 2 * kBW + kBH;
     static constexpr int kEdge = 2 * kBW + 2 * kBH;
-    // ids carry the thread index above 7 piece bits and stay below kRoot;
-    // block keys fit 15 bits
-    static_assert(kThreads >= 32 && kThreads <= 128 && (kThreads & (kThreads - 1)) == 0,
-                  "32..128 threads, a power of two");
+    // ids carry the thread index above kLocBits piece bits and stay below
+    // kBorderRoot (an entry below it is a parent id); block keys fit 15 bits
+    static_assert(kThreads >= 32 && (kThreads << kLocBits) <= kBorderRoot && (kThreads & (kThreads - 1)) == 0,
+                  "32..256 threads, a power of two");
     static_assert((BLX & (BLX - 1)) == 0, "BLX must be a power of two");
     static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
     static_assert((kEdge * 2) % 16 == 0, "border records must stay 16-byte aligned");
@@ -172,10 +178,13 @@ __device__ __forceinline__ int piece_end(uint32_t ends, int u) { return u + lobi
 // ---------------------------------------------------------------------------
 // Shared-memory label-equivalence lists of one block.
 
+// Id of piece `loc` of the lane tile of thread t.
+__device__ __forceinline__ int piece_id(int t, int loc) { return (t << kLocBits) | loc; }
+
 // (masked on both fields, so no entry value can address outside the table)
 template <class G, int kCap>
 __device__ __forceinline__ int par_index(int id) {
-    return (id & (kCap - 1)) * G::kThreads + ((id >> 7) & (G::kThreads - 1));
+    return (id & (kCap - 1)) * G::kThreads + ((id >> kLocBits) & (G::kThreads - 1));
 }
 
 // Root of id and the root's entry.  Path halving rewrites only non-root

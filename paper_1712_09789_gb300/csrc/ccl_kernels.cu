@@ -1,8 +1,8 @@
 // ccl_kernels.cu -- the steps of the block-based labeller as sm_103a kernels,
 // and the launchers that enqueue them on a stream.
 //
-//   k_block_local   step 1, Kernel 1 (Sec. 3.1) on blocks of 32*BLX x 8*BLY
-//                   pixels.  Every thread labels its 32 x 8 lane tile band by
+//   k_block_local   step 1, Kernel 1 (Sec. 3.1) on blocks of 32*BLX x kLH*BLY
+//                   pixels.  Every thread labels its 32 x kLH lane tile band by
 //                   band: coarse labelling hangs each piece under the first
 //                   piece of the band above that it touches (row connection
 //                   is free inside a piece; column connection by bit
@@ -50,7 +50,7 @@ __device__ unsigned long long g_variant_ops[3];
 // Per-block scratch regions, indexed by the global block (item) index; sized
 // for capacity, only the used parts are touched.
 struct Scratch {
-    uint32_t *masks;   // [blocks][threads][8 rows]
+    uint32_t *masks;   // [blocks][threads][kLH rows]
     uint4 *vstream;    // [blocks][kVChunksMax][threads]: piece values, 8 per chunk
     uint16_t *edges;   // [blocks][edge entries]
     uint64_t *P;       // [blocks][slots]
@@ -207,7 +207,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     if (t == 0) sm.err = 0;
     for (int i = t; i < LocalSmem<G, kCap>::kWords; i += T) sm.border[i] = 0u;
 
-    // -- initialization: the lane tile's 8 rows as masks (all loads in flight
+    // -- initialization: the lane tile's kLH rows as masks (all loads in flight
     // at once; pixels outside the image are background)
     uint32_t mrow[kLH];
     if (vec_in && xl + kLW <= W && yl + kLH <= H) {
@@ -254,7 +254,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             if (nq == 16) {
                 for (int j = 0; j < 16; ++j) {
                     const int q = sm.xq[j][t];
-                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err, ops);
+                    union_private<G, kCap>(par, piece_id(t, q >> 7), piece_id(t, q & 127), cap, err, ops);
                 }
                 nq = 0;
             }
@@ -280,7 +280,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const int u0 = lobit(P | 0x80000000u);
                 const int up = P ? base_prev + __popc(pS & upto(u0)) - 1 : 0;
                 const uint16_t ue = par[up * T + t];
-                const uint16_t ent = (V::kCol && P) ? ((ue & kRoot) ? (uint16_t)((t << 7) | up) : ue)
+                const uint16_t ent = (V::kCol && P) ? ((ue & kRoot) ? (uint16_t)piece_id(t, up) : ue)
                                                     : (uint16_t)(kRoot | piece_key<G>(tx, ty, k, A, rb, a0));
                 if (act) par[(npieces + i) * T + t] = ent;
                 // (a piece above is a further contact of at most one piece of
@@ -306,7 +306,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             for (int j = 0; j < nqmax; ++j) {
                 if (j < nq) {
                     const int q = sm.xq[j][t];
-                    union_private<G, kCap>(par, (t << 7) | (q >> 7), (t << 7) | (q & 127), cap, err, ops);
+                    union_private<G, kCap>(par, piece_id(t, q >> 7), piece_id(t, q & 127), cap, err, ops);
                 }
             }
             base_prev = npieces;
@@ -366,8 +366,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl];
             const int np = __popc(elem_starts<kConn8, V::kRow>(A, Bm));
             const int lnp = __popc(elem_starts<kConn8, V::kRow>(lA, lB));
-            const int me_first = (t << 7) | mb;
-            const int l_last = (tl << 7) | (lbase + lnp - 1);
+            const int me_first = piece_id(t, mb);
+            const int l_last = piece_id(tl, lbase + lnp - 1);
             // column 0 of my band k beside column 31 of the left band k
             const uint32_t side = kConn8 ? (A | Bm) & ((lA | lB) >> 31) : (A & (lA >> 31)) | (Bm & (lB >> 31));
             seam(hasl && (side & 1u), me_first, l_last);
@@ -375,11 +375,11 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const uint32_t nA = mrow[(k + 1) * R];
                 const uint32_t lnA = sm.mask[(k + 1) * R][tl];
                 const int l_next_last =
-                    (tl << 7) | (lbase + lnp + __popc(elem_starts<kConn8, V::kRow>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
+                    piece_id(tl, lbase + lnp + __popc(elem_starts<kConn8, V::kRow>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
                 // lower row of my band k, column 0 ~ upper row of the left band k+1, column 31
                 seam(hasl && (Bm & 1u) && (lnA >> 31), me_first, l_next_last);
                 // upper row of my band k+1, column 0 ~ lower row of the left band k, column 31
-                seam(hasl && (nA & 1u) && (lB >> 31), (t << 7) | (mb + np), l_last);
+                seam(hasl && (nA & 1u) && (lB >> 31), piece_id(t, mb + np), l_last);
             }
             mb += np;
             lbase += lnp;
@@ -402,12 +402,12 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             S &= S - 1u;
             E &= E - 1u;
             uint32_t P = act ? (uB & touch_range<kConn8>(A0 & run_bits(a0, a1))) : 0u;
-            const int me = (t << 7) | i;
+            const int me = piece_id(t, i);
             while (__any_sync(kFull, P != 0u)) {
                 room(1);
                 const bool hp = P != 0u;
                 const int u = hp ? lobit(P) : 0;
-                seam(hp, me, (tu << 7) | (ubase + __popc(uS & upto(u)) - 1));
+                seam(hp, me, piece_id(tu, ubase + __popc(uS & upto(u)) - 1));
                 if (hp) P &= ~upto(piece_end(uE, u));
             }
         }
@@ -417,11 +417,11 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const bool ul = hasu && tx > 0 && (A0 & 1u);
             const int tul = ul ? tu - 1 : t;
             const uint32_t ulB = sm.mask[kLH - 1][tul];
-            seam(ul && (ulB >> 31), t << 7,
-                 (tul << 7) | (sm.lastbase[tul] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - 2][tul], ulB)) - 1));
+            seam(ul && (ulB >> 31), piece_id(t, 0),
+                 piece_id(tul, sm.lastbase[tul] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - 2][tul], ulB)) - 1));
             const bool ur = hasu && tx + 1 < G::BLX && (A0 >> 31);
             const int tur = ur ? tu + 1 : t;
-            seam(ur && (sm.mask[kLH - 1][tur] & 1u), (t << 7) | (__popc(S00) - 1), (tur << 7) | sm.lastbase[tur]);
+            seam(ur && (sm.mask[kLH - 1][tur] & 1u), piece_id(t, __popc(S00) - 1), piece_id(tur, sm.lastbase[tur]));
         }
         flush();
     }
@@ -430,7 +430,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     // -- compress: every own entry points straight at its root (the finds
     // only read, so every store here is a final root)
     for (int loc = 0; loc < npieces; ++loc) {
-        const int id = (t << 7) | loc;
+        const int id = piece_id(t, loc);
         const int root = find_root_ro<G, kCap>(vpar, id, cap, err);
         if (root != id) vpar[loc * T + t] = (uint16_t)root;
     }
@@ -453,7 +453,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const int a0 = lobit(S), a1 = lobit(E);
             S &= S - 1u;
             E &= E - 1u;
-            if (A0 & run_bits(a0, a1)) mark((t << 7) | i);
+            if (A0 & run_bits(a0, a1)) mark(piece_id(t, i));
         }
     }
     if (ty == G::BLY - 1) {
@@ -462,7 +462,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const int a0 = lobit(S), a1 = lobit(E);
             S &= S - 1u;
             E &= E - 1u;
-            if (BL & run_bits(a0, a1)) mark((t << 7) | i);
+            if (BL & run_bits(a0, a1)) mark(piece_id(t, i));
         }
     }
     if (tx == 0 || tx == G::BLX - 1) {
@@ -471,8 +471,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         for (int k = 0; k < NB; ++k) {
             const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
             const int np = __popc(elem_starts<kConn8, V::kRow>(mrow[k * R], mrow[k * R + R - 1]));
-            if (tx == 0 && (OR & 1u)) mark((t << 7) | mb);
-            if (tx == G::BLX - 1 && (OR >> 31)) mark((t << 7) | (mb + np - 1));
+            if (tx == 0 && (OR & 1u)) mark(piece_id(t, mb));
+            if (tx == G::BLX - 1 && (OR >> 31)) mark(piece_id(t, mb + np - 1));
             mb += np;
         }
     }
@@ -554,7 +554,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         const uint32_t A = sm.mask[0][lt];
         uint16_t v = kBg;
         if ((A >> bit) & 1u)
-            v = border_slot(value_of((lt << 7) | (__popc(elem_starts<kConn8, V::kRow>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
+            v = border_slot(value_of(piece_id(lt, __popc(elem_starts<kConn8, V::kRow>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
         Eb[G::kEdgeTop + c] = v;
         // bottom row: the last band of the lane tiles with ty == BLY - 1
         const int lb2 = (G::BLY - 1) * G::BLX + lt;
@@ -562,14 +562,14 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         v = kBg;
         if ((Bl >> bit) & 1u)
             v = border_slot(value_of(
-                (lb2 << 7) | (sm.lastbase[lb2] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
+                piece_id(lb2, sm.lastbase[lb2] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
         Eb[G::kEdgeBottom + c] = v;
     }
     for (int i = t; i < 2 * G::kBH; i += T) {
         // left column (first G::kBH indices) and right column of the block
         const bool right = i >= G::kBH;
         const int r = right ? i - G::kBH : i;
-        const int lt = (r >> 3) * G::BLX + (right ? G::BLX - 1 : 0);
+        const int lt = (r / kLH) * G::BLX + (right ? G::BLX - 1 : 0);
         const int rr = r & (kLH - 1), k = rr / R;
         const uint32_t m = sm.mask[rr][lt];
         uint16_t v = kBg;
@@ -578,7 +578,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             for (int j = 0; j < k; ++j) base += __popc(elem_starts<kConn8, V::kRow>(sm.mask[j * R][lt], sm.mask[j * R + R - 1][lt]));
             const int loc = right ? base + __popc(elem_starts<kConn8, V::kRow>(sm.mask[k * R][lt], sm.mask[k * R + R - 1][lt])) - 1
                                   : base;
-            v = border_slot(value_of((lt << 7) | loc));
+            v = border_slot(value_of(piece_id(lt, loc)));
         }
         Eb[(right ? G::kEdgeRight : G::kEdgeLeft) + r] = v;
     }
@@ -587,7 +587,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         uint4 *vout = s.vstream + (size_t)b * kVChunksMax * T + t;
         HalfQueue vq;
         for (int loc = 0; loc < npieces; ++loc) {
-            vq.push(value_of((t << 7) | loc));
+            vq.push(value_of(piece_id(t, loc)));
             if ((loc & 7) == 7) vout[(size_t)(loc >> 3) * T] = vq.bits();
         }
         if (npieces & 7) {
@@ -598,8 +598,9 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     // -- row masks for the write-out pass
     {
         uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
-        mo[0] = make_uint4(mrow[0], mrow[1], mrow[2], mrow[3]);
-        mo[1] = make_uint4(mrow[4], mrow[5], mrow[6], mrow[7]);
+#pragma unroll
+        for (int q = 0; q < kLH / 4; ++q)
+            mo[q] = make_uint4(mrow[4 * q], mrow[4 * q + 1], mrow[4 * q + 2], mrow[4 * q + 3]);
     }
     if (err) atomicOr(&sm.err, err);
     if (kCount) {
@@ -617,7 +618,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 }
 
 template <class G, bool kConn8, int kMode = 0, bool kCount = false>
-__global__ void __launch_bounds__(G::kThreads, (Variant<kConn8, kMode>::kCap == 64 ? 1024 : 640) / G::kThreads)
+__global__ void __launch_bounds__(G::kThreads, 1024 / G::kThreads)
     k_block_local(JobTable jt, Scratch s, int cap) {
     using Sm = LocalSmem<G, Variant<kConn8, kMode>::kCap>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -823,8 +824,15 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     report(err);
 
     const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
-    const uint4 mA = mi[0], mB = mi[1];
-    const uint32_t mrow[kLH] = {mA.x, mA.y, mA.z, mA.w, mB.x, mB.y, mB.z, mB.w};
+    uint32_t mrow[kLH];
+#pragma unroll
+    for (int q = 0; q < kLH / 4; ++q) {
+        const uint4 m4 = mi[q];
+        mrow[4 * q] = m4.x;
+        mrow[4 * q + 1] = m4.y;
+        mrow[4 * q + 2] = m4.z;
+        mrow[4 * q + 3] = m4.w;
+    }
 #pragma unroll
     for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
     // per-piece values, 8 per chunk; the next chunk is always already in flight
@@ -962,9 +970,9 @@ size_t blocks_of(int H, int W) {
     return (((size_t)W + G::kBW - 1) / G::kBW) * (((size_t)H + G::kBH - 1) / G::kBH);
 }
 
-using G0 = Geo<16, 8>;
-using G1 = Geo<8, 8>;
-using G2 = Geo<32, 4>;
+using G0 = Geo<16, 16>;
+using G1 = Geo<8, 16>;
+using G2 = Geo<32, 8>;
 
 }  // namespace
 
