@@ -721,6 +721,9 @@ def bench_serving(torch, ccl, seconds, rates=(2000, 5000, 10000), warm=0.5):
     with ccl.CclServer(max_slots=64, n_streams=4, max_batch=32, hbm_budget_bytes=8 << 30) as srv:
         for i in range(len(frames)):       # warm the server, its graphs and the autotuner
             srv.wait(srv.submit(hv[i], ov[i], 8))
+        for _ in range(3):                 # and bursts, so that full batches have run on every stream
+            for t in [srv.submit(hv[i], ov[i], 8) for i in range(len(frames))]:
+                srv.wait(t)
         for rate in rates:
             arr = synth.poisson_arrivals(rate, warm + seconds, seed=rate)
             owner = [None] * len(frames)

@@ -72,8 +72,10 @@ ccl_status ensure_capacity(Runner &R, size_t njobs, size_t blocks) {
             return CCL_ERR_CUDA;
     if (njobs <= R.cap_jobs && blocks <= R.cap_blocks) return CCL_OK;
     drop_graphs(R);
-    const size_t nj = std::max(njobs + njobs / 4, std::max<size_t>(R.cap_jobs, 16));
-    const size_t nb = std::max(blocks + blocks / 4, R.cap_blocks);
+    // doubling: a stream of growing batches (a server warming up) re-sizes,
+    // re-allocates and re-captures only a few times
+    const size_t nj = std::max(2 * njobs, std::max<size_t>(R.cap_jobs, 16));
+    const size_t nb = std::max(2 * blocks, R.cap_blocks);
     if (R.d_table) cudaFree(R.d_table);
     if (R.d_ws) cudaFree(R.d_ws);
     R.d_table = nullptr;

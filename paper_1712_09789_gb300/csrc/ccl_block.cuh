@@ -37,11 +37,6 @@
 namespace ccl {
 
 constexpr int kLW = 32;                 // lane tile width (bits of a row mask)
-constexpr int kLH = 4;                  // lane tile height (rows of a thread)
-constexpr int kPieceCapMax = kLH * 16;  // pieces per lane tile: at most 32 per two-row band
-constexpr int kLocBits = 6;             // piece index bits of a piece id (thread << kLocBits | piece)
-static_assert(kPieceCapMax <= (1 << kLocBits), "piece indices must fit their bits");
-constexpr int kVChunksMax = kPieceCapMax / 8;  // 8 two-byte values per 16-byte chunk
 constexpr uint16_t kRoot = 0x8000;
 constexpr uint16_t kBorderRoot = 0x4000;  // entry of a root once its border slot is known: kBorderRoot | slot
 constexpr uint16_t kBg = 0xFFFF;
@@ -53,11 +48,15 @@ constexpr int kErrGlobalCap = 2;
 
 constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
 
-template <int BLX_, int BLY_>
+template <int BLX_, int BLY_, int LH_>
 struct Geo {
     static constexpr int BLX = BLX_;                  // lane tiles across a block
     static constexpr int BLY = BLY_;                  // lane tiles down a block
+    static constexpr int kLH = LH_;                   // lane tile height (rows of a thread)
     static constexpr int kThreads = BLX * BLY;
+    static constexpr int kPieceCap = kLH * 16;        // elements per lane tile: at most 32 per two-row band
+    static constexpr int kLocBits = ilog2(kPieceCap); // piece index bits of a piece id
+    static constexpr int kVChunks = kPieceCap / 8;    // 8 two-byte values per 16-byte chunk
     static constexpr int kBW = kLW * BLX;
     static constexpr int kBH = kLH * BLY;
     static constexpr int kBWLog2 = ilog2(kBW);
@@ -76,6 +75,7 @@ struct Geo {
     static_assert(kThreads >= 32 && (kThreads << kLocBits) <= kBorderRoot && (kThreads & (kThreads - 1)) == 0,
                   "32..256 threads, a power of two");
     static_assert((BLX & (BLX - 1)) == 0, "BLX must be a power of two");
+    static_assert(kLH % 4 == 0 && (kPieceCap & (kPieceCap - 1)) == 0, "lane tiles of 4 or 8 rows");
     static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
     static_assert((kEdge * 2) % 16 == 0, "border records must stay 16-byte aligned");
 };
@@ -83,7 +83,7 @@ struct Geo {
 // Band layout of a lane tile for one connectivity: bands of two rows; a band
 // holds at most 16 pieces under 8-connectivity (pieces are runs of the OR of
 // its rows), 32 under 4-connectivity (one per column at most).
-template <bool kConn8>
+template <bool kConn8, int kLH>
 struct Bands {
     static constexpr int kRows = 2;                // rows per band
     static constexpr int kN = kLH / kRows;         // bands per lane tile
@@ -156,7 +156,7 @@ __device__ __forceinline__ uint32_t band_ends(uint32_t A, uint32_t B) {
 // of its own, and the links between neighbouring columns are refined).  Along
 // columns: an element takes the first element above it that it touches as
 // parent (else every contact with the band above is refined).
-template <bool kConn8, int kMode>
+template <bool kConn8, int kMode, int kLH>
 struct Variant {
     static constexpr bool kRow = kMode == 0 || kMode == 1;
     static constexpr bool kCol = kMode == 0 || kMode == 2;
@@ -179,12 +179,13 @@ __device__ __forceinline__ int piece_end(uint32_t ends, int u) { return u + lobi
 // Shared-memory label-equivalence lists of one block.
 
 // Id of piece `loc` of the lane tile of thread t.
-__device__ __forceinline__ int piece_id(int t, int loc) { return (t << kLocBits) | loc; }
+template <class G>
+__device__ __forceinline__ int piece_id(int t, int loc) { return (t << G::kLocBits) | loc; }
 
 // (masked on both fields, so no entry value can address outside the table)
 template <class G, int kCap>
 __device__ __forceinline__ int par_index(int id) {
-    return (id & (kCap - 1)) * G::kThreads + ((id >> kLocBits) & (G::kThreads - 1));
+    return (id & (kCap - 1)) * G::kThreads + ((id >> G::kLocBits) & (G::kThreads - 1));
 }
 
 // Root of id and the root's entry.  Path halving rewrites only non-root

@@ -41,9 +41,11 @@ struct JobTable {
     unsigned total;
 };
 
-// Block shapes (lane tiles across x down): 0 = 16x8 (512x64 pixels, 128
-// threads), 1 = 8x8 (256x64, 64 threads), 2 = 32x4 (1024x32, 128 threads).
-constexpr int kNumGeo = 3;
+// Block shapes (lane tiles across x down, lane tile rows): 0 = 16x16 of
+// 32x4 (512x64 pixels, 256 threads), 1 = 8x16 of 32x4 (256x64, 128 threads),
+// 2 = 32x8 of 32x4 (1024x32, 256 threads), 3 = 16x8 of 32x8 (512x64, 128
+// threads).
+constexpr int kNumGeo = 4;
 const char *geo_name(int geo);
 size_t geo_blocks(int geo, int H, int W);
 size_t geo_workspace_bytes(int geo, size_t blocks);

@@ -50,8 +50,8 @@ __device__ unsigned long long g_variant_ops[3];
 // Per-block scratch regions, indexed by the global block (item) index; sized
 // for capacity, only the used parts are touched.
 struct Scratch {
-    uint32_t *masks;   // [blocks][threads][kLH rows]
-    uint4 *vstream;    // [blocks][kVChunksMax][threads]: piece values, 8 per chunk
+    uint32_t *masks;   // [blocks][threads][lane tile rows]
+    uint4 *vstream;    // [blocks][G::kVChunks][threads]: piece values, 8 per chunk
     uint16_t *edges;   // [blocks][edge entries]
     uint64_t *P;       // [blocks][slots]
     int32_t *nslots;   // [blocks]
@@ -138,7 +138,7 @@ struct LocalSmem {
     static constexpr int kCap = kCap_;
     static constexpr int kWords = kCap * G::kThreads / 32;  // bitmap words over all entries
     uint16_t par[kCap * G::kThreads];  // list entries, see ccl_block.cuh
-    uint32_t mask[kLH][G::kThreads];   // row masks
+    uint32_t mask[G::kLH][G::kThreads];   // row masks
     uint32_t border[kWords];           // bit per entry: root owning a block-border pixel
     uint32_t prefix[kWords];           // border roots in the words before
     uint32_t warp_tot[G::kThreads / 32];
@@ -163,7 +163,7 @@ __device__ __forceinline__ int piece_key(int tx, int ty, int k, uint32_t A, uint
     const uint32_t top = A & rb;
     const int row = 2 * k + (top ? 0 : 1);
     const int col = top ? lobit(top) : a0;
-    return ((kLH * ty + row) << G::kBWLog2) + kLW * tx + col;
+    return ((G::kLH * ty + row) << G::kBWLog2) + kLW * tx + col;
 }
 
 // 8 two-byte values collected low half first in a 128-bit shift register.
@@ -180,9 +180,9 @@ struct HalfQueue {
 
 template <class G, bool kConn8, int kMode, bool kCount>
 __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
-                                              LocalSmem<G, Variant<kConn8, kMode>::kCap> &sm, int cap) {
-    using Bd = Bands<kConn8>;
-    using V = Variant<kConn8, kMode>;
+                                              LocalSmem<G, Variant<kConn8, kMode, G::kLH>::kCap> &sm, int cap) {
+    using Bd = Bands<kConn8, G::kLH>;
+    using V = Variant<kConn8, kMode, G::kLH>;
     constexpr int kCap = V::kCap;
     constexpr int R = Bd::kRows;
     constexpr int NB = Bd::kN;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     const int x0 = bx * G::kBW, y0 = by * G::kBH;
     const int t = threadIdx.x;
     const int tx = t & (G::BLX - 1), ty = t >> G::kBLXLog2;
-    const int xl = x0 + kLW * tx, yl = y0 + kLH * ty;
+    const int xl = x0 + kLW * tx, yl = y0 + G::kLH * ty;
     int err = 0;
     unsigned cnt[3] = {0u, 0u, 0u};
     unsigned *const ops = kCount ? cnt : nullptr;
@@ -207,22 +207,22 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     if (t == 0) sm.err = 0;
     for (int i = t; i < LocalSmem<G, kCap>::kWords; i += T) sm.border[i] = 0u;
 
-    // -- initialization: the lane tile's kLH rows as masks (all loads in flight
+    // -- initialization: the lane tile's G::kLH rows as masks (all loads in flight
     // at once; pixels outside the image are background)
-    uint32_t mrow[kLH];
-    if (vec_in && xl + kLW <= W && yl + kLH <= H) {
-        uint4 raw[2 * kLH];
+    uint32_t mrow[G::kLH];
+    if (vec_in && xl + kLW <= W && yl + G::kLH <= H) {
+        uint4 raw[2 * G::kLH];
         const uint8_t *p = img + (size_t)yl * pitch + xl;
 #pragma unroll
-        for (int r = 0; r < kLH; ++r) {
+        for (int r = 0; r < G::kLH; ++r) {
             raw[2 * r] = ldg_nc16(p + (size_t)r * pitch);
             raw[2 * r + 1] = ldg_nc16(p + (size_t)r * pitch + 16);
         }
 #pragma unroll
-        for (int r = 0; r < kLH; ++r) mrow[r] = nz16(raw[2 * r]) | (nz16(raw[2 * r + 1]) << 16);
+        for (int r = 0; r < G::kLH; ++r) mrow[r] = nz16(raw[2 * r]) | (nz16(raw[2 * r + 1]) << 16);
     } else {
 #pragma unroll
-        for (int r = 0; r < kLH; ++r) {
+        for (int r = 0; r < G::kLH; ++r) {
             uint32_t m = 0;
             const int y = yl + r;
             if (y < H && xl < W) {
@@ -234,7 +234,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         }
     }
 #pragma unroll
-    for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
+    for (int r = 0; r < G::kLH; ++r) sm.mask[r][t] = mrow[r];
 
     // -- coarse labelling and refinement, band by band, on the thread's own
     // entries only.  A piece touching the band above takes the first piece it
@@ -254,7 +254,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             if (nq == 16) {
                 for (int j = 0; j < 16; ++j) {
                     const int q = sm.xq[j][t];
-                    union_private<G, kCap>(par, piece_id(t, q >> 7), piece_id(t, q & 127), cap, err, ops);
+                    union_private<G, kCap>(par, piece_id<G>(t, q >> 7), piece_id<G>(t, q & 127), cap, err, ops);
                 }
                 nq = 0;
             }
@@ -280,7 +280,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const int u0 = lobit(P | 0x80000000u);
                 const int up = P ? base_prev + __popc(pS & upto(u0)) - 1 : 0;
                 const uint16_t ue = par[up * T + t];
-                const uint16_t ent = (V::kCol && P) ? ((ue & kRoot) ? (uint16_t)piece_id(t, up) : ue)
+                const uint16_t ent = (V::kCol && P) ? ((ue & kRoot) ? (uint16_t)piece_id<G>(t, up) : ue)
                                                     : (uint16_t)(kRoot | piece_key<G>(tx, ty, k, A, rb, a0));
                 if (act) par[(npieces + i) * T + t] = ent;
                 // (a piece above is a further contact of at most one piece of
@@ -306,7 +306,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             for (int j = 0; j < nqmax; ++j) {
                 if (j < nq) {
                     const int q = sm.xq[j][t];
-                    union_private<G, kCap>(par, piece_id(t, q >> 7), piece_id(t, q & 127), cap, err, ops);
+                    union_private<G, kCap>(par, piece_id<G>(t, q >> 7), piece_id<G>(t, q & 127), cap, err, ops);
                 }
             }
             base_prev = npieces;
@@ -366,8 +366,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const uint32_t lA = sm.mask[k * R][tl], lB = sm.mask[k * R + R - 1][tl];
             const int np = __popc(elem_starts<kConn8, V::kRow>(A, Bm));
             const int lnp = __popc(elem_starts<kConn8, V::kRow>(lA, lB));
-            const int me_first = piece_id(t, mb);
-            const int l_last = piece_id(tl, lbase + lnp - 1);
+            const int me_first = piece_id<G>(t, mb);
+            const int l_last = piece_id<G>(tl, lbase + lnp - 1);
             // column 0 of my band k beside column 31 of the left band k
             const uint32_t side = kConn8 ? (A | Bm) & ((lA | lB) >> 31) : (A & (lA >> 31)) | (Bm & (lB >> 31));
             seam(hasl && (side & 1u), me_first, l_last);
@@ -375,11 +375,11 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
                 const uint32_t nA = mrow[(k + 1) * R];
                 const uint32_t lnA = sm.mask[(k + 1) * R][tl];
                 const int l_next_last =
-                    piece_id(tl, lbase + lnp + __popc(elem_starts<kConn8, V::kRow>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
+                    piece_id<G>(tl, lbase + lnp + __popc(elem_starts<kConn8, V::kRow>(lnA, sm.mask[(k + 1) * R + R - 1][tl])) - 1);
                 // lower row of my band k, column 0 ~ upper row of the left band k+1, column 31
                 seam(hasl && (Bm & 1u) && (lnA >> 31), me_first, l_next_last);
                 // upper row of my band k+1, column 0 ~ lower row of the left band k, column 31
-                seam(hasl && (nA & 1u) && (lB >> 31), piece_id(t, mb + np), l_last);
+                seam(hasl && (nA & 1u) && (lB >> 31), piece_id<G>(t, mb + np), l_last);
             }
             mb += np;
             lbase += lnp;
@@ -390,7 +390,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     {
         const bool hasu = ty > 0;
         const int tu = hasu ? t - G::BLX : t;
-        const uint32_t uA = sm.mask[kLH - R][tu], uB = sm.mask[kLH - 1][tu];
+        const uint32_t uA = sm.mask[G::kLH - R][tu], uB = sm.mask[G::kLH - 1][tu];
         const uint32_t uS = elem_starts<kConn8, V::kRow>(uA, uB), uE = elem_ends<kConn8, V::kRow>(uA, uB);
         const int ubase = sm.lastbase[tu];
         uint32_t S = hasu ? S00 : 0u;
@@ -402,12 +402,12 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             S &= S - 1u;
             E &= E - 1u;
             uint32_t P = act ? (uB & touch_range<kConn8>(A0 & run_bits(a0, a1))) : 0u;
-            const int me = piece_id(t, i);
+            const int me = piece_id<G>(t, i);
             while (__any_sync(kFull, P != 0u)) {
                 room(1);
                 const bool hp = P != 0u;
                 const int u = hp ? lobit(P) : 0;
-                seam(hp, me, piece_id(tu, ubase + __popc(uS & upto(u)) - 1));
+                seam(hp, me, piece_id<G>(tu, ubase + __popc(uS & upto(u)) - 1));
                 if (hp) P &= ~upto(piece_end(uE, u));
             }
         }
@@ -416,12 +416,12 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             room(2);
             const bool ul = hasu && tx > 0 && (A0 & 1u);
             const int tul = ul ? tu - 1 : t;
-            const uint32_t ulB = sm.mask[kLH - 1][tul];
-            seam(ul && (ulB >> 31), piece_id(t, 0),
-                 piece_id(tul, sm.lastbase[tul] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - 2][tul], ulB)) - 1));
+            const uint32_t ulB = sm.mask[G::kLH - 1][tul];
+            seam(ul && (ulB >> 31), piece_id<G>(t, 0),
+                 piece_id<G>(tul, sm.lastbase[tul] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[G::kLH - 2][tul], ulB)) - 1));
             const bool ur = hasu && tx + 1 < G::BLX && (A0 >> 31);
             const int tur = ur ? tu + 1 : t;
-            seam(ur && (sm.mask[kLH - 1][tur] & 1u), piece_id(t, __popc(S00) - 1), piece_id(tur, sm.lastbase[tur]));
+            seam(ur && (sm.mask[G::kLH - 1][tur] & 1u), piece_id<G>(t, __popc(S00) - 1), piece_id<G>(tur, sm.lastbase[tur]));
         }
         flush();
     }
@@ -430,7 +430,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     // -- compress: every own entry points straight at its root (the finds
     // only read, so every store here is a final root)
     for (int loc = 0; loc < npieces; ++loc) {
-        const int id = piece_id(t, loc);
+        const int id = piece_id<G>(t, loc);
         const int root = find_root_ro<G, kCap>(vpar, id, cap, err);
         if (root != id) vpar[loc * T + t] = (uint16_t)root;
     }
@@ -445,7 +445,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         const int bit = par_index<G, kCap>(root_of(id));
         atomicOr(&sm.border[bit >> 5], 1u << (bit & 31));
     };
-    const uint32_t AL = mrow[kLH - R], BL = mrow[kLH - 1];
+    const uint32_t AL = mrow[G::kLH - R], BL = mrow[G::kLH - 1];
     const uint32_t SL = elem_starts<kConn8, V::kRow>(AL, BL), EL = elem_ends<kConn8, V::kRow>(AL, BL);
     if (ty == 0) {
         uint32_t S = S00, E = E00;
@@ -453,7 +453,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const int a0 = lobit(S), a1 = lobit(E);
             S &= S - 1u;
             E &= E - 1u;
-            if (A0 & run_bits(a0, a1)) mark(piece_id(t, i));
+            if (A0 & run_bits(a0, a1)) mark(piece_id<G>(t, i));
         }
     }
     if (ty == G::BLY - 1) {
@@ -462,7 +462,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             const int a0 = lobit(S), a1 = lobit(E);
             S &= S - 1u;
             E &= E - 1u;
-            if (BL & run_bits(a0, a1)) mark(piece_id(t, i));
+            if (BL & run_bits(a0, a1)) mark(piece_id<G>(t, i));
         }
     }
     if (tx == 0 || tx == G::BLX - 1) {
@@ -471,8 +471,8 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         for (int k = 0; k < NB; ++k) {
             const uint32_t OR = mrow[k * R] | mrow[k * R + R - 1];
             const int np = __popc(elem_starts<kConn8, V::kRow>(mrow[k * R], mrow[k * R + R - 1]));
-            if (tx == 0 && (OR & 1u)) mark(piece_id(t, mb));
-            if (tx == G::BLX - 1 && (OR >> 31)) mark(piece_id(t, mb + np - 1));
+            if (tx == 0 && (OR & 1u)) mark(piece_id<G>(t, mb));
+            if (tx == G::BLX - 1 && (OR >> 31)) mark(piece_id<G>(t, mb + np - 1));
             mb += np;
         }
     }
@@ -554,23 +554,23 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
         const uint32_t A = sm.mask[0][lt];
         uint16_t v = kBg;
         if ((A >> bit) & 1u)
-            v = border_slot(value_of(piece_id(lt, __popc(elem_starts<kConn8, V::kRow>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
+            v = border_slot(value_of(piece_id<G>(lt, __popc(elem_starts<kConn8, V::kRow>(A, sm.mask[R - 1][lt]) & upto(bit)) - 1)));
         Eb[G::kEdgeTop + c] = v;
         // bottom row: the last band of the lane tiles with ty == BLY - 1
         const int lb2 = (G::BLY - 1) * G::BLX + lt;
-        const uint32_t Bl = sm.mask[kLH - 1][lb2];
+        const uint32_t Bl = sm.mask[G::kLH - 1][lb2];
         v = kBg;
         if ((Bl >> bit) & 1u)
             v = border_slot(value_of(
-                piece_id(lb2, sm.lastbase[lb2] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[kLH - R][lb2], Bl) & upto(bit)) - 1)));
+                piece_id<G>(lb2, sm.lastbase[lb2] + __popc(elem_starts<kConn8, V::kRow>(sm.mask[G::kLH - R][lb2], Bl) & upto(bit)) - 1)));
         Eb[G::kEdgeBottom + c] = v;
     }
     for (int i = t; i < 2 * G::kBH; i += T) {
         // left column (first G::kBH indices) and right column of the block
         const bool right = i >= G::kBH;
         const int r = right ? i - G::kBH : i;
-        const int lt = (r / kLH) * G::BLX + (right ? G::BLX - 1 : 0);
-        const int rr = r & (kLH - 1), k = rr / R;
+        const int lt = (r / G::kLH) * G::BLX + (right ? G::BLX - 1 : 0);
+        const int rr = r & (G::kLH - 1), k = rr / R;
         const uint32_t m = sm.mask[rr][lt];
         uint16_t v = kBg;
         if (right ? (m >> 31) : (m & 1u)) {
@@ -578,16 +578,16 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             for (int j = 0; j < k; ++j) base += __popc(elem_starts<kConn8, V::kRow>(sm.mask[j * R][lt], sm.mask[j * R + R - 1][lt]));
             const int loc = right ? base + __popc(elem_starts<kConn8, V::kRow>(sm.mask[k * R][lt], sm.mask[k * R + R - 1][lt])) - 1
                                   : base;
-            v = border_slot(value_of(piece_id(lt, loc)));
+            v = border_slot(value_of(piece_id<G>(lt, loc)));
         }
         Eb[(right ? G::kEdgeRight : G::kEdgeLeft) + r] = v;
     }
     // -- per-piece values, in piece order
     {
-        uint4 *vout = s.vstream + (size_t)b * kVChunksMax * T + t;
+        uint4 *vout = s.vstream + (size_t)b * G::kVChunks * T + t;
         HalfQueue vq;
         for (int loc = 0; loc < npieces; ++loc) {
-            vq.push(value_of(piece_id(t, loc)));
+            vq.push(value_of(piece_id<G>(t, loc)));
             if ((loc & 7) == 7) vout[(size_t)(loc >> 3) * T] = vq.bits();
         }
         if (npieces & 7) {
@@ -597,9 +597,9 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
     }
     // -- row masks for the write-out pass
     {
-        uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
+        uint4 *mo = reinterpret_cast<uint4 *>(s.masks + ((size_t)b * T + t) * G::kLH);
 #pragma unroll
-        for (int q = 0; q < kLH / 4; ++q)
+        for (int q = 0; q < G::kLH / 4; ++q)
             mo[q] = make_uint4(mrow[4 * q], mrow[4 * q + 1], mrow[4 * q + 2], mrow[4 * q + 3]);
     }
     if (err) atomicOr(&sm.err, err);
@@ -618,9 +618,13 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
 }
 
 template <class G, bool kConn8, int kMode = 0, bool kCount = false>
-__global__ void __launch_bounds__(G::kThreads, 1024 / G::kThreads)
+// (1024 threads per SM, 64 registers; 4-connectivity on 32x8 lane tiles is
+// held to 5 CTAs by its shared memory anyway and gets the registers instead)
+__global__ void __launch_bounds__(G::kThreads,
+                                  (G::kLH == 8 && Variant<kConn8, kMode, G::kLH>::kCap == 128 ? 640 : 1024) /
+                                      G::kThreads)
     k_block_local(JobTable jt, Scratch s, int cap) {
-    using Sm = LocalSmem<G, Variant<kConn8, kMode>::kCap>;
+    using Sm = LocalSmem<G, Variant<kConn8, kMode, G::kLH>::kCap>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm &sm = *reinterpret_cast<Sm *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 0, iter, sm.item); ++iter) {
@@ -785,7 +789,7 @@ template <class G>
 struct WriteSmem {
     int slot_label[G::kSlots];
     int runlab[G::BLY][G::kBW];          // label of every piece at its start column, one band of all lane tiles
-    uint32_t mask[kLH][G::kThreads];     // row masks of the block
+    uint32_t mask[G::kLH][G::kThreads];     // row masks of the block
     ItemSlot item;
 };
 
@@ -798,7 +802,7 @@ __device__ __forceinline__ int runlab_index(int tx, int c) { return kLW * tx + (
 template <class G, bool kConn8, bool kRow>
 __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
                                               WriteSmem<G> &sm, int cap, uint32_t bound) {
-    using Bd = Bands<kConn8>;
+    using Bd = Bands<kConn8, G::kLH>;
     constexpr int R = Bd::kRows;
     constexpr int NB = Bd::kN;
     constexpr int T = G::kThreads;
@@ -823,10 +827,10 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     }
     report(err);
 
-    const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * T + t) * kLH);
-    uint32_t mrow[kLH];
+    const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + ((size_t)b * T + t) * G::kLH);
+    uint32_t mrow[G::kLH];
 #pragma unroll
-    for (int q = 0; q < kLH / 4; ++q) {
+    for (int q = 0; q < G::kLH / 4; ++q) {
         const uint4 m4 = mi[q];
         mrow[4 * q] = m4.x;
         mrow[4 * q + 1] = m4.y;
@@ -834,9 +838,9 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
         mrow[4 * q + 3] = m4.w;
     }
 #pragma unroll
-    for (int r = 0; r < kLH; ++r) sm.mask[r][t] = mrow[r];
+    for (int r = 0; r < G::kLH; ++r) sm.mask[r][t] = mrow[r];
     // per-piece values, 8 per chunk; the next chunk is always already in flight
-    const uint4 *vin = s.vstream + (size_t)b * kVChunksMax * T + t;
+    const uint4 *vin = s.vstream + (size_t)b * G::kVChunks * T + t;
     int npieces = 0;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
@@ -892,7 +896,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
             }
 #pragma unroll
             for (int rr = 0; rr < R; ++rr) {
-                const int y = y0 + kLH * ry + k * R + rr;
+                const int y = y0 + G::kLH * ry + k * R + rr;
                 if (y >= H) break;
                 const uint32_t m = rr == 0 ? ma : mbm;
                 int v[4];
@@ -943,8 +947,8 @@ template <class G>
 Layout layout_for(size_t nb) {
     Layout l;
     size_t off = 0;
-    l.masks = off;   off += up256(nb * G::kThreads * kLH * sizeof(uint32_t));
-    l.vstream = off; off += up256(nb * kVChunksMax * G::kThreads * sizeof(uint4));
+    l.masks = off;   off += up256(nb * G::kThreads * G::kLH * sizeof(uint32_t));
+    l.vstream = off; off += up256(nb * G::kVChunks * G::kThreads * sizeof(uint4));
     l.edges = off;   off += up256(nb * G::kEdge * sizeof(uint16_t));
     l.P = off;       off += up256(nb * G::kSlots * sizeof(uint64_t));
     l.nslots = off;  off += up256(nb * sizeof(int32_t));
@@ -970,9 +974,13 @@ size_t blocks_of(int H, int W) {
     return (((size_t)W + G::kBW - 1) / G::kBW) * (((size_t)H + G::kBH - 1) / G::kBH);
 }
 
-using G0 = Geo<16, 16>;
-using G1 = Geo<8, 16>;
-using G2 = Geo<32, 8>;
+// 512x64, 256x64 and 1024x32 blocks of 32x4 lane tiles, and 512x64 blocks
+// of 32x8 lane tiles (fewer, longer per-thread chains: better once an image
+// fills every SM many times over)
+using G0 = Geo<16, 16, 4>;
+using G1 = Geo<8, 16, 4>;
+using G2 = Geo<32, 8, 4>;
+using G3 = Geo<16, 8, 8>;
 
 }  // namespace
 
@@ -1092,7 +1100,7 @@ struct GeoLaunch {
 
 template <class G, bool kConn8>
 bool geo_launch_conn(int dev, GeoLaunch &g) {
-    const int bytes = (int)sizeof(LocalSmem<G, Variant<kConn8, 0>::kCap>);
+    const int bytes = (int)sizeof(LocalSmem<G, Variant<kConn8, 0, G::kLH>::kCap>);
     if (cudaFuncSetAttribute(k_block_local<G, kConn8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
         cudaSuccess)
         return false;
@@ -1132,7 +1140,7 @@ bool geo_launch(GeoLaunch &out) {
 template <class G>
 void caps_for(size_t nb, int cap, int &local_cap, int &global_cap, uint32_t &bound) {
     const long long slots = (long long)nb * G::kSlots;
-    local_cap = cap > 0 ? cap : kPieceCapMax * G::kThreads + 16;
+    local_cap = cap > 0 ? cap : G::kPieceCap * G::kThreads + 16;
     global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
     bound = (uint32_t)slots;
 }
@@ -1143,14 +1151,14 @@ int launch_table(int conn, const JobTable &jt, unsigned grid_local, unsigned gri
                  const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream) {
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<true, 0>::kCap>), stream>>>(
+        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<true, 0, G::kLH>::kCap>), stream>>>(
             jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<G, true><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
         ev = timing_mark(stream, ev, kKindMerge);
         k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     } else {
-        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<false, 0>::kCap>), stream>>>(
+        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<false, 0, G::kLH>::kCap>), stream>>>(
             jt, s, local_cap);
         ev = timing_mark(stream, ev, kKindLocal);
         k_block_merge<G, false><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
@@ -1212,7 +1220,7 @@ template <bool kConn8, int kMode>
 int launch_variant_t(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
                      cudaStream_t stream, int cap) {
     using G = G0;
-    using V = Variant<kConn8, kMode>;
+    using V = Variant<kConn8, kMode, G::kLH>;
     const int bytes = (int)sizeof(LocalSmem<G, V::kCap>);
     if (cudaFuncSetAttribute(k_block_local<G, kConn8, kMode, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              bytes) != cudaSuccess)
@@ -1253,7 +1261,7 @@ int launch_variant_c(int mode, const uint8_t *img, int H, int W, size_t pitch, i
 }  // namespace
 
 const char *geo_name(int geo) {
-    static const char *names[kNumGeo] = {"512x64", "256x64", "1024x32"};
+    static const char *names[kNumGeo] = {"512x64", "256x64", "1024x32", "512x64x8"};
     return (geo >= 0 && geo < kNumGeo) ? names[geo] : "";
 }
 
@@ -1261,6 +1269,7 @@ void geo_block_shape(int geo, int *bw, int *bh) {
     switch (geo) {
         case 1: *bw = G1::kBW; *bh = G1::kBH; break;
         case 2: *bw = G2::kBW; *bh = G2::kBH; break;
+        case 3: *bw = G3::kBW; *bh = G3::kBH; break;
         default: *bw = G0::kBW; *bh = G0::kBH; break;
     }
 }
@@ -1269,6 +1278,7 @@ size_t geo_blocks(int geo, int H, int W) {
     switch (geo) {
         case 1: return blocks_of<G1>(H, W);
         case 2: return blocks_of<G2>(H, W);
+        case 3: return blocks_of<G3>(H, W);
         default: return blocks_of<G0>(H, W);
     }
 }
@@ -1277,14 +1287,28 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
     switch (geo) {
         case 1: return layout_for<G1>(blocks).total;
         case 2: return layout_for<G2>(blocks).total;
+        case 3: return layout_for<G3>(blocks).total;
         default: return layout_for<G0>(blocks).total;
     }
 }
 
-size_t workspace_bytes(int H, int W) { return geo_workspace_bytes(0, geo_blocks(0, H, W)); }
+// A single image runs on 512x64 blocks: 32x4 lane tiles while the image has
+// fewer blocks than fill the GPU several times over (short per-thread chains
+// keep more warps busy per SM), 32x8 lane tiles from 1024 blocks on (about
+// 5800x5800 pixels; fewer seams once every SM is full).
+constexpr size_t kTallFromBlocks = 1024;
+static_assert(G0::kBW == G3::kBW && G0::kBH == G3::kBH, "both single-image shapes cover the same blocks");
+
+size_t workspace_bytes(int H, int W) {
+    const size_t nb = blocks_of<G0>(H, W);
+    const size_t a = layout_for<G0>(nb).total, b = layout_for<G3>(nb).total;
+    return a > b ? a : b;
+}
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap) {
+    if (blocks_of<G3>(H, W) >= kTallFromBlocks)
+        return launch_single<G3>(img, H, W, pitch, conn, labels, ws, stream, cap);
     return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
 }
 
@@ -1293,6 +1317,7 @@ int prepare_geo(int geo) {
     switch (geo) {
         case 1: return geo_launch<G1>(gl) ? 0 : -1;
         case 2: return geo_launch<G2>(gl) ? 0 : -1;
+        case 3: return geo_launch<G3>(gl) ? 0 : -1;
         default: return geo_launch<G0>(gl) ? 0 : -1;
     }
 }
@@ -1302,6 +1327,7 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
     switch (geo) {
         case 1: return launch_batch<G1>(conn, hdr, jobs, ws, capacity, stream, cap);
         case 2: return launch_batch<G2>(conn, hdr, jobs, ws, capacity, stream, cap);
+        case 3: return launch_batch<G3>(conn, hdr, jobs, ws, capacity, stream, cap);
         default: return launch_batch<G0>(conn, hdr, jobs, ws, capacity, stream, cap);
     }
 }

@@ -64,12 +64,12 @@ def test_batched_argument_checks_without_gpu():
     assert lib.ccl_label_batched(arr, 1, 6, None) == ccl.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_batched(None, 0, 8, None) == ccl.CCL_OK
     assert lib.ccl_label_batched_tile(arr, 1, 8, 99, None) == ccl.CCL_ERR_INVALID_ARG
-    assert ccl.ccl_tile_names() == ["512x64", "256x64", "1024x32"]
+    assert ccl.ccl_tile_names() == ["512x64", "256x64", "1024x32", "512x64x8"]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("conn", (4, 8))
-@pytest.mark.parametrize("tile", (0, 1, 2))
+@pytest.mark.parametrize("tile", (0, 1, 2, 3))
 def test_uneven_batch_every_tile(conn, tile):
     imgs = uneven_batch(24, seed=tile * 10 + conn)
     imgs += [np.zeros((0, 7), np.uint8), np.ones((1, 1), np.uint8), synth.spiral(301),

@@ -122,6 +122,14 @@ def test_stress_closed_forms_8192():
     assert lab.max() == 1
 
 
+@pytest.mark.parametrize("conn", CONNS)
+def test_large_image_ragged(conn):
+    """An image of at least 1024 blocks (single images of that size run on
+    lane tiles of 8 rows), with ragged tails in both directions."""
+    for p, seed in ((0.5, 1), (0.3, 2)):
+        assert_parity(synth.bernoulli(4100, 8200, p, seed), conn, f"large ragged p={p}")
+
+
 def test_pitch_alignment_and_nonzero_bytes():
     torch = _torch()
     g = np.random.default_rng(7)
