@@ -157,7 +157,9 @@ ccl_status ccl_autotune_batched(const ccl_image *images, int n, int connectivity
 /* Block shape ccl_label_batched() would use for this batch; -1 if untuned. */
 ccl_status ccl_batched_tile(const ccl_image *images, int n, int connectivity, int *tile);
 
-/* Number of block shapes, and the name of one ("512x64": width x height). */
+/* Number of block shapes, and the name of one ("512x64": width x height, on
+ * lane tiles of 32 x 4 pixels; "512x64x8": the same block on 32 x 8 lane
+ * tiles). */
 int ccl_tile_count(void);
 const char *ccl_tile_name(int tile);
 
