@@ -1294,8 +1294,11 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
 
 // A single image runs on 512x64 blocks: 32x4 lane tiles while the image has
 // fewer blocks than fill the GPU several times over (short per-thread chains
-// keep more warps busy per SM), 32x8 lane tiles from 1024 blocks on (about
-// 5800x5800 pixels; fewer seams once every SM is full).
+// keep more warps busy per SM); under 8-connectivity 32x8 lane tiles from
+// 1024 blocks on (about 5800x5800 pixels; fewer seams and instructions once
+// every SM is full).  Under 4-connectivity 32x8 lane tiles hold only 5 CTAs
+// of 128 threads per SM (shared memory), and 32x4 stays faster at every size
+// measured (up to 8192x8192).
 constexpr size_t kTallFromBlocks = 1024;
 static_assert(G0::kBW == G3::kBW && G0::kBH == G3::kBH, "both single-image shapes cover the same blocks");
 
@@ -1307,7 +1310,7 @@ size_t workspace_bytes(int H, int W) {
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap) {
-    if (blocks_of<G3>(H, W) >= kTallFromBlocks)
+    if (conn == 8 && blocks_of<G3>(H, W) >= kTallFromBlocks)
         return launch_single<G3>(img, H, W, pitch, conn, labels, ws, stream, cap);
     return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
 }

@@ -124,8 +124,8 @@ def test_stress_closed_forms_8192():
 
 @pytest.mark.parametrize("conn", CONNS)
 def test_large_image_ragged(conn):
-    """An image of at least 1024 blocks (single images of that size run on
-    lane tiles of 8 rows), with ragged tails in both directions."""
+    """An image of at least 1024 blocks (single 8-connected images of that
+    size run on lane tiles of 8 rows), with ragged tails in both directions."""
     for p, seed in ((0.5, 1), (0.3, 2)):
         assert_parity(synth.bernoulli(4100, 8200, p, seed), conn, f"large ragged p={p}")
 
