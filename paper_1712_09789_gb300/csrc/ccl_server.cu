@@ -125,6 +125,10 @@ struct ccl_server {
     int on_device = 0;
     bool stop = false;
     std::thread sched;
+    // block shape per connectivity (index 0: 4, 1: 8), fixed at the first
+    // batch so that each stream keeps one graph runner whose capacity the
+    // first full batches settle; -1 until then (scheduler thread only)
+    int tile[2] = {-1, -1};
 
     // statistics
     Clock::time_point t_create, t_first_submit, t_last_done;
@@ -214,8 +218,9 @@ ccl_status launch(ccl_server *s, Batch *b) {
             return CCL_ERR_CUDA;
         imgs.push_back(ccl_image{dimg, dlab, r->H, r->W, r->dpitch});
     }
-    int tile = 0;
-    if (ccl_batched_tile(imgs.data(), (int)imgs.size(), b->reqs.front()->conn, &tile) != CCL_OK || tile < 0)
+    int &tile = s->tile[b->reqs.front()->conn == 8 ? 1 : 0];
+    if (tile < 0 &&
+        (ccl_batched_tile(imgs.data(), (int)imgs.size(), b->reqs.front()->conn, &tile) != CCL_OK || tile < 0))
         tile = 0;
     ccl_status status =
         ccl_label_batched_tile(imgs.data(), (int)imgs.size(), b->reqs.front()->conn, tile, st);
