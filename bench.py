@@ -1,33 +1,38 @@
 #!/usr/bin/env python3
 """Benchmark of the block-based CCL hot path on GB300.
 
-Default workload (one "step"): the 4096x4096 single-image set -- i.i.d.
-Bernoulli foreground at densities 0.1..0.9 and granular noise (g = 4, 16) at
-0.5, seeds 0..2 (33 images) -- each labelled with 4- and 8-connectivity
-through ``ccl_label`` (66 labelings, 1.107 Gpixel per step).  Inputs are
-resident in HBM when the timed region starts; 33 distinct inputs and 66
-distinct outputs (4.98 GB) cycle through every step, so nothing of one step
-is still in the 129 MB L2 when the same image comes back.
+Headline workload (one "step"): the 8192x8192 Bernoulli(p=0.5, seed 0) image
+labelled with 8-connectivity through ``ccl_label`` 32 times.  Four device
+copies of the image and four label buffers are cycled, so consecutive
+labelings touch different memory; one labeling reads 67 MB and writes
+268 MB, more than the 129 MB L2, so nothing of a labeling is still in L2 when
+its buffers come back.  Inputs are resident in HBM when the timed region
+starts.
 
 The JSON line carries, besides the contract keys:
   roofline      the dominant kernel's algorithmic bytes per launch divided by
-                its mean CUDA-event duration over the timed region, against
+                its mean CUDA-event duration, taken in a second pass of the
+                same steps with per-kernel events on the launching stream
+                (the headline pass records no per-kernel events), against
                 the measured HBM copy bandwidth;
-  cpu_baseline  the CPU oracle timed on a bounded sample of the same work;
-  e2e           the same metric through ``ccl_label_host`` (host buffers,
-                copies inside the timed region);
+  kernels       that pass's per-kernel launches, mean times and shares;
+  cpu_baseline  the CPU oracle timed on a bounded sample of the same image
+                (CPU model and core count recorded);
+  e2e           the same metric through ``ccl_label_host_async`` from pinned
+                host buffers on three streams (copies inside the timed region);
   clocks        SM clocks and throttle reasons sampled during the timed region;
-  extra         the 8192x8192 Bernoulli(0.5) 8-connectivity image (L2 flushed
-                between repetitions) with its per-kernel breakdown; single
-                512^2 and 4096^2 images, L2 flushed and warm (min, median,
-                mean, stdev); the 256-image uneven batch (batched graph vs
-                plain launches, and the CPU oracle over the batch on every
-                host core); the serving stream at 2k/5k/10k requests/s
-                (p50/p99, Gpixel/s); the coarse-labelling variants of
-                Sec. 4.2 (time, counters); component statistics of the
-                8192^2 labels; 512^3 volumes (6/26-connectivity).
+  extra         the 4096x4096 noise set (density sweep and granular noise,
+                both connectivities); single 512^2 and 4096^2 images, L2
+                flushed and warm (min, median, mean, stdev); the 256-image
+                uneven batch (batched graph vs plain launches, and the CPU
+                oracle over the batch on every host core); the serving stream
+                at 2k/5k/10k requests/s (p50/p99 and stage percentiles,
+                Gpixel/s); the coarse-labelling variants of Sec. 4.2 (time,
+                counters); component statistics of the 8192^2 labels; 512^3
+                volumes (6/26-connectivity).
 
-``--impl reference`` times the CPU oracle instead (the reference arm).
+``--impl reference`` times the CPU oracle instead (the reference arm), on
+the same 8192x8192 image.
 """
 from __future__ import annotations
 
@@ -54,8 +59,14 @@ KERNEL_BYTES_PER_PIXEL = {   # the path's algorithmic bytes each kernel moves, p
     "k_block_merge": 0,      # block border records only
     "k_block_write": 4,      # writes every label once
 }
-SIDE = 4096
+SIDE = 4096                  # the 4096x4096 noise set (an extra)
 CONNS = (4, 8)
+HEAD_N = 8192                # the headline image: 8192x8192 Bernoulli(0.5), seed 0
+HEAD_CONN = 8
+HEAD_COPIES = 4              # device copies of the image / label buffers cycled
+HEAD_PER_STEP = 32           # labelings per step
+HEAD_WORKLOAD = ("8192x8192 uint8 Bernoulli(p=0.5, seed 0) image, 8-connectivity, plain ccl_label path, "
+                 "32 labelings per step")
 
 
 def load_peaks():
@@ -91,7 +102,7 @@ def recorded_traffic(kernel: str):
         return None
     text = open(path).read()
     m_sha = re.search(r"^csrc_digest:\s*([0-9a-f]+)", text, re.M)
-    m_b = re.search(r"^dram_bytes_per_launch_4096:\s*([0-9.eE+]+)", text, re.M)
+    m_b = re.search(r"^dram_bytes_per_launch_8192:\s*([0-9.eE+]+)", text, re.M)
     if not m_sha or not m_b or m_sha.group(1) != csrc_digest():
         return None
     return float(m_b.group(1))
@@ -182,50 +193,63 @@ def noise_4096_images():
     return list(synth.noise_4096_set(SIDE))
 
 
+def host_cpu():
+    """CPU model and online core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    import platform
+
+    return {"cpu_model": model or platform.processor() or platform.machine(), "nproc": os.cpu_count()}
+
+
 # ---------------------------------------------------------------------------
 def run_reference(args):
-    """The reference arm: the CPU oracle on the host, one bounded sample of the
-    step's work per step."""
+    """The reference arm: the CPU oracle on the host, on the headline image;
+    each step is one labeling of the 8192x8192 image (a bounded sample of the
+    headline step's 32)."""
     rank, world, _ = dist_setup()
     if rank != 0:
         return 0
-    import numpy as np
-
     import oracle
     from paper_1712_09789_gb300 import synth
 
     oracle.build()
-    imgs = [img for _, img in synth.noise_4096_set(SIDE, seeds=(0,))]
-    # calibrate: seconds per row of a 4096-wide image
+    img = synth.bernoulli(HEAD_N, HEAD_N, 0.5, 0)
+    for _ in range(args.warmup):
+        oracle.label(img, HEAD_CONN)
     t0 = time.perf_counter()
-    oracle.label(np.ascontiguousarray(imgs[4][:256]), 8)
-    per_row = (time.perf_counter() - t0) / 256
-    budget = 90.0
-    rows = int(max(8, min(SIDE, budget / max(1, args.steps + args.warmup) / per_row)))
-    work = [(img, c) for c in CONNS for img in imgs]
-
-    def step(i):
-        img, conn = work[i % len(work)]
-        oracle.label(np.ascontiguousarray(img[:rows]), conn)
-
-    for i in range(args.warmup):
-        step(i)
-    t0 = time.perf_counter()
-    for i in range(args.steps):
-        step(args.warmup + i)
+    for _ in range(args.steps):
+        oracle.label(img, HEAD_CONN)
     dt = time.perf_counter() - t0
-    px = rows * SIDE * args.steps
+    px = HEAD_N * HEAD_N * args.steps
     value = px / dt / 1e9
-    sample = (f"{rows}-row x 4096 strips of the 4096x4096 noise set (seed 0), cycling densities, "
-              f"granularities and both connectivities, one strip per step")
+    sample = (f"one labeling of the 8192x8192 Bernoulli(0.5) image per step, 8-connectivity, "
+              f"single thread; the GPU arm's step labels it 32 times")
+    cpu = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "4096x4096 uint8 noise set (configs: density sweep + granular), "
-                               "CPU oracle two-pass union-find", "rows_per_step": rows},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": {"workload": HEAD_WORKLOAD + " (CPU oracle: one labeling per step)",
+                   "H": HEAD_N, "W": HEAD_N, "connectivity": HEAD_CONN},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, **cpu},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -234,11 +258,10 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------
 def run_ours(args):
-    import numpy as np
     import torch
 
     from paper_1712_09789_gb300 import build as lib_build
-    from paper_1712_09789_gb300 import ccl
+    from paper_1712_09789_gb300 import ccl, synth
 
     rank, world, local = dist_setup()
     torch.cuda.set_device(local)
@@ -259,16 +282,15 @@ def run_ours(args):
     def max_over_ranks(v: float) -> float:
         return max_over_ranks_tensor(torch, v, world, "cuda")
 
-    named = noise_4096_images()
-    host = [img for _, img in named]
-    dev = [torch.from_numpy(img).cuda() for img in host]
-    work = [(i, c) for c in CONNS for i in range(len(dev))]
-    outs = [torch.empty((SIDE, SIDE), dtype=torch.int32, device="cuda") for _ in work]
-    px_step = len(work) * SIDE * SIDE
+    img_np = synth.bernoulli(HEAD_N, HEAD_N, 0.5, 0)
+    dev = [torch.from_numpy(img_np).cuda() for _ in range(HEAD_COPIES)]
+    outs = [torch.empty((HEAD_N, HEAD_N), dtype=torch.int32, device="cuda") for _ in range(HEAD_COPIES)]
+    px_step = HEAD_PER_STEP * HEAD_N * HEAD_N
 
     def step():
-        for k, (i, c) in enumerate(work):
-            ccl.ccl_label(dev[i], c, labels=outs[k])
+        for k in range(HEAD_PER_STEP):
+            j = k % HEAD_COPIES
+            ccl.ccl_label(dev[j], HEAD_CONN, labels=outs[j])
 
     for _ in range(args.warmup):
         step()
@@ -276,11 +298,10 @@ def run_ours(args):
     if status != ccl.CCL_OK:
         raise RuntimeError(f"device status after warm-up: {ccl.ccl_status_string(status)}")
 
-    # -- timed region: device time with CUDA events, per-kernel events on the
-    # launching stream (the current stream, which ccl_label uses)
+    # -- timed region: device time with CUDA events on the launching stream
+    # (the current stream, which ccl_label uses); no per-kernel events here
     cvd = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
     sampler = ClockSampler(cvd[local].strip() if local < len(cvd) else str(local))
-    ccl.ccl_debug_kernel_timing(True)
     sampler.start()
     barrier()
     torch.cuda.synchronize()
@@ -292,90 +313,90 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ktimes = ccl.ccl_debug_kernel_times()
-    ccl.ccl_debug_kernel_timing(False)
     status = ccl.ccl_get_device_status()
     if status != ccl.CCL_OK:
         raise RuntimeError(f"device status after timed region: {ccl.ccl_status_string(status)}")
     ms = max_over_ranks(e0.elapsed_time(e1))
     value = weak_scaling_value(world, px_step, args.steps, ms)
 
+    # -- per-kernel pass: the same steps again, with CUDA events recorded on
+    # the launching stream around every kernel
+    ccl.ccl_debug_kernel_timing(True)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    ktimes = ccl.ccl_debug_kernel_times()
+    ccl.ccl_debug_kernel_timing(False)
+
     hbm_gbs, peak_kind, _ = load_peaks()
     total_kernel_ms = sum(v[0] for v in ktimes.values()) or 1.0
     dominant = max(ktimes, key=lambda k: ktimes[k][0])
     dom_ms, dom_n = ktimes[dominant]
     dom_avg_s = dom_ms / max(1, dom_n) / 1e3
-    algo_bytes = KERNEL_BYTES_PER_PIXEL[dominant] * SIDE * SIDE
+    algo_bytes = KERNEL_BYTES_PER_PIXEL[dominant] * HEAD_N * HEAD_N
     achieved = algo_bytes / dom_avg_s / 1e9
     traffic = recorded_traffic(dominant)
     roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": hbm_gbs,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm_gbs,
                 "traffic": traffic, "algorithmic_bytes_per_launch": algo_bytes,
-                "mean_launch_us": dom_avg_s * 1e6}
-    kernels = {k: {"launches": n, "mean_us": (t / n * 1e3) if n else None,
-                   "share": t / total_kernel_ms} for k, (t, n) in ktimes.items()}
+                "mean_launch_us": dom_avg_s * 1e6,
+                "timing": "mean CUDA-event duration per launch, from a second pass of the same steps"}
+    kernels = {}
+    for k, (t, n) in ktimes.items():
+        mean_us = (t / n * 1e3) if n else None
+        kb = KERNEL_BYTES_PER_PIXEL.get(k, 0) * HEAD_N * HEAD_N
+        kernels[k] = {"launches": n, "mean_us": mean_us, "share": t / total_kernel_ms,
+                      "algorithmic_gbs": (kb / (mean_us * 1e3)) if (mean_us and kb) else None}
     path_frac = value * 1e9 / world * BYTES_PER_PIXEL / (hbm_gbs * 1e9)
+    us_per_image = ms * 1e3 / (args.steps * HEAD_PER_STEP)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {
-            "workload": "4096x4096 uint8 noise set: Bernoulli p=0.1..0.9 and granular g=4,16 at p=0.5, "
-                        "seeds 0..2 (33 images), each with 4- and 8-connectivity (66 labelings/step), "
-                        "plain ccl_label path",
-            "images": len(dev), "H": SIDE, "W": SIDE, "connectivity": list(CONNS),
-            "pixels_per_step": px_step,
-            "l2": "inputs larger than L2: 33 inputs (554 MB) and 66 outputs (4.4 GB) cycle every step",
+            "workload": HEAD_WORKLOAD, "H": HEAD_N, "W": HEAD_N, "connectivity": HEAD_CONN,
+            "labelings_per_step": HEAD_PER_STEP, "pixels_per_step": px_step,
+            "l2": "inputs larger than L2: each labeling reads 67 MB and writes 268 MB; 4 input copies "
+                  "and 4 label buffers cycle",
         },
+        "us_per_image": us_per_image,
         "hbm_roofline_frac_path": path_frac,
         "roofline": roofline,
         "kernels": kernels,
-        "gpu_launches": int(sum(n for _, n in ktimes.values())),
+        "gpu_launches": 3 * HEAD_PER_STEP * args.steps,
         "clocks": clocks,
     }
 
     # -- e2e through host buffers (copies inside the timed region)
     if not args.no_e2e:
-        line["e2e"] = bench_e2e(torch, ccl, host, work, args, world, max_over_ranks)
+        line["e2e"] = bench_e2e(torch, ccl, img_np, args, world, max_over_ranks)
 
-    # -- extra: the 8192x8192 Bernoulli(0.5) 8-connectivity image
     if rank == 0 and not args.no_extra:
-        line["extra"] = bench_8192(torch, ccl, hbm_gbs)
-
-    # -- extra: single 512x512 and 4096x4096 images, L2 flushed and warm
-    if rank == 0 and not args.no_extra:
-        line["extra"]["single_512"] = bench_single(torch, ccl, 512, hbm_gbs)
-        line["extra"]["single_4096"] = bench_single(torch, ccl, 4096, hbm_gbs)
-
-    # -- extra: the uneven 256-image batch, batched graph vs plain launches
-    if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
-
-    # -- extra: the serving stream (Poisson arrivals of mixed-resolution host
-    # frames through the continuous-batching server); it runs before the
-    # large statistics and volume workloads, which leave the host and device
-    # memory in a different state
-    if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["serving"] = bench_serving(torch, ccl, args.serving_seconds)
-
-    # -- extra: the coarse-labelling variants of Sec. 4.2 (time and counters)
-    if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["variants"] = bench_variants(torch, ccl)
-
-    # -- extra: component statistics of the 8192^2 labels
-    if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["component_stats"] = bench_stats(torch, ccl)
-
-    # -- extra: 3D volumes (512^3 noise, 6- and 26-connectivity)
-    if rank == 0 and not args.no_extra:
-        line.setdefault("extra", {})["volume_512"] = bench_volume(torch, ccl, hbm_gbs)
+        extra = line.setdefault("extra", {})
+        # the 4096x4096 noise set, both connectivities
+        extra["noise_4096"] = bench_noise_4096(torch, ccl, hbm_gbs)
+        # single 512x512 and 4096x4096 images, L2 flushed and warm
+        extra["single_512"] = bench_single(torch, ccl, 512, hbm_gbs)
+        extra["single_4096"] = bench_single(torch, ccl, 4096, hbm_gbs)
+        # the uneven 256-image batch, batched graph vs plain launches
+        extra["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
+        # the serving stream (Poisson arrivals of mixed-resolution host frames
+        # through the continuous-batching server); it runs before the large
+        # statistics and volume workloads, which leave the host and device
+        # memory in a different state
+        extra["serving"] = bench_serving(torch, ccl, args.serving_seconds)
+        # the coarse-labelling variants of Sec. 4.2 (time and counters)
+        extra["variants"] = bench_variants(torch, ccl)
+        # component statistics of the 8192^2 labels
+        extra["component_stats"] = bench_stats(torch, ccl)
+        # 3D volumes (512^3 noise, 6- and 26-connectivity)
+        extra["volume_512"] = bench_volume(torch, ccl, hbm_gbs)
 
     # -- the CPU oracle over the whole uneven batch on every host core (after
     # the GPU extras: its worker processes load the host)
     if rank == 0 and world == 1 and not args.no_extra and not args.no_cpu:
-        from paper_1712_09789_gb300 import synth
-
         try:
             cores = oracle_all_cores(synth.batch_uneven(256, seed=0), 8)
         except Exception as exc:  # the CPU baseline must not cost the GPU numbers
@@ -384,7 +405,7 @@ def run_ours(args):
 
     # -- CPU oracle on a bounded sample, rank 0 at N = 1 only
     if rank == 0 and world == 1 and not args.no_cpu:
-        line["cpu_baseline"] = bench_cpu(host, work, outs)
+        line["cpu_baseline"] = bench_cpu(img_np, outs[(HEAD_PER_STEP - 1) % HEAD_COPIES])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -443,35 +464,50 @@ def bench_single(torch, ccl, N, hbm_gbs, reps=100, warm=10):
     return res
 
 
-def bench_8192(torch, ccl, hbm_gbs):
-    from paper_1712_09789_gb300 import synth
+def bench_noise_4096(torch, ccl, hbm_gbs, reps=5):
+    """The 4096x4096 noise set: Bernoulli p = 0.1..0.9 and granular noise
+    (g = 4, 16) at p = 0.5, seeds 0..2 (33 images), each labelled with 4- and
+    8-connectivity (66 labelings, 1.107 Gpixel per pass).  33 inputs and 66
+    outputs (4.98 GB) cycle, so nothing of a pass is in L2 when the same
+    image comes back.  `reps` timed passes after two warm-up passes, then one
+    more pass with per-kernel events for the shares."""
+    named = noise_4096_images()
+    dev = [torch.from_numpy(img).cuda() for _, img in named]
+    work = [(i, c) for c in CONNS for i in range(len(dev))]
+    outs = [torch.empty((SIDE, SIDE), dtype=torch.int32, device="cuda") for _ in work]
 
-    N = 8192
-    img = torch.from_numpy(synth.bernoulli(N, N, 0.5, 0)).cuda()
-    out = torch.empty((N, N), dtype=torch.int32, device="cuda")
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    for _ in range(3):
-        ccl.ccl_label(img, 8, labels=out)
-    reps = 30
-    times = []
-    ccl.ccl_debug_kernel_timing(True)
+    def one_pass():
+        for k, (i, c) in enumerate(work):
+            ccl.ccl_label(dev[i], c, labels=outs[k])
+
+    for _ in range(2):
+        one_pass()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
     for _ in range(reps):
-        flush.fill_(1)  # evict the previous repetition's data from L2
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        ccl.ccl_label(img, 8, labels=out)
-        b.record()
-        b.synchronize()
-        times.append(a.elapsed_time(b))
+        one_pass()
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    ccl.ccl_debug_kernel_timing(True)
+    one_pass()
+    torch.cuda.synchronize()
     kt = ccl.ccl_debug_kernel_times()
     ccl.ccl_debug_kernel_timing(False)
-    med = statistics.median(times)
-    gpx = N * N / (med / 1e3) / 1e9
-    return {"workload": "8192x8192 Bernoulli p=0.5 seed 0, 8-connectivity, L2 flushed between reps",
-            "median_us": med * 1e3, "min_us": min(times) * 1e3, "mean_us": statistics.mean(times) * 1e3,
-            "stdev_us": statistics.pstdev(times) * 1e3,
-            "gpixel_s": gpx, "hbm_roofline_frac": gpx * 1e9 * BYTES_PER_PIXEL / (hbm_gbs * 1e9),
-            "kernels_mean_us": {k: (t / n * 1e3 if n else None) for k, (t, n) in kt.items()}}
+    if ccl.ccl_get_device_status() != ccl.CCL_OK:
+        raise RuntimeError("4096x4096 noise set reported a device error")
+    px = len(work) * SIDE * SIDE
+    gpx = px / (ms / 1e3) / 1e9
+    tot = sum(t for t, _ in kt.values()) or 1.0
+    res = {"workload": "4096x4096 noise set: Bernoulli p=0.1..0.9 and granular g=4,16 at p=0.5, seeds 0..2, "
+                       "4- and 8-connectivity (66 labelings per pass)",
+           "ms_per_pass": ms, "gpixel_s": gpx,
+           "hbm_roofline_frac": gpx * 1e9 * BYTES_PER_PIXEL / (hbm_gbs * 1e9),
+           "kernels": {k: {"mean_us": (t / n * 1e3 if n else None), "share": t / tot} for k, (t, n) in kt.items()}}
+    del dev, outs
+    torch.cuda.empty_cache()
+    return res
 
 
 def _oracle_batch_task(task):
@@ -754,63 +790,82 @@ def bench_serving(torch, ccl, seconds, rates=(2000, 5000, 10000), warm=0.5):
                 "offered_gpixel_s": rate * mean_px / 1e9, "requests": int(st["completed"]),
                 "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
                 "delivered_gpixel_s": st["gpixel_s"], "rejected": int(st["rejected"]),
-                "late_submissions": late}
+                "late_submissions": late,
+                "stages_ms": {k: [st[f"{k}_p50_ms"], st[f"{k}_p99_ms"]] for k in ("queue", "h2d", "label", "d2h")},
+                "batches": int(st["batches"]), "multi_request_batches": int(st["multi_request_batches"]),
+                "overlapped_batches": int(st["overlapped_batches"]),
+                "max_batch_requests": int(st["max_batch_requests"]),
+                "max_batches_in_flight": int(st["max_batches_in_flight"])}
     return res
 
 
-def bench_e2e(torch, ccl, host, work, args, world, max_over_ranks):
-    import numpy as np
-
-    pinned = [torch.from_numpy(h).pin_memory() for h in host]
-    pin_np = [p.numpy() for p in pinned]
-    out = torch.empty((SIDE, SIDE), dtype=torch.int32).pin_memory().numpy()
+def bench_e2e(torch, ccl, img_np, args, world, max_over_ranks, n_streams=3):
+    """The headline step end to end through ``ccl_label_host_async``: every
+    labeling copies its image from pinned host memory to the device, labels
+    it and copies the labels back to pinned host memory, on three streams in
+    turn so that one image's copies overlap another's labelling.  The timed
+    region ends when every stream has finished (host clock)."""
+    pin_in = [torch.from_numpy(img_np).pin_memory().numpy() for _ in range(HEAD_COPIES)]
+    pin_out = [torch.empty((HEAD_N, HEAD_N), dtype=torch.int32).pin_memory().numpy() for _ in range(n_streams)]
+    streams = [torch.cuda.Stream() for _ in range(n_streams)]
     steps = max(1, min(3, args.steps))
 
     def step():
-        for i, c in work:
-            ccl.ccl_label_host(pin_np[i], c, labels=out)
+        for k in range(HEAD_PER_STEP):
+            si = k % n_streams
+            ccl.ccl_label_host_async(pin_in[k % HEAD_COPIES], pin_out[si], HEAD_CONN, stream=streams[si])
 
-    step()  # warm-up: grows the library's staging buffers
+    step()  # warm-up: grows the library's staging buffers of each stream
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
         step()
+    for st in streams:
+        st.synchronize()
     dt = max_over_ranks(time.perf_counter() - t0)
-    px = len(work) * SIDE * SIDE
+    status = ccl.ccl_get_device_status()
+    for st in streams:
+        ccl.ccl_release_stream(st)
+    if status != ccl.CCL_OK:
+        raise RuntimeError(f"e2e: device status {ccl.ccl_status_string(status)}")
+    px = HEAD_PER_STEP * HEAD_N * HEAD_N
+    h2d = HEAD_PER_STEP * HEAD_N * HEAD_N
+    d2h = HEAD_PER_STEP * HEAD_N * HEAD_N * 4
     return {"value": world * px * steps / dt / 1e9, "unit": UNIT,
-            "h2d_bytes_per_step": len(work) * SIDE * SIDE,
-            "d2h_bytes_per_step": len(work) * SIDE * SIDE * 4,
-            "steps": steps, "api": "ccl_label_host (pinned host buffers, synchronous per image)"}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": steps,
+            "host_link_gbs": (h2d + d2h) * steps / dt / 1e9,
+            "api": f"ccl_label_host_async on {n_streams} streams (pinned host buffers, copies in both "
+                   f"directions inside the timed region)"}
 
 
-def bench_cpu(host, work, outs):
+def bench_cpu(img_np, gpu_labels, budget=12.0):
+    """The CPU oracle, single thread, on the headline image: repeated until
+    `budget` seconds of labelling; its first result is compared with the
+    GPU's labels of the same image."""
     import numpy as np
 
     import oracle
 
     oracle.build()
-    budget = 15.0
-    done, px, checked = 0, 0, 0
-    t_total = 0.0
-    for k, (i, c) in enumerate(work):
+    n, t_total, want = 0, 0.0, None
+    while t_total < budget or n == 0:
         t0 = time.perf_counter()
-        want = oracle.label(host[i], c)
+        r = oracle.label(img_np, HEAD_CONN)
         t_total += time.perf_counter() - t0
-        px += host[i].size
-        done += 1
-        if np.array_equal(outs[k].cpu().numpy(), want):
-            checked += 1
-        if t_total >= budget:
-            break
-    return {"value": px / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of the step's 66 labelings (4096x4096 each), single thread",
-            "parity_bit_exact": f"{checked}/{done}"}
+        if want is None:
+            want = r
+        n += 1
+    same = bool(np.array_equal(gpu_labels.cpu().numpy(), want))
+    return {"value": n * img_np.size / t_total / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} labelings of the 8192x8192 Bernoulli(0.5) image, 8-connectivity, single thread "
+                      f"({t_total:.1f} s)",
+            **host_cpu(), "parity_bit_exact": same}
 
 
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extra", action="store_true")

@@ -113,6 +113,20 @@ ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch,
                           int connectivity, int32_t *host_labels, void *stream);
 
 /*
+ * ccl_label_host() without the wait: the copy in, the labelling and the copy
+ * out are only enqueued on `stream`, and the labels are in `host_labels`
+ * once the stream has reached that point (cudaStreamSynchronize, an event,
+ * or ccl_get_device_status()).  Both host buffers must stay valid and
+ * untouched until then; they must be page-locked for the copies to run
+ * asynchronously.  Each (device, stream) has its own staging buffers, so
+ * images enqueued on several streams overlap their copies with one another's
+ * labelling.  Errors as ccl_label() (argument errors synchronously, nothing
+ * enqueued); device errors surface through ccl_get_device_status().
+ */
+ccl_status ccl_label_host_async(const uint8_t *host_img, int H, int W, size_t pitch,
+                                int connectivity, int32_t *host_labels, void *stream);
+
+/*
  * One image of a batch (device pointers; same rules as ccl_label()).
  */
 typedef struct {
@@ -171,12 +185,16 @@ const char *ccl_tile_name(int tile);
  * A scheduler thread keeps submitted requests in arrival order and starts a
  * batch on an idle CUDA stream with as many requests from the front of the
  * queue as fit: at most max_batch per batch, at most max_slots on the device
- * at once, device buffers carved from a resident arena of hbm_budget_bytes
- * (the admission is by free arena memory) and one connectivity per batch.
- * Requests that arrive while others run are admitted as slots and memory free
- * up.  A batch is: frame copies in, one batched labelling (ccl_label_batched
- * with the tuned or default block shape), label copies out.  Batches on
- * different streams overlap on the device.
+ * at once, one connectivity per batch, and device memory carved from a
+ * resident arena of hbm_budget_bytes -- each frame's image and labels plus
+ * the batch's job table and labelling scratch (admission is by free arena
+ * memory; the server uses no other device memory).  Requests that arrive
+ * while others run are admitted as slots and memory free up.  A batch is:
+ * frame copies in, the three labelling kernels over all blocks of all its
+ * frames (persistent CTAs taking blocks from a device work counter), and
+ * label copies out in increasing frame size; each request completes as soon
+ * as its own labels are in host memory.  Batches on different streams
+ * overlap on the device.
  */
 typedef struct {
     int max_slots;            /* requests on the device at once, >= 1 */
@@ -193,6 +211,21 @@ typedef struct {
     size_t arena_bytes, arena_used_bytes;
     double p50_ms, p99_ms, max_ms, mean_ms;  /* submit -> labels in host memory */
     double gpixel_s;                    /* pixels / (last completion - first submit) */
+    /* Stages, per request (each request of a batch counts its batch's
+     * device stages once): queue = submit -> admitted into a batch (host
+     * clock); h2d, label, d2h = the batch's frame copies in, its labelling
+     * kernels and its label copies out (CUDA events on its stream). */
+    double queue_p50_ms, queue_p99_ms;
+    double h2d_p50_ms, h2d_p99_ms;
+    double label_p50_ms, label_p99_ms;
+    double d2h_p50_ms, d2h_p99_ms;
+    uint64_t batches;                   /* batches retired */
+    uint64_t multi_request_batches;     /* of those, batches of more than one request */
+    uint64_t overlapped_batches;        /* batches whose device span (copy-in start to
+                                           copy-out end) overlapped that of another
+                                           batch retired before it */
+    int max_batch_requests;             /* largest batch */
+    int max_batches_in_flight;          /* most batches on the device at once */
 } ccl_server_stats_t;
 
 typedef struct ccl_server ccl_server;
@@ -201,11 +234,20 @@ typedef struct ccl_server ccl_server;
 ccl_status ccl_server_create(const ccl_server_config *config, ccl_server **server);
 
 /*
+ * Arena bytes one H x W frame needs when it is served alone (image, labels,
+ * labelling scratch and job table).  A server refuses a frame larger than its
+ * whole arena by this measure; size hbm_budget_bytes as a multiple of it for
+ * the frames that should be on the device at once.
+ */
+ccl_status ccl_server_frame_bytes(int H, int W, size_t *bytes);
+
+/*
  * Queues one frame: host_img u8 [H][pitch], host_labels int32 [H][W], both
  * owned by the caller and untouched by it until the request completes
  * (page-locked memory gives asynchronous copies).  Writes a ticket.
  * CCL_ERR_INVALID_ARG as ccl_label() (and for an empty frame),
- * CCL_ERR_UNSUPPORTED for a frame larger than the whole arena.
+ * CCL_ERR_UNSUPPORTED for a frame whose ccl_server_frame_bytes() exceeds the
+ * whole arena.
  */
 ccl_status ccl_server_submit(ccl_server *server, const uint8_t *host_img, int H, int W, size_t pitch,
                              int connectivity, int32_t *host_labels, uint64_t *ticket);
@@ -243,8 +285,8 @@ void ccl_server_destroy(ccl_server *server);
  * scratch is a fixed array of ccl_noalloc_max_workspace_bytes() bytes
  * (64 MiB) that every GPU loading the library reserves until the process
  * exits; this call allocates nothing.  Images whose ccl_workspace_size()
- * exceeds that limit (for example more than 4096 x 8192 pixels) are rejected
- * with CCL_ERR_UNSUPPORTED and nothing is enqueued.  The first call on a device
+ * exceeds that limit (about 1.34 bytes per pixel, so about 50 million
+ * pixels) are rejected with CCL_ERR_UNSUPPORTED and nothing is enqueued.  The first call on a device
  * looks up the array's device address, so make that first call before any
  * stream capture.  All calls share the array: calls whose work overlaps on the
  * GPU (other streams, other host threads) race on it and must be serialised by
@@ -255,6 +297,17 @@ ccl_status ccl_label_noalloc(const uint8_t *img, int H, int W, size_t pitch, int
 
 /* Size in bytes of the fixed scratch array used by ccl_label_noalloc(). */
 size_t ccl_noalloc_max_workspace_bytes(void);
+
+/*
+ * Frees what the library holds for `stream` on the current device: the
+ * scratch and staging buffers of ccl_label(), ccl_label_host(),
+ * ccl_label_host_async(), ccl_label_variant(), ccl_component_stats() and
+ * ccl_label_3d(), and the graphs, scratch and staging of ccl_label_batched().
+ * Waits for the stream first.  Call it before destroying a stream that was
+ * given to those entry points; a later call on the stream allocates afresh.
+ * The library has no other per-stream state.
+ */
+ccl_status ccl_release_stream(void *stream);
 
 /*
  * Waits for `stream`, then reports and clears the current device's error

@@ -60,7 +60,14 @@ class CclServerStats(ctypes.Structure):
                 ("in_flight", ctypes.c_int), ("queued", ctypes.c_int), ("pixels", ctypes.c_uint64),
                 ("arena_bytes", ctypes.c_size_t), ("arena_used_bytes", ctypes.c_size_t),
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double),
-                ("mean_ms", ctypes.c_double), ("gpixel_s", ctypes.c_double)]
+                ("mean_ms", ctypes.c_double), ("gpixel_s", ctypes.c_double),
+                ("queue_p50_ms", ctypes.c_double), ("queue_p99_ms", ctypes.c_double),
+                ("h2d_p50_ms", ctypes.c_double), ("h2d_p99_ms", ctypes.c_double),
+                ("label_p50_ms", ctypes.c_double), ("label_p99_ms", ctypes.c_double),
+                ("d2h_p50_ms", ctypes.c_double), ("d2h_p99_ms", ctypes.c_double),
+                ("batches", ctypes.c_uint64), ("multi_request_batches", ctypes.c_uint64),
+                ("overlapped_batches", ctypes.c_uint64), ("max_batch_requests", ctypes.c_int),
+                ("max_batches_in_flight", ctypes.c_int)]
 
 
 _SIGS = {
@@ -73,7 +80,10 @@ _SIGS = {
                                 _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "ccl_label_host": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
                                   _c.c_void_p, _c.c_void_p]),
+    "ccl_label_host_async": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
+                                        _c.c_void_p, _c.c_void_p]),
     "ccl_get_device_status": (_c.c_int, [_c.c_void_p]),
+    "ccl_release_stream": (_c.c_int, [_c.c_void_p]),
     "ccl_label_noalloc": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_void_p,
                                      _c.c_void_p]),
     "ccl_noalloc_max_workspace_bytes": (_c.c_size_t, []),
@@ -90,6 +100,7 @@ _SIGS = {
     "ccl_batched_tile": (_c.c_int, [_c.POINTER(CclImage), _c.c_int, _c.c_int, _c.POINTER(_c.c_int)]),
     "ccl_tile_count": (_c.c_int, []),
     "ccl_server_create": (_c.c_int, [_c.POINTER(CclServerConfig), _c.POINTER(_c.c_void_p)]),
+    "ccl_server_frame_bytes": (_c.c_int, [_c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
     "ccl_server_submit": (_c.c_int, [_c.c_void_p, _c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int,
                                      _c.c_void_p, _c.POINTER(_c.c_uint64)]),
     "ccl_server_wait": (_c.c_int, [_c.c_void_p, _c.c_uint64, _c.c_int]),
@@ -128,6 +139,21 @@ def load() -> ctypes.CDLL:
 def _check(st: int, where: str):
     if st != CCL_OK:
         raise CclError(st, where)
+
+
+def _device_guard(device):
+    """Context that makes `device` the current CUDA device.  The library takes
+    its per-device scratch (and the no-allocation array's address) from the
+    current device, so every call runs with the tensors' device current."""
+    import torch
+
+    return torch.cuda.device(device)
+
+
+def _call(name: str, device, *args):
+    """Calls C-ABI function `name` with `device` current (see _device_guard)."""
+    with _device_guard(device):
+        return getattr(load(), name)(*args)
 
 
 def ccl_status_string(status: int) -> str:
@@ -177,7 +203,7 @@ def ccl_label(img, connectivity: int = 8, labels=None, stream=None):
     """Canonical labels of a device image (``ccl_label``).  Returns ``labels``."""
     H, W, pitch = _image_args(img)
     labels = _labels_for(img, labels)
-    st = load().ccl_label(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+    st = _call("ccl_label", img.device, img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                           _stream_ptr(stream, img.device))
     _check(st, "ccl_label")
     return labels
@@ -190,7 +216,7 @@ def ccl_label_noalloc(img, connectivity: int = 8, labels=None, stream=None):
     such callers; overlapping calls race on the shared scratch."""
     H, W, pitch = _image_args(img)
     labels = _labels_for(img, labels)
-    st = load().ccl_label_noalloc(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+    st = _call("ccl_label_noalloc", img.device, img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                                   _stream_ptr(stream, img.device))
     _check(st, "ccl_label_noalloc")
     return labels
@@ -222,7 +248,7 @@ def ccl_label_3d(vol, connectivity: int = 26, labels=None, stream=None):
     elif (labels.dtype != torch.int32 or tuple(labels.shape) != (D, H, W) or not labels.is_contiguous()
           or labels.device != vol.device):
         raise ValueError("labels must be a contiguous int32 tensor of the volume's shape and device")
-    st = load().ccl_label_3d(vol.data_ptr(), D, H, W, pitch, connectivity, labels.data_ptr(),
+    st = _call("ccl_label_3d", vol.device, vol.data_ptr(), D, H, W, pitch, connectivity, labels.data_ptr(),
                              _stream_ptr(stream, vol.device))
     _check(st, "ccl_label_3d")
     return labels
@@ -240,7 +266,7 @@ def ccl_label_variant(img, connectivity: int = 8, variant: int = 0, labels=None,
     H, W, pitch = _image_args(img)
     labels = _labels_for(img, labels)
     cnt = (ctypes.c_ulonglong * 3)()
-    st = load().ccl_label_variant(img.data_ptr(), H, W, pitch, connectivity, variant, labels.data_ptr(),
+    st = _call("ccl_label_variant", img.device, img.data_ptr(), H, W, pitch, connectivity, variant, labels.data_ptr(),
                                   cnt if counters else None, _stream_ptr(stream, img.device))
     _check(st, "ccl_label_variant")
     if counters:
@@ -264,14 +290,15 @@ def ccl_component_stats(labels, stream=None, capacity=None):
     if labels.dtype != torch.int32 or labels.dim() != 2 or not labels.is_cuda or not labels.is_contiguous():
         raise ValueError("labels must be a contiguous 2D int32 CUDA tensor")
     H, W = labels.shape
-    lib = load()
     sp = _stream_ptr(stream, labels.device)
     n = ctypes.c_int(0)
     if capacity is None:
-        _check(lib.ccl_component_stats(labels.data_ptr(), H, W, None, 0, ctypes.byref(n), sp), "ccl_component_stats")
+        _check(_call("ccl_component_stats", labels.device, labels.data_ptr(), H, W, None, 0, ctypes.byref(n), sp),
+               "ccl_component_stats")
         capacity = n.value
     buf = torch.empty(max(1, capacity) * 40, dtype=torch.uint8, device=labels.device)
-    _check(lib.ccl_component_stats(labels.data_ptr(), H, W, buf.data_ptr(), capacity, ctypes.byref(n), sp),
+    _check(_call("ccl_component_stats", labels.device, labels.data_ptr(), H, W, buf.data_ptr(), capacity,
+                 ctypes.byref(n), sp),
            "ccl_component_stats")
     k = min(n.value, capacity)
     return np.frombuffer(buf[: k * 40].cpu().numpy().tobytes(), dtype=np.dtype(COMPONENT_DTYPE))
@@ -292,7 +319,7 @@ def ccl_label_ws(img, workspace, connectivity: int = 8, labels=None, stream=None
     H, W, pitch = _image_args(img)
     labels = _labels_for(img, labels)
     nbytes = workspace.numel() * workspace.element_size()
-    st = load().ccl_label_ws(img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
+    st = _call("ccl_label_ws", img.device, img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                              workspace.data_ptr(), nbytes, _stream_ptr(stream, img.device))
     _check(st, "ccl_label_ws")
     return labels
@@ -314,18 +341,49 @@ def ccl_label_host(img: np.ndarray, connectivity: int = 8, labels: np.ndarray | 
         raise ValueError("labels must be a contiguous int32 array of the image's shape")
     import torch
 
-    st = load().ccl_label_host(img.ctypes.data, H, W, pitch, connectivity, labels.ctypes.data,
-                               _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device())))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = _call("ccl_label_host", dev, img.ctypes.data, H, W, pitch, connectivity, labels.ctypes.data,
+               _stream_ptr(stream, dev))
     _check(st, "ccl_label_host")
     return labels
+
+
+def ccl_label_host_async(img: np.ndarray, labels: np.ndarray, connectivity: int = 8, stream=None) -> None:
+    """Enqueues copy in, labelling and copy out of a host image on ``stream``
+    (``ccl_label_host_async``); ``labels`` holds the result once the stream
+    has reached that point.  Both arrays should be page-locked (e.g. numpy
+    views of pinned torch tensors) and must stay alive until then."""
+    if not isinstance(img, np.ndarray) or img.dtype != np.uint8 or img.ndim != 2:
+        raise ValueError("image must be a 2D numpy uint8 array")
+    H, W = img.shape
+    if W > 0 and H > 1 and img.strides[1] != 1:
+        raise ValueError("image rows must be contiguous")
+    if labels.dtype != np.int32 or labels.shape != (H, W) or not labels.flags.c_contiguous:
+        raise ValueError("labels must be a contiguous int32 array of the image's shape")
+    pitch = img.strides[0] if H > 1 else W
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = _call("ccl_label_host_async", dev, img.ctypes.data, H, W, pitch, connectivity, labels.ctypes.data,
+               _stream_ptr(stream, dev))
+    _check(st, "ccl_label_host_async")
 
 
 def ccl_get_device_status(stream=None) -> int:
     """Waits for the stream and returns (and clears) the device status code."""
     import torch
 
-    return load().ccl_get_device_status(
-        _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device())))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    return _call("ccl_get_device_status", dev, _stream_ptr(stream, dev))
+
+
+def ccl_release_stream(stream=None) -> None:
+    """Frees the library's scratch, staging and batched graphs held for
+    ``stream`` (``ccl_release_stream``); call before the stream goes away."""
+    import torch
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    _check(_call("ccl_release_stream", dev, _stream_ptr(stream, dev)), "ccl_release_stream")
 
 
 def ccl_debug_set_iteration_cap(cap: int) -> None:
@@ -366,9 +424,9 @@ def ccl_label_batched(pairs, connectivity: int = 8, stream=None, tile: int | Non
     arr = _batch_array(pairs)
     sp = _stream_ptr(stream, dev)
     if tile is None:
-        st = load().ccl_label_batched(arr, len(pairs), connectivity, sp)
+        st = _call("ccl_label_batched", dev, arr, len(pairs), connectivity, sp)
     else:
-        st = load().ccl_label_batched_tile(arr, len(pairs), connectivity, tile, sp)
+        st = _call("ccl_label_batched_tile", dev, arr, len(pairs), connectivity, tile, sp)
     _check(st, "ccl_label_batched")
     return [lab for _, lab in pairs]
 
@@ -377,21 +435,30 @@ def ccl_autotune_batched(pairs, connectivity: int = 8, stream=None) -> int:
     """Time every block shape on the batch, remember and return the fastest."""
     arr = _batch_array(pairs)
     out = ctypes.c_int(-1)
-    _check(load().ccl_autotune_batched(arr, len(pairs), connectivity, _stream_ptr(stream, pairs[0][0].device),
-                                       ctypes.byref(out)), "ccl_autotune_batched")
+    dev = pairs[0][0].device
+    _check(_call("ccl_autotune_batched", dev, arr, len(pairs), connectivity, _stream_ptr(stream, dev),
+                 ctypes.byref(out)), "ccl_autotune_batched")
     return out.value
 
 
 def ccl_batched_tile(pairs, connectivity: int = 8) -> int:
     arr = _batch_array(pairs)
     out = ctypes.c_int(-1)
-    _check(load().ccl_batched_tile(arr, len(pairs), connectivity, ctypes.byref(out)), "ccl_batched_tile")
+    _check(_call("ccl_batched_tile", pairs[0][0].device, arr, len(pairs), connectivity, ctypes.byref(out)),
+           "ccl_batched_tile")
     return out.value
 
 
 def ccl_tile_names() -> list:
     lib = load()
     return [lib.ccl_tile_name(i).decode() for i in range(lib.ccl_tile_count())]
+
+
+def ccl_server_frame_bytes(H: int, W: int) -> int:
+    """Arena bytes one H x W frame needs when served alone (``ccl_server_frame_bytes``)."""
+    out = ctypes.c_size_t(0)
+    _check(load().ccl_server_frame_bytes(H, W, ctypes.byref(out)), "ccl_server_frame_bytes")
+    return out.value
 
 
 class CclServer:

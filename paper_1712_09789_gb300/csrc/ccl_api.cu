@@ -71,6 +71,44 @@ int current_cap() {
     return g_cap;
 }
 
+
+// Copies a host image into the library's staging buffers of (device,
+// stream), labels it and copies the labels back to host memory, all enqueued
+// on `stream`.  Consecutive calls on one stream reuse the same staging
+// buffers in stream order; calls on different streams have their own.
+ccl_status enqueue_host(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,
+                        int32_t *host_labels, void *stream) {
+    ccl_status st = check_image_args(host_img, H, W, pitch, connectivity, host_labels);
+    if (st != CCL_OK || H == 0 || W == 0) return st;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t dpitch = ((size_t)W + 15) & ~(size_t)15;
+    const size_t img_bytes = dpitch * (size_t)H;
+    const size_t lab_bytes = (size_t)H * (size_t)W * sizeof(int32_t);
+    const size_t need = ccl::workspace_bytes(H, W);
+    // held until everything is enqueued (see ccl_label)
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevBuf &b = g_scratch[{dev, s}];
+    DevBuf &bi = g_host_img[{dev, s}];
+    DevBuf &bl = g_host_lab[{dev, s}];
+    if (b.bytes < need || bi.bytes < img_bytes || bl.bytes < lab_bytes) {
+        if (cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+        if ((st = grow(b, need)) != CCL_OK) return st;
+        if ((st = grow(bi, img_bytes)) != CCL_OK) return st;
+        if ((st = grow(bl, lab_bytes)) != CCL_OK) return st;
+    }
+    if (cudaMemcpy2DAsync(bi.ptr, dpitch, host_img, pitch, (size_t)W, (size_t)H, cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return CCL_ERR_CUDA;
+    if (ccl::launch_label(static_cast<const uint8_t *>(bi.ptr), H, W, dpitch, connectivity,
+                          static_cast<int32_t *>(bl.ptr), b.ptr, s, g_cap) != 0)
+        return CCL_ERR_CUDA;
+    if (cudaMemcpyAsync(host_labels, bl.ptr, lab_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CCL_ERR_CUDA;
+    return CCL_OK;
+}
+
 }  // namespace
 
 namespace ccl {
@@ -134,21 +172,19 @@ ccl_status ccl_label(const uint8_t *img, int H, int W, size_t pitch, int connect
     if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t need = ccl::workspace_bytes(H, W);
-    void *ws = nullptr;
-    int cap = 0;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        DevBuf &b = g_scratch[{dev, s}];
-        if (b.bytes < need) {
-            // the old buffer may still be in use by earlier work on this stream
-            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-            st = grow(b, need);
-            if (st != CCL_OK) return st;
-        }
-        ws = b.ptr;
-        cap = g_cap;
+    // The lock is held until the launches are enqueued: another host thread
+    // on the same stream that needs a larger buffer would otherwise free this
+    // one after its stream wait but before this call's kernels are on the
+    // stream.
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevBuf &b = g_scratch[{dev, s}];
+    if (b.bytes < need) {
+        // the old buffer may still be in use by earlier work on this stream
+        if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+        st = grow(b, need);
+        if (st != CCL_OK) return st;
     }
-    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, ws, s, cap) != 0) return CCL_ERR_CUDA;
+    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, b.ptr, s, g_cap) != 0) return CCL_ERR_CUDA;
     return CCL_OK;
 }
 
@@ -166,20 +202,15 @@ ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int
         if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
         cudaStream_t s = static_cast<cudaStream_t>(stream);
         const size_t need = ccl::variant_workspace_bytes(H, W);
-        void *ws = nullptr;
-        int cap = 0;
-        {
-            std::lock_guard<std::mutex> lk(g_mu);
-            DevBuf &b = g_scratch[{dev, s}];
-            if (b.bytes < need) {
-                if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-                st = grow(b, need);
-                if (st != CCL_OK) return st;
-            }
-            ws = b.ptr;
-            cap = g_cap;
+        // held until the launches are enqueued (see ccl_label)
+        std::lock_guard<std::mutex> lk(g_mu);
+        DevBuf &b = g_scratch[{dev, s}];
+        if (b.bytes < need) {
+            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+            st = grow(b, need);
+            if (st != CCL_OK) return st;
         }
-        if (ccl::launch_label_variant(img, H, W, pitch, connectivity, variant, labels, ws, s, cap) != 0)
+        if (ccl::launch_label_variant(img, H, W, pitch, connectivity, variant, labels, b.ptr, s, g_cap) != 0)
             return CCL_ERR_CUDA;
     }
     if (counters) {
@@ -201,8 +232,10 @@ ccl_status ccl_component_stats(const int32_t *labels, int H, int W, ccl_componen
     if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t ws_bytes = (ccl::stats_workspace_bytes(H, W) + 255) & ~(size_t)255;
-    void *ws = nullptr;
+    uint32_t host[2] = {0, 0};
     {
+        // held until the call's work is done: the count is read back from
+        // the shared scratch (see ccl_label)
         std::lock_guard<std::mutex> lk(g_mu);
         DevBuf &b = g_stats[{dev, s}];
         if (b.bytes < ws_bytes + 256) {
@@ -210,59 +243,48 @@ ccl_status ccl_component_stats(const int32_t *labels, int H, int W, ccl_componen
             const ccl_status st = grow(b, ws_bytes + 256);
             if (st != CCL_OK) return st;
         }
-        ws = b.ptr;
+        void *ws = b.ptr;
+        // the last 256 bytes hold the component count and the count of bad pixels
+        uint32_t *tail = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + ws_bytes);
+        if (cudaMemsetAsync(tail, 0, 8, s) != cudaSuccess) return CCL_ERR_CUDA;
+        if (ccl::launch_stats(labels, H, W, out, capacity, ws, tail, reinterpret_cast<int *>(tail + 1), s) != 0)
+            return CCL_ERR_CUDA;
+        if (cudaMemcpyAsync(host, tail, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return CCL_ERR_CUDA;
     }
-    // the last 256 bytes hold the component count and the count of bad pixels
-    uint32_t *tail = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + ws_bytes);
-    if (cudaMemsetAsync(tail, 0, 8, s) != cudaSuccess) return CCL_ERR_CUDA;
-    if (ccl::launch_stats(labels, H, W, out, capacity, ws, tail, reinterpret_cast<int *>(tail + 1), s) != 0)
-        return CCL_ERR_CUDA;
-    uint32_t host[2] = {0, 0};
-    if (cudaMemcpyAsync(host, tail, sizeof(host), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return CCL_ERR_CUDA;
     *count = (int)host[0];
     return host[1] ? CCL_ERR_INVALID_ARG : CCL_OK;
 }
 
 ccl_status ccl_label_host(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,
                           int32_t *host_labels, void *stream) {
-    ccl_status st = check_image_args(host_img, H, W, pitch, connectivity, host_labels);
+    ccl_status st = enqueue_host(host_img, H, W, pitch, connectivity, host_labels, stream);
     if (st != CCL_OK || H == 0 || W == 0) return st;
+    return ccl_get_device_status(stream);
+}
+
+ccl_status ccl_label_host_async(const uint8_t *host_img, int H, int W, size_t pitch, int connectivity,
+                                int32_t *host_labels, void *stream) {
+    return enqueue_host(host_img, H, W, pitch, connectivity, host_labels, stream);
+}
+
+ccl_status ccl_release_stream(void *stream) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t dpitch = ((size_t)W + 15) & ~(size_t)15;
-    const size_t img_bytes = dpitch * (size_t)H;
-    const size_t lab_bytes = (size_t)H * (size_t)W * sizeof(int32_t);
-    const size_t need = ccl::workspace_bytes(H, W);
-    void *ws, *dimg, *dlab;
-    int cap;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        DevBuf &b = g_scratch[{dev, s}];
-        DevBuf &bi = g_host_img[{dev, s}];
-        DevBuf &bl = g_host_lab[{dev, s}];
-        if (b.bytes < need || bi.bytes < img_bytes || bl.bytes < lab_bytes) {
-            if (cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-            if ((st = grow(b, need)) != CCL_OK) return st;
-            if ((st = grow(bi, img_bytes)) != CCL_OK) return st;
-            if ((st = grow(bl, lab_bytes)) != CCL_OK) return st;
+        for (auto *m : {&g_scratch, &g_host_img, &g_host_lab, &g_stats, &g_volume}) {
+            auto it = m->find({dev, s});
+            if (it == m->end()) continue;
+            if (it->second.ptr) cudaFree(it->second.ptr);
+            m->erase(it);
         }
-        ws = b.ptr;
-        dimg = bi.ptr;
-        dlab = bl.ptr;
-        cap = g_cap;
     }
-    if (cudaMemcpy2DAsync(dimg, dpitch, host_img, pitch, (size_t)W, (size_t)H, cudaMemcpyHostToDevice, s) !=
-        cudaSuccess)
-        return CCL_ERR_CUDA;
-    if (ccl::launch_label(static_cast<const uint8_t *>(dimg), H, W, dpitch, connectivity,
-                          static_cast<int32_t *>(dlab), ws, s, cap) != 0)
-        return CCL_ERR_CUDA;
-    if (cudaMemcpyAsync(host_labels, dlab, lab_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return CCL_ERR_CUDA;
-    return ccl_get_device_status(stream);
+    ccl::release_batched_stream(dev, s);
+    return CCL_OK;
 }
 
 void ccl_debug_kernel_timing(int enable) { ccl::timing_enable(enable != 0); }
@@ -301,18 +323,15 @@ ccl_status ccl_label_3d(const uint8_t *img, int D, int H, int W, size_t pitch, i
     if (cudaGetDevice(&dev) != cudaSuccess) return CCL_ERR_CUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t need = ccl::volume_workspace_bytes(D, H, W);
-    void *ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        DevBuf &b = g_volume[{dev, s}];
-        if (b.bytes < need) {
-            if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-            const ccl_status st = grow(b, need);
-            if (st != CCL_OK) return st;
-        }
-        ws = b.ptr;
+    // held until the launches are enqueued (see ccl_label)
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevBuf &b = g_volume[{dev, s}];
+    if (b.bytes < need) {
+        if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
+        const ccl_status st = grow(b, need);
+        if (st != CCL_OK) return st;
     }
-    if (ccl::launch_volume(img, D, H, W, pitch, connectivity, labels, ws, s, current_cap()) != 0)
+    if (ccl::launch_volume(img, D, H, W, pitch, connectivity, labels, b.ptr, s, g_cap) != 0)
         return CCL_ERR_CUDA;
     return CCL_OK;
 }

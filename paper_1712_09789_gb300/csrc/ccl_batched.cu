@@ -194,6 +194,18 @@ ccl_status run_batch(const Prepared &pb, int conn, int geo, cudaStream_t stream)
     return CCL_OK;
 }
 
+void destroy_runner(Runner *R) {
+    drop_graphs(*R);
+    for (int i = 0; i < kRing; ++i) {
+        if (R->done[i]) cudaEventDestroy(R->done[i]);
+        if (R->h_table[i]) cudaFreeHost(R->h_table[i]);
+    }
+    if (R->d_table) cudaFree(R->d_table);
+    if (R->d_ws) cudaFree(R->d_ws);
+    if (R->capture) cudaStreamDestroy(R->capture);
+    delete R;
+}
+
 // --- autotune cache ----------------------------------------------------------
 
 std::mutex g_tmu;
@@ -320,6 +332,25 @@ int chosen_tile(const ccl_image *images, int n, int conn) {
 }
 
 }  // namespace
+
+namespace ccl {
+
+int release_batched_stream(int dev, cudaStream_t stream) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    int n = 0;
+    for (auto it = g_runners.begin(); it != g_runners.end();) {
+        if (std::get<0>(it->first) == dev && std::get<1>(it->first) == stream) {
+            destroy_runner(it->second);
+            it = g_runners.erase(it);
+            ++n;
+        } else {
+            ++it;
+        }
+    }
+    return n;
+}
+
+}  // namespace ccl
 
 extern "C" {
 

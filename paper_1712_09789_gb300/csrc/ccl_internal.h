@@ -92,6 +92,10 @@ size_t volume_workspace_bytes(int D, int H, int W);
 int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                   cudaStream_t stream, int cap);
 
+// Frees the batched runners (graphs, scratch, staging) of (dev, stream); the
+// caller has waited for the stream.  Returns how many were freed.
+int release_batched_stream(int dev, cudaStream_t stream);
+
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
 int read_and_clear_volume_error(int *value);

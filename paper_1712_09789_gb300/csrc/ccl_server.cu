@@ -3,22 +3,30 @@
 // Requests carry host frames.  A scheduler thread keeps them in arrival
 // order and forms a batch from the front of the queue whenever a CUDA stream
 // is idle: requests join while the batch is below max_batch, fewer than
-// max_slots requests are on the device, their device buffers fit in the
-// resident arena (the server's share of HBM, hbm_budget_bytes) and they have
-// the connectivity of the batch's first request.  A batch is enqueued on its
-// stream as: one host->device copy per frame, one batched labelling (graph
-// replay of the persistent kernels), one device->host copy per frame and a
-// host callback.  The callback hands the batch back to the scheduler, which
-// frees its arena ranges (admitting waiting requests) and wakes the waiters.
-// With several streams, copies of one batch overlap kernels of another.
+// max_slots requests are on the device, their device buffers and the batch's
+// scratch fit in the resident arena (the server's share of HBM,
+// hbm_budget_bytes) and they have the connectivity of the batch's first
+// request.  Every byte the server uses on the device comes from that arena:
+// frames, labels, the batch's job table and its labelling scratch.
 //
-// Latency of a request = time from ccl_server_submit() to the callback of
-// its batch (labels are in host memory by then).
+// A batch is enqueued on its stream as: one host->device copy per frame, the
+// job table copy, the three labelling kernels over all blocks of the batch
+// (persistent grids pulling blocks from a device work counter), then one
+// device->host copy per frame in increasing size, each followed by a host
+// callback that completes that request (a small frame does not wait for a
+// large frame's copy-out), and a final callback that hands the batch back to
+// the scheduler, which frees its arena ranges and the stream.  With several
+// streams, copies of one batch overlap kernels of another.
+//
+// Latency of a request = time from ccl_server_submit() to the callback after
+// its label copy (labels are in host memory by then).  Per batch, CUDA events
+// split the device side into copy-in, labelling and copy-out; the scheduler
+// reads them when it retires the batch.
 #include <algorithm>
-#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstdint>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -34,9 +42,11 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
-double seconds_since(Clock::time_point t0, Clock::time_point t) {
-    return std::chrono::duration<double>(t - t0).count();
+double ms_between(Clock::time_point a, Clock::time_point b) {
+    return 1e3 * std::chrono::duration<double>(b - a).count();
 }
+
+size_t up256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // First-fit allocator over one device arena; ranges are 256-byte aligned.
 class Arena {
@@ -48,7 +58,7 @@ class Arena {
         used_ = 0;
     }
     bool alloc(size_t bytes, size_t &off) {
-        bytes = (bytes + 255) & ~(size_t)255;
+        bytes = up256(bytes);
         for (auto it = free_.begin(); it != free_.end(); ++it) {
             if (it->second >= bytes) {
                 off = it->first;
@@ -63,7 +73,7 @@ class Arena {
         return false;
     }
     void release(size_t off, size_t bytes) {
-        bytes = (bytes + 255) & ~(size_t)255;
+        bytes = up256(bytes);
         used_ -= bytes;
         auto it = free_.emplace(off, bytes).first;
         auto nx = std::next(it);
@@ -87,6 +97,8 @@ class Arena {
     size_t size_ = 0, used_ = 0;
 };
 
+struct Batch;
+
 struct Request {
     uint64_t ticket = 0;
     const uint8_t *host_img = nullptr;
@@ -94,8 +106,9 @@ struct Request {
     int H = 0, W = 0, conn = 8;
     size_t pitch = 0, dpitch = 0;
     size_t img_off = 0, lab_off = 0;
-    Clock::time_point t_submit, t_done;
-    bool done = false;
+    Batch *batch = nullptr;
+    Clock::time_point t_submit, t_admit, t_done;
+    bool done = false;     // visible to waiters
     ccl_status status = CCL_OK;
 };
 
@@ -103,7 +116,38 @@ struct Batch {
     ccl_server *srv = nullptr;
     std::vector<Request *> reqs;
     int stream = 0;
+    int geo = 0;
+    size_t blocks = 0;
+    size_t ws_off = 0, ws_bytes = 0;   // labelling scratch
+    size_t tab_off = 0, tab_bytes = 0; // job table
+    bool failed = false;
+    // per-request copy-out callback arguments (index into reqs); `done` is
+    // set by the callback, under the server lock
+    struct CopyDone {
+        Batch *b;
+        int idx;
+        bool done;
+    };
+    std::vector<CopyDone> cds;
 };
+
+// Per-stream state: the stream, page-locked staging of the job table and the
+// events that split a batch into copy-in, labelling and copy-out.
+struct StreamCtx {
+    cudaStream_t s = nullptr;
+    bool busy = false;
+    unsigned char *h_table = nullptr;
+    size_t h_table_bytes = 0;
+    cudaEvent_t ev[4] = {};
+};
+
+// Percentile q of v (sorted copy).
+double pct(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const size_t i = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
+    return v[i];
+}
 
 }  // namespace
 
@@ -112,32 +156,83 @@ struct ccl_server {
     int device = 0;
     unsigned char *arena_base = nullptr;
     Arena arena;
-    std::vector<cudaStream_t> streams;
-    std::vector<bool> stream_busy;
+    std::vector<StreamCtx> streams;
 
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<Request *> pending;
     std::map<uint64_t, Request *> requests;
-    std::deque<Batch *> finished;
+    std::deque<Batch *> finished;     // batch callbacks that ran
     uint64_t next_ticket = 1;
-    uint64_t events = 0;  // bumped by every submission and finished batch
+    uint64_t events = 0;  // bumped by every submission and callback
     int on_device = 0;
+    int batches_on_device = 0;
     bool stop = false;
     std::thread sched;
     // block shape per connectivity (index 0: 4, 1: 8), fixed at the first
-    // batch so that each stream keeps one graph runner whose capacity the
-    // first full batches settle; -1 until then (scheduler thread only)
+    // batch of that connectivity (scheduler thread only); -1 until then
     int tile[2] = {-1, -1};
 
     // statistics
-    Clock::time_point t_create, t_first_submit, t_last_done;
+    Clock::time_point t_first_submit, t_last_done;
     bool any_submit = false;
-    uint64_t submitted = 0, completed = 0, rejected = 0, pixels = 0;
-    std::vector<double> latencies_ms;
+    uint64_t submitted = 0, completed = 0, rejected = 0, pixels = 0, batches = 0, multi_batches = 0;
+    uint64_t overlapped = 0;
+    int max_batch_seen = 0, max_batches_in_flight = 0;
+    std::vector<double> latencies_ms, queue_ms, h2d_ms, label_ms, d2h_ms;
+    // device spans [copy-in start, copy-out end] of recently retired batches,
+    // in ms after `t0_event` (recorded once at creation)
+    cudaEvent_t t0_event = nullptr;
+    std::deque<std::pair<float, float>> recent_spans;
 };
 
 namespace {
+
+size_t image_bytes(const Request &r) { return r.dpitch * (size_t)r.H; }
+size_t label_bytes(const Request &r) { return (size_t)r.H * (size_t)r.W * sizeof(int32_t); }
+size_t table_bytes(size_t jobs) { return sizeof(ccl::JobHeader) + jobs * sizeof(ccl::Job); }
+
+// Largest labelling scratch any block shape needs for an H x W frame.
+size_t frame_scratch_bytes(int H, int W) {
+    size_t m = 0;
+    for (int g = 0; g < ccl::kNumGeo; ++g)
+        m = std::max(m, ccl::geo_workspace_bytes(g, ccl::geo_blocks(g, H, W)));
+    return m;
+}
+
+// Arena bytes that one frame served alone needs: image, labels, scratch and
+// a one-entry job table, each rounded to the arena's 256-byte granule.
+size_t lone_frame_bytes(int H, int W) {
+    const size_t dpitch = ((size_t)W + 15) & ~(size_t)15;
+    return up256(dpitch * (size_t)H) + up256((size_t)H * (size_t)W * sizeof(int32_t)) +
+           up256(frame_scratch_bytes(H, W)) + up256(table_bytes(1));
+}
+
+// Completes one request once its labels are in host memory (CUDA's callback
+// thread; no CUDA calls here).
+void CUDART_CB on_copy_done(void *p) {
+    Batch::CopyDone *cd = static_cast<Batch::CopyDone *>(p);
+    Batch *b = cd->b;
+    ccl_server *s = b->srv;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        Request *r = b->reqs[cd->idx];
+        cd->done = true;
+        s->arena.release(r->img_off, image_bytes(*r));
+        s->arena.release(r->lab_off, label_bytes(*r));
+        const Clock::time_point now = Clock::now();
+        r->t_done = now;
+        r->done = true;
+        --s->on_device;
+        ++s->completed;
+        s->pixels += (uint64_t)r->H * (uint64_t)r->W;
+        s->latencies_ms.push_back(ms_between(r->t_submit, now));
+        s->t_last_done = now;
+        ++s->events;
+    }
+    s->cv_done.notify_all();
+    s->cv_sched.notify_one();
+}
 
 void CUDART_CB on_batch_done(void *p) {
     Batch *b = static_cast<Batch *>(p);
@@ -150,40 +245,77 @@ void CUDART_CB on_batch_done(void *p) {
     s->cv_sched.notify_one();
 }
 
-size_t image_bytes(const Request &r) { return r.dpitch * (size_t)r.H; }
-size_t label_bytes(const Request &r) { return (size_t)r.H * (size_t)r.W * sizeof(int32_t); }
-
-// Runs with s->mu held.  Hands finished batches back: frees their arena
-// ranges and marks their requests done.
+// Runs with s->mu held: retires finished batches -- stage times from their
+// events, the device-overlap record, their scratch and their stream.
 void reap_locked(ccl_server *s) {
-    const Clock::time_point now = Clock::now();
     while (!s->finished.empty()) {
         Batch *b = s->finished.front();
         s->finished.pop_front();
-        s->stream_busy[b->stream] = false;
-        for (Request *r : b->reqs) {
-            s->arena.release(r->img_off, image_bytes(*r));
-            s->arena.release(r->lab_off, label_bytes(*r));
-            r->done = true;
-            r->t_done = now;
-            --s->on_device;
-            ++s->completed;
-            s->pixels += (uint64_t)r->H * (uint64_t)r->W;
-            s->latencies_ms.push_back(1e3 * std::chrono::duration<double>(now - r->t_submit).count());
-            s->t_last_done = now;
+        StreamCtx &c = s->streams[b->stream];
+        float t01 = 0.f, t12 = 0.f, t23 = 0.f, a = 0.f, e = 0.f;
+        const bool ok = cudaEventElapsedTime(&t01, c.ev[0], c.ev[1]) == cudaSuccess &&
+                        cudaEventElapsedTime(&t12, c.ev[1], c.ev[2]) == cudaSuccess &&
+                        cudaEventElapsedTime(&t23, c.ev[2], c.ev[3]) == cudaSuccess &&
+                        cudaEventElapsedTime(&a, s->t0_event, c.ev[0]) == cudaSuccess &&
+                        cudaEventElapsedTime(&e, s->t0_event, c.ev[3]) == cudaSuccess;
+        if (ok) {
+            for (size_t k = 0; k < b->reqs.size(); ++k) {
+                s->h2d_ms.push_back(t01);
+                s->label_ms.push_back(t12);
+                s->d2h_ms.push_back(t23);
+            }
+            bool overlap = false;
+            for (const auto &sp : s->recent_spans)
+                if (sp.first < e && a < sp.second) overlap = true;
+            if (overlap) ++s->overlapped;
+            s->recent_spans.emplace_back(a, e);
+            if (s->recent_spans.size() > 64) s->recent_spans.pop_front();
+        } else {
+            cudaGetLastError();
         }
+        s->arena.release(b->ws_off, b->ws_bytes);
+        s->arena.release(b->tab_off, b->tab_bytes);
+        c.busy = false;
+        --s->batches_on_device;
         delete b;
     }
-    s->cv_done.notify_all();
+}
+
+// Gives the last request of batch b back to the front of the queue.
+void unadmit_last_locked(ccl_server *s, Batch *b) {
+    Request *r = b->reqs.back();
+    b->reqs.pop_back();
+    b->blocks -= ccl::geo_blocks(b->geo, r->H, r->W);
+    s->arena.release(r->img_off, image_bytes(*r));
+    s->arena.release(r->lab_off, label_bytes(*r));
+    r->batch = nullptr;
+    --s->on_device;
+    s->pending.push_front(r);
+}
+
+// Block shape for a connectivity, fixed at its first batch: the tuned one for
+// that frame size if the autotuner has one, else the 512x64 blocks.
+int tile_for(ccl_server *s, const Request &r) {
+    int &tile = s->tile[r.conn == 8 ? 1 : 0];
+    if (tile < 0) {
+        const ccl_image im{r.host_img, r.host_labels, r.H, r.W, r.pitch};
+        if (ccl_batched_tile(&im, 1, r.conn, &tile) != CCL_OK || tile < 0 || tile >= ccl::kNumGeo) tile = 0;
+    }
+    return tile;
 }
 
 // Runs with s->mu held: takes requests from the front of the queue for one
-// batch on `stream`; returns null when nothing can be admitted now.
+// batch on `stream`, with frames, scratch and job table carved from the
+// arena; returns null when nothing can be admitted now.
 Batch *admit_locked(ccl_server *s, int stream) {
+    if (s->pending.empty()) return nullptr;
+    const int conn = s->pending.front()->conn;
+    const int geo = tile_for(s, *s->pending.front());
     Batch *b = nullptr;
+    const Clock::time_point now = Clock::now();
     while (!s->pending.empty()) {
         Request *r = s->pending.front();
-        if (b && ((int)b->reqs.size() >= s->cfg.max_batch || r->conn != b->reqs.front()->conn)) break;
+        if (b && ((int)b->reqs.size() >= s->cfg.max_batch || r->conn != conn)) break;
         if (s->on_device >= s->cfg.max_slots) break;
         size_t io = 0, lo = 0;
         if (!s->arena.alloc(image_bytes(*r), io)) break;
@@ -199,39 +331,120 @@ Batch *admit_locked(ccl_server *s, int stream) {
             b = new Batch();
             b->srv = s;
             b->stream = stream;
+            b->geo = geo;
         }
+        r->batch = b;
+        r->t_admit = now;
         b->reqs.push_back(r);
+        b->blocks += ccl::geo_blocks(geo, r->H, r->W);
     }
+    if (!b) return nullptr;
+    // the batch's scratch and job table; drop requests from its end until
+    // they fit (a frame alone always fits an empty arena: submit checks it)
+    while (true) {
+        b->ws_bytes = ccl::geo_workspace_bytes(geo, b->blocks);
+        b->tab_bytes = table_bytes(b->reqs.size());
+        if (s->arena.alloc(b->ws_bytes, b->ws_off)) {
+            if (s->arena.alloc(b->tab_bytes, b->tab_off)) break;
+            s->arena.release(b->ws_off, b->ws_bytes);
+        }
+        unadmit_last_locked(s, b);
+        if (b->reqs.empty()) {
+            delete b;
+            return nullptr;
+        }
+    }
+    for (Request *r : b->reqs) s->queue_ms.push_back(ms_between(r->t_submit, r->t_admit));
+    b->cds.reserve(b->reqs.size());
+    for (int i = 0; i < (int)b->reqs.size(); ++i) b->cds.push_back({b, i, false});
     return b;
 }
 
-// Enqueues a batch (without the lock): copies in, labels, copies out, callback.
+// Enqueues a batch (without the lock): copies in, job table, the three
+// labelling kernels, copies out (smallest first) with a callback after each,
+// and the batch's final callback.
 ccl_status launch(ccl_server *s, Batch *b) {
-    cudaStream_t st = s->streams[b->stream];
-    std::vector<ccl_image> imgs;
-    imgs.reserve(b->reqs.size());
-    for (Request *r : b->reqs) {
-        uint8_t *dimg = s->arena_base + r->img_off;
-        int32_t *dlab = reinterpret_cast<int32_t *>(s->arena_base + r->lab_off);
+    StreamCtx &c = s->streams[b->stream];
+    cudaStream_t st = c.s;
+    unsigned char *base = s->arena_base;
+    if (cudaEventRecord(c.ev[0], st) != cudaSuccess) return CCL_ERR_CUDA;
+    ccl::JobHeader hdr{};
+    hdr.njobs = (unsigned)b->reqs.size();
+    hdr.total = (unsigned)b->blocks;
+    std::memcpy(c.h_table, &hdr, sizeof(hdr));
+    ccl::Job *jobs = reinterpret_cast<ccl::Job *>(c.h_table + sizeof(hdr));
+    int bw = 0, bh = 0;
+    ccl::geo_block_shape(b->geo, &bw, &bh);
+    unsigned block0 = 0;
+    for (size_t k = 0; k < b->reqs.size(); ++k) {
+        Request *r = b->reqs[k];
+        uint8_t *dimg = base + r->img_off;
+        int32_t *dlab = reinterpret_cast<int32_t *>(base + r->lab_off);
         if (cudaMemcpy2DAsync(dimg, r->dpitch, r->host_img, r->pitch, (size_t)r->W, (size_t)r->H,
                               cudaMemcpyHostToDevice, st) != cudaSuccess)
             return CCL_ERR_CUDA;
-        imgs.push_back(ccl_image{dimg, dlab, r->H, r->W, r->dpitch});
+        ccl::Job &j = jobs[k];
+        j.img = dimg;
+        j.labels = dlab;
+        j.pitch = r->dpitch;
+        j.H = r->H;
+        j.W = r->W;
+        j.nbx = (r->W + bw - 1) / bw;
+        j.nby = (r->H + bh - 1) / bh;
+        j.block0 = block0;
+        // arena ranges are 256-byte aligned and dpitch a multiple of 16
+        j.flags = ccl::kJobVecIn | ((r->W & 3) == 0 ? ccl::kJobVecOut : 0u);
+        block0 += (unsigned)j.nbx * (unsigned)j.nby;
     }
-    int &tile = s->tile[b->reqs.front()->conn == 8 ? 1 : 0];
-    if (tile < 0 &&
-        (ccl_batched_tile(imgs.data(), (int)imgs.size(), b->reqs.front()->conn, &tile) != CCL_OK || tile < 0))
-        tile = 0;
-    ccl_status status =
-        ccl_label_batched_tile(imgs.data(), (int)imgs.size(), b->reqs.front()->conn, tile, st);
-    if (status != CCL_OK) return status;
-    for (Request *r : b->reqs) {
-        if (cudaMemcpyAsync(r->host_labels, s->arena_base + r->lab_off, label_bytes(*r), cudaMemcpyDeviceToHost,
-                            st) != cudaSuccess)
+    if (cudaEventRecord(c.ev[1], st) != cudaSuccess) return CCL_ERR_CUDA;
+    unsigned char *dtab = base + b->tab_off;
+    if (cudaMemcpyAsync(dtab, c.h_table, b->tab_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return CCL_ERR_CUDA;
+    if (ccl::launch_jobs(b->geo, b->reqs.front()->conn, reinterpret_cast<ccl::JobHeader *>(dtab),
+                         reinterpret_cast<const ccl::Job *>(dtab + sizeof(ccl::JobHeader)), base + b->ws_off,
+                         b->blocks, st, ccl::iteration_cap_api()) != 0)
+        return CCL_ERR_CUDA;
+    if (cudaEventRecord(c.ev[2], st) != cudaSuccess) return CCL_ERR_CUDA;
+    std::vector<int> order(b->reqs.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return label_bytes(*b->reqs[x]) < label_bytes(*b->reqs[y]); });
+    for (int k : order) {
+        Request *r = b->reqs[k];
+        if (cudaMemcpyAsync(r->host_labels, base + r->lab_off, label_bytes(*r), cudaMemcpyDeviceToHost, st) !=
+                cudaSuccess ||
+            cudaLaunchHostFunc(st, on_copy_done, &b->cds[k]) != cudaSuccess)
             return CCL_ERR_CUDA;
     }
+    if (cudaEventRecord(c.ev[3], st) != cudaSuccess) return CCL_ERR_CUDA;
     if (cudaLaunchHostFunc(st, on_batch_done, b) != cudaSuccess) return CCL_ERR_CUDA;
     return CCL_OK;
+}
+
+// Runs with s->mu held (released around the stream wait): a batch whose
+// enqueue failed never reaches its final callback.  Waits for what was
+// enqueued, then fails every request whose labels were not copied out.
+void fail_batch_locked(ccl_server *s, Batch *b, ccl_status st, std::unique_lock<std::mutex> &lk) {
+    b->failed = true;
+    lk.unlock();
+    cudaStreamSynchronize(s->streams[b->stream].s);
+    cudaGetLastError();
+    lk.lock();
+    for (size_t k = 0; k < b->reqs.size(); ++k) {
+        if (b->cds[k].done) continue;  // its copy-out callback completed it
+        Request *r = b->reqs[k];
+        s->arena.release(r->img_off, image_bytes(*r));
+        s->arena.release(r->lab_off, label_bytes(*r));
+        r->status = st;
+        r->done = true;
+        --s->on_device;
+    }
+    s->arena.release(b->ws_off, b->ws_bytes);
+    s->arena.release(b->tab_off, b->tab_bytes);
+    s->streams[b->stream].busy = false;
+    --s->batches_on_device;
+    delete b;
+    s->cv_done.notify_all();
 }
 
 void scheduler(ccl_server *s) {
@@ -239,36 +452,25 @@ void scheduler(ccl_server *s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         reap_locked(s);
-        if (s->stop && s->pending.empty() && s->on_device == 0) break;
+        if (s->stop && s->pending.empty() && s->batches_on_device == 0) break;
         bool launched = false;
         for (int i = 0; i < (int)s->streams.size() && !s->stop; ++i) {
-            if (s->stream_busy[i]) continue;
+            if (s->streams[i].busy) continue;
             Batch *b = admit_locked(s, i);
             if (!b) break;
-            s->stream_busy[i] = true;
+            s->streams[i].busy = true;
+            ++s->batches_on_device;
+            ++s->batches;
+            if (b->reqs.size() > 1) ++s->multi_batches;
+            s->max_batch_seen = std::max(s->max_batch_seen, (int)b->reqs.size());
+            s->max_batches_in_flight = std::max(s->max_batches_in_flight, s->batches_on_device);
             lk.unlock();
             const ccl_status st = launch(s, b);
             lk.lock();
-            if (st != CCL_OK) {
-                // the batch never reaches its callback: let whatever was
-                // enqueued drain, then fail its requests here
-                lk.unlock();
-                cudaStreamSynchronize(s->streams[i]);
-                lk.lock();
-                s->stream_busy[i] = false;
-                for (Request *r : b->reqs) {
-                    s->arena.release(r->img_off, image_bytes(*r));
-                    s->arena.release(r->lab_off, label_bytes(*r));
-                    r->status = st;
-                    r->done = true;
-                    --s->on_device;
-                }
-                delete b;
-                s->cv_done.notify_all();
-            }
+            if (st != CCL_OK) fail_batch_locked(s, b, st, lk);
             launched = true;
         }
-        if (s->stop && s->on_device == 0) {
+        if (s->stop && s->batches_on_device == 0) {
             // drop what was never admitted
             for (Request *r : s->pending) {
                 r->status = CCL_ERR_BUSY;
@@ -280,11 +482,24 @@ void scheduler(ccl_server *s) {
         }
         if (!launched) {
             // everything admissible was started: sleep until something changes
-            // (a submission or a finished batch); the wait releases the lock,
-            // which the completion callback needs
+            // (a submission or a callback); the wait releases the lock, which
+            // the callbacks need
             const uint64_t seen = s->events;
             s->cv_sched.wait_for(lk, std::chrono::milliseconds(5), [&] { return s->events != seen; });
         }
+    }
+}
+
+void destroy_streams(ccl_server *s) {
+    for (auto &c : s->streams) {
+        if (c.s) {
+            cudaStreamSynchronize(c.s);
+            cudaStreamDestroy(c.s);
+        }
+        for (auto &e : c.ev)
+            if (e) cudaEventDestroy(e);
+        if (c.h_table) cudaFreeHost(c.h_table);
+        c = StreamCtx{};
     }
 }
 
@@ -311,17 +526,31 @@ ccl_status ccl_server_create(const ccl_server_config *config, ccl_server **out) 
     }
     s->arena.reset(config->hbm_budget_bytes);
     s->streams.resize(config->n_streams);
-    s->stream_busy.assign(config->n_streams, false);
-    for (auto &st : s->streams) {
-        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaFree(s->arena_base);
-            delete s;
-            return CCL_ERR_CUDA;
-        }
+    bool ok = cudaEventCreate(&s->t0_event) == cudaSuccess;
+    for (auto &c : s->streams) {
+        ok = ok && cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking) == cudaSuccess;
+        for (auto &e : c.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+        c.h_table_bytes = table_bytes((size_t)config->max_batch);
+        ok = ok && cudaMallocHost(&c.h_table, c.h_table_bytes) == cudaSuccess;
     }
-    s->t_create = Clock::now();
+    ok = ok && cudaEventRecord(s->t0_event, s->streams[0].s) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        destroy_streams(s);
+        if (s->t0_event) cudaEventDestroy(s->t0_event);
+        cudaFree(s->arena_base);
+        delete s;
+        return CCL_ERR_CUDA;
+    }
     s->sched = std::thread(scheduler, s);
     *out = s;
+    return CCL_OK;
+}
+
+ccl_status ccl_server_frame_bytes(int H, int W, size_t *bytes) {
+    if (!bytes || H < 1 || W < 1) return CCL_ERR_INVALID_ARG;
+    if ((long long)H * (long long)W > 2147483646LL) return CCL_ERR_UNSUPPORTED;
+    *bytes = lone_frame_bytes(H, W);
     return CCL_OK;
 }
 
@@ -342,8 +571,8 @@ ccl_status ccl_server_submit(ccl_server *s, const uint8_t *host_img, int H, int 
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        // a frame that could never fit the arena is refused outright
-        if (((image_bytes(*r) + 255) & ~(size_t)255) + ((label_bytes(*r) + 255) & ~(size_t)255) > s->arena.size()) {
+        // a frame that could never fit the arena, even alone, is refused
+        if (lone_frame_bytes(H, W) > s->arena.size()) {
             ++s->rejected;
             delete r;
             return CCL_ERR_UNSUPPORTED;
@@ -406,21 +635,28 @@ ccl_status ccl_server_stats(ccl_server *s, ccl_server_stats_t *out) {
     st.arena_bytes = s->arena.size();
     st.arena_used_bytes = s->arena.used();
     if (!s->latencies_ms.empty()) {
-        std::vector<double> v = s->latencies_ms;
-        std::sort(v.begin(), v.end());
-        const auto pct = [&](double q) {
-            const size_t i = std::min(v.size() - 1, (size_t)(q * (double)(v.size() - 1) + 0.5));
-            return v[i];
-        };
         double sum = 0;
-        for (double x : v) sum += x;
-        st.p50_ms = pct(0.50);
-        st.p99_ms = pct(0.99);
-        st.max_ms = v.back();
-        st.mean_ms = sum / (double)v.size();
-        const double span = seconds_since(s->t_first_submit, s->t_last_done);
+        for (double x : s->latencies_ms) sum += x;
+        st.p50_ms = pct(s->latencies_ms, 0.50);
+        st.p99_ms = pct(s->latencies_ms, 0.99);
+        st.max_ms = *std::max_element(s->latencies_ms.begin(), s->latencies_ms.end());
+        st.mean_ms = sum / (double)s->latencies_ms.size();
+        const double span = ms_between(s->t_first_submit, s->t_last_done) / 1e3;
         st.gpixel_s = span > 0 ? (double)s->pixels / span / 1e9 : 0.0;
     }
+    st.queue_p50_ms = pct(s->queue_ms, 0.50);
+    st.queue_p99_ms = pct(s->queue_ms, 0.99);
+    st.h2d_p50_ms = pct(s->h2d_ms, 0.50);
+    st.h2d_p99_ms = pct(s->h2d_ms, 0.99);
+    st.label_p50_ms = pct(s->label_ms, 0.50);
+    st.label_p99_ms = pct(s->label_ms, 0.99);
+    st.d2h_p50_ms = pct(s->d2h_ms, 0.50);
+    st.d2h_p99_ms = pct(s->d2h_ms, 0.99);
+    st.batches = s->batches;
+    st.multi_request_batches = s->multi_batches;
+    st.overlapped_batches = s->overlapped;
+    st.max_batch_requests = s->max_batch_seen;
+    st.max_batches_in_flight = s->max_batches_in_flight;
     *out = st;
     return CCL_OK;
 }
@@ -429,7 +665,14 @@ ccl_status ccl_server_reset_stats(ccl_server *s) {
     if (!s) return CCL_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     s->latencies_ms.clear();
+    s->queue_ms.clear();
+    s->h2d_ms.clear();
+    s->label_ms.clear();
+    s->d2h_ms.clear();
     s->submitted = s->completed = s->rejected = s->pixels = 0;
+    s->batches = s->multi_batches = s->overlapped = 0;
+    s->max_batch_seen = 0;
+    s->max_batches_in_flight = s->batches_on_device;
     s->any_submit = false;
     return CCL_OK;
 }
@@ -443,10 +686,8 @@ void ccl_server_destroy(ccl_server *s) {
     }
     s->cv_sched.notify_one();
     if (s->sched.joinable()) s->sched.join();
-    for (auto &st : s->streams) {
-        cudaStreamSynchronize(st);
-        cudaStreamDestroy(st);
-    }
+    destroy_streams(s);
+    if (s->t0_event) cudaEventDestroy(s->t0_event);
     for (auto &kv : s->requests) delete kv.second;
     cudaFree(s->arena_base);
     delete s;

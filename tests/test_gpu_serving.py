@@ -46,6 +46,15 @@ def test_server_argument_checks_without_gpu():
     assert lib.ccl_server_create(ccl.ctypes.byref(cfg), ccl.ctypes.byref(h)) == ccl.CCL_ERR_INVALID_ARG
 
 
+def test_frame_bytes_counts_scratch_without_gpu():
+    ccl_build.build()
+    b = ccl.ccl_server_frame_bytes(1080, 1920)
+    assert b > 1080 * 1920 * 5 and b % 256 == 0
+    assert ccl.ccl_server_frame_bytes(2160, 3840) > 3.9 * b
+    with pytest.raises(ccl.CclError):
+        ccl.ccl_server_frame_bytes(0, 5)
+
+
 @pytest.mark.gpu
 def test_alone_equals_in_mix_equals_oracle():
     frames = pinned_frames(18, seed=1)
@@ -58,6 +67,7 @@ def test_alone_equals_in_mix_equals_oracle():
             assert srv.wait(t) == ccl.CCL_OK
             alone.append(out.copy())
         # the mix: all at once from two submitting threads
+        srv.reset_stats()
         outs = [pinned_labels(f.shape) for f in frames]
         tickets = [None] * len(frames)
 
@@ -73,8 +83,18 @@ def test_alone_equals_in_mix_equals_oracle():
         for t in tickets:
             assert srv.wait(t) == ccl.CCL_OK
         st = srv.stats()
-        assert st["completed"] == 2 * len(frames) and st["rejected"] == 0
+        assert st["completed"] == len(frames) and st["rejected"] == 0
         assert 0 < st["p50_ms"] <= st["p99_ms"] <= st["max_ms"]
+        # continuous batching, shown by the server's own records: some batch
+        # held several requests, several batches were on the device at once,
+        # and some batch's device span (copy-in to copy-out, CUDA events)
+        # overlapped another's
+        assert st["multi_request_batches"] >= 1 and st["max_batch_requests"] >= 2
+        assert st["max_batches_in_flight"] >= 2
+        assert st["overlapped_batches"] >= 1
+        assert 0 < st["label_p50_ms"] <= st["label_p99_ms"]
+        assert 0 <= st["queue_p50_ms"] <= st["queue_p99_ms"]
+        assert st["arena_used_bytes"] == 0
     for i, f in enumerate(frames):
         want = oracle.label(f, conns[i])
         np.testing.assert_array_equal(alone[i], want, err_msg=f"alone {i}")
@@ -83,10 +103,12 @@ def test_alone_equals_in_mix_equals_oracle():
 
 @pytest.mark.gpu
 def test_admission_by_arena_memory():
-    # the arena holds only two 1920x1080 frames (image + labels) at a time,
-    # so requests are admitted as earlier ones release their memory
+    # the arena holds only two 1920x1080 frames (image, labels, their
+    # labelling scratch and job table) at a time, so requests are admitted as
+    # earlier ones release their memory
     frames = pinned_frames(10, seed=2, sizes=((1080, 1920),))
-    per_frame = 1080 * 1920 * 5 + 1024
+    per_frame = ccl.ccl_server_frame_bytes(1080, 1920)
+    assert per_frame > 1080 * 1920 * 5  # the scratch is counted too
     with ccl.CclServer(max_slots=16, n_streams=4, max_batch=8, hbm_budget_bytes=2 * per_frame + 4096) as srv:
         outs = [pinned_labels(f.shape) for f in frames]
         tickets = [srv.submit(f, o, 8) for f, o in zip(frames, outs)]
@@ -94,6 +116,7 @@ def test_admission_by_arena_memory():
             assert srv.wait(t, 60000) == ccl.CCL_OK
         st = srv.stats()
         assert st["completed"] == len(frames) and st["arena_used_bytes"] == 0
+        assert st["max_batches_in_flight"] <= 2 and st["max_batch_requests"] <= 2
         # a frame larger than the whole arena is refused outright
         big = np.zeros((2160, 3840), np.uint8)
         with pytest.raises(ccl.CclError) as e:

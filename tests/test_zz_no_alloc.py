@@ -3,12 +3,13 @@ allocate device memory while they run (for example a program whose memory
 pool owns the whole GPU, or a loop that must not let cudaMalloc/cudaFree block
 the device).  Its scratch is the library's fixed per-device array.
 
-The GPU test calls it through the C ABI twice in a row on different images and
-requires the labels of each call to equal those of ``ccl_label`` bit for bit
-(labels are integers, so the tolerance is zero), which also shows that what
-the first call left in the shared array does not disturb the second.  The
-file sorts last so that a run stopping at the first failure has already run
-every other test; it passes alone in a fresh process as well.
+The GPU test calls it through the C ABI three times in a row -- a large image,
+a small one, then the large one again -- so that every call runs over what
+the previous call left in the shared array.  Each call's labels must equal
+those of ``ccl_label`` and of the CPU oracle bit for bit (labels are integers,
+so the tolerance is zero).  The file sorts last so that a run stopping at the
+first failure has already run every other test; it passes alone in a fresh
+process as well.
 """
 import pytest
 
@@ -29,13 +30,17 @@ def test_noalloc_declared_and_exported_without_gpu():
 
 
 @pytest.mark.gpu
-def test_noalloc_matches_ccl_label_on_two_calls_in_a_row():
+def test_noalloc_matches_ccl_label_and_oracle_on_calls_in_a_row():
+    import numpy as np
     import torch
 
+    import oracle
+
     ccl_build.build()
-    cases = [(synth.bernoulli(1000, 1537, 0.5, 11), 8),
-             (synth.smoothed(4096, 4096, 8.0, 0.5, 12), 4)]
-    # the larger image fills about half of the 64 MiB scratch
+    large = (synth.smoothed(4096, 4096, 8.0, 0.5, 12), 4)
+    small = (synth.bernoulli(1000, 1537, 0.5, 11), 8)
+    cases = [large, small, large]
+    # the 4096 x 4096 image needs about a third of the 64 MiB scratch
     assert ccl.ccl_workspace_size(4096, 4096) <= ccl.ccl_noalloc_max_workspace_bytes()
     imgs = [torch.from_numpy(img).cuda() for img, _ in cases]
     outs = [torch.full(img.shape, -7, dtype=torch.int32, device="cuda") for img in imgs]
@@ -43,10 +48,11 @@ def test_noalloc_matches_ccl_label_on_two_calls_in_a_row():
     for (img_np, conn), img, out in zip(cases, imgs, outs):
         ccl.ccl_label_noalloc(img, conn, labels=out)
     assert ccl.ccl_get_device_status() == ccl.CCL_OK
-    for (img_np, conn), img, out in zip(cases, imgs, outs):
+    for k, ((img_np, conn), img, out) in enumerate(zip(cases, imgs, outs)):
         want = ccl.ccl_label(img, conn)
         assert ccl.ccl_get_device_status() == ccl.CCL_OK
-        assert torch.equal(out, want), f"{tuple(img.shape)} conn={conn}"
+        assert torch.equal(out, want), f"call {k}: {tuple(img.shape)} conn={conn}"
+        np.testing.assert_array_equal(out.cpu().numpy(), oracle.label(img_np, conn), err_msg=f"call {k}")
     # an image beyond the scratch limit is refused with a clear status
     big = torch.zeros((8192, 8192), dtype=torch.uint8, device="cuda")
     with pytest.raises(ccl.CclError) as e:
