@@ -12,16 +12,20 @@
 // A batch is enqueued on its stream as: one host->device copy per frame, the
 // job table copy, the three labelling kernels over all blocks of the batch
 // (persistent grids pulling blocks from a device work counter), then one
-// device->host copy per frame in increasing size, each followed by a host
-// callback that completes that request (a small frame does not wait for a
-// large frame's copy-out), and a final callback that hands the batch back to
-// the scheduler, which frees its arena ranges and the stream.  With several
-// streams, copies of one batch overlap kernels of another.
+// device->host copy per frame in increasing size, each followed by an event.
+// A completion thread per stream waits on those events in order (blocking
+// synchronisation, so it sleeps) and completes each request as soon as its
+// own labels are in host memory: a small frame does not wait for a large
+// frame's copy-out, and the GPU never waits for the host.  When the batch's
+// last event has passed, the thread retires the batch: it frees its arena
+// ranges and hands the stream back to the scheduler.  No CUDA call is made
+// while the server's lock is held.  With several streams, copies of one batch
+// overlap kernels of another.
 //
-// Latency of a request = time from ccl_server_submit() to the callback after
-// its label copy (labels are in host memory by then).  Per batch, CUDA events
-// split the device side into copy-in, labelling and copy-out; the scheduler
-// reads them when it retires the batch.
+// Latency of a request = time from ccl_server_submit() until its completion
+// thread has seen its label copy finish (labels are in host memory by then).
+// Per batch, CUDA events split the device side into copy-in, labelling and
+// copy-out.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -120,25 +124,22 @@ struct Batch {
     size_t blocks = 0;
     size_t ws_off = 0, ws_bytes = 0;   // labelling scratch
     size_t tab_off = 0, tab_bytes = 0; // job table
-    bool failed = false;
-    // per-request copy-out callback arguments (index into reqs); `done` is
-    // set by the callback, under the server lock
-    struct CopyDone {
-        Batch *b;
-        int idx;
-        bool done;
-    };
-    std::vector<CopyDone> cds;
+    std::vector<int> order;            // copy-out order (indices into reqs)
 };
 
-// Per-stream state: the stream, page-locked staging of the job table and the
-// events that split a batch into copy-in, labelling and copy-out.
+// Per-stream state: the stream, page-locked staging of the job table, the
+// events that split a batch into copy-in, labelling and copy-out, one event
+// per request's label copy, and the completion thread that watches them.
 struct StreamCtx {
     cudaStream_t s = nullptr;
     bool busy = false;
     unsigned char *h_table = nullptr;
     size_t h_table_bytes = 0;
     cudaEvent_t ev[4] = {};
+    std::vector<cudaEvent_t> req_ev;
+    Batch *watch = nullptr;            // the batch its thread waits on
+    std::condition_variable cv;
+    std::thread waiter;
 };
 
 // Percentile q of v (sorted copy).
@@ -156,15 +157,15 @@ struct ccl_server {
     int device = 0;
     unsigned char *arena_base = nullptr;
     Arena arena;
-    std::vector<StreamCtx> streams;
+    std::deque<StreamCtx> streams;     // (a deque: StreamCtx is not movable)
+    bool quit_waiters = false;
 
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<Request *> pending;
     std::map<uint64_t, Request *> requests;
-    std::deque<Batch *> finished;     // batch callbacks that ran
     uint64_t next_ticket = 1;
-    uint64_t events = 0;  // bumped by every submission and callback
+    uint64_t events = 0;  // bumped by every submission and completion
     int on_device = 0;
     int batches_on_device = 0;
     bool stop = false;
@@ -208,56 +209,54 @@ size_t lone_frame_bytes(int H, int W) {
            up256(frame_scratch_bytes(H, W)) + up256(table_bytes(1));
 }
 
-// Completes one request once its labels are in host memory (CUDA's callback
-// thread; no CUDA calls here).
-void CUDART_CB on_copy_done(void *p) {
-    Batch::CopyDone *cd = static_cast<Batch::CopyDone *>(p);
-    Batch *b = cd->b;
-    ccl_server *s = b->srv;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        Request *r = b->reqs[cd->idx];
-        cd->done = true;
-        s->arena.release(r->img_off, image_bytes(*r));
-        s->arena.release(r->lab_off, label_bytes(*r));
-        const Clock::time_point now = Clock::now();
-        r->t_done = now;
-        r->done = true;
-        --s->on_device;
-        ++s->completed;
-        s->pixels += (uint64_t)r->H * (uint64_t)r->W;
-        s->latencies_ms.push_back(ms_between(r->t_submit, now));
-        s->t_last_done = now;
-        ++s->events;
-    }
-    s->cv_done.notify_all();
-    s->cv_sched.notify_one();
+// Runs with s->mu held: request r's labels are in host memory.
+void complete_locked(ccl_server *s, Request *r, Clock::time_point now) {
+    s->arena.release(r->img_off, image_bytes(*r));
+    s->arena.release(r->lab_off, label_bytes(*r));
+    r->t_done = now;
+    r->done = true;
+    --s->on_device;
+    ++s->completed;
+    s->pixels += (uint64_t)r->H * (uint64_t)r->W;
+    s->latencies_ms.push_back(ms_between(r->t_submit, now));
+    s->t_last_done = now;
 }
 
-void CUDART_CB on_batch_done(void *p) {
-    Batch *b = static_cast<Batch *>(p);
-    ccl_server *s = b->srv;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        s->finished.push_back(b);
-        ++s->events;
-    }
-    s->cv_sched.notify_one();
-}
-
-// Runs with s->mu held: retires finished batches -- stage times from their
-// events, the device-overlap record, their scratch and their stream.
-void reap_locked(ccl_server *s) {
-    while (!s->finished.empty()) {
-        Batch *b = s->finished.front();
-        s->finished.pop_front();
-        StreamCtx &c = s->streams[b->stream];
+// Completion thread of stream `i`: waits (sleeping) on the events of the
+// batch it is given, completes each request when its label copy is done, and
+// retires the batch after its last event.
+void waiter(ccl_server *s, int i) {
+    cudaSetDevice(s->device);
+    StreamCtx &c = s->streams[i];
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        c.cv.wait(lk, [&] { return c.watch != nullptr || s->quit_waiters; });
+        if (!c.watch) break;
+        Batch *b = c.watch;
+        lk.unlock();
+        for (size_t k = 0; k < b->order.size(); ++k) {
+            const bool ok = cudaEventSynchronize(c.req_ev[k]) == cudaSuccess;
+            const Clock::time_point now = Clock::now();
+            {
+                std::lock_guard<std::mutex> g(s->mu);
+                Request *r = b->reqs[b->order[k]];
+                if (!ok) r->status = CCL_ERR_CUDA;
+                complete_locked(s, r, now);
+                ++s->events;
+            }
+            s->cv_done.notify_all();
+            s->cv_sched.notify_one();
+        }
+        // stage times and the device span of the batch (no lock held)
         float t01 = 0.f, t12 = 0.f, t23 = 0.f, a = 0.f, e = 0.f;
-        const bool ok = cudaEventElapsedTime(&t01, c.ev[0], c.ev[1]) == cudaSuccess &&
-                        cudaEventElapsedTime(&t12, c.ev[1], c.ev[2]) == cudaSuccess &&
-                        cudaEventElapsedTime(&t23, c.ev[2], c.ev[3]) == cudaSuccess &&
-                        cudaEventElapsedTime(&a, s->t0_event, c.ev[0]) == cudaSuccess &&
-                        cudaEventElapsedTime(&e, s->t0_event, c.ev[3]) == cudaSuccess;
+        bool ok = cudaEventSynchronize(c.ev[3]) == cudaSuccess;
+        ok = ok && cudaEventElapsedTime(&t01, c.ev[0], c.ev[1]) == cudaSuccess &&
+             cudaEventElapsedTime(&t12, c.ev[1], c.ev[2]) == cudaSuccess &&
+             cudaEventElapsedTime(&t23, c.ev[2], c.ev[3]) == cudaSuccess &&
+             cudaEventElapsedTime(&a, s->t0_event, c.ev[0]) == cudaSuccess &&
+             cudaEventElapsedTime(&e, s->t0_event, c.ev[3]) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+        lk.lock();
         if (ok) {
             for (size_t k = 0; k < b->reqs.size(); ++k) {
                 s->h2d_ms.push_back(t01);
@@ -270,14 +269,15 @@ void reap_locked(ccl_server *s) {
             if (overlap) ++s->overlapped;
             s->recent_spans.emplace_back(a, e);
             if (s->recent_spans.size() > 64) s->recent_spans.pop_front();
-        } else {
-            cudaGetLastError();
         }
         s->arena.release(b->ws_off, b->ws_bytes);
         s->arena.release(b->tab_off, b->tab_bytes);
         c.busy = false;
+        c.watch = nullptr;
         --s->batches_on_device;
+        ++s->events;
         delete b;
+        s->cv_sched.notify_one();
     }
 }
 
@@ -355,8 +355,6 @@ Batch *admit_locked(ccl_server *s, int stream) {
         }
     }
     for (Request *r : b->reqs) s->queue_ms.push_back(ms_between(r->t_submit, r->t_admit));
-    b->cds.reserve(b->reqs.size());
-    for (int i = 0; i < (int)b->reqs.size(); ++i) b->cds.push_back({b, i, false});
     return b;
 }
 
@@ -405,34 +403,31 @@ ccl_status launch(ccl_server *s, Batch *b) {
                          b->blocks, st, ccl::iteration_cap_api()) != 0)
         return CCL_ERR_CUDA;
     if (cudaEventRecord(c.ev[2], st) != cudaSuccess) return CCL_ERR_CUDA;
-    std::vector<int> order(b->reqs.size());
+    std::vector<int> &order = b->order;
+    order.resize(b->reqs.size());
     for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return label_bytes(*b->reqs[x]) < label_bytes(*b->reqs[y]); });
-    for (int k : order) {
-        Request *r = b->reqs[k];
+    for (size_t k = 0; k < order.size(); ++k) {
+        Request *r = b->reqs[order[k]];
         if (cudaMemcpyAsync(r->host_labels, base + r->lab_off, label_bytes(*r), cudaMemcpyDeviceToHost, st) !=
                 cudaSuccess ||
-            cudaLaunchHostFunc(st, on_copy_done, &b->cds[k]) != cudaSuccess)
+            cudaEventRecord(c.req_ev[k], st) != cudaSuccess)
             return CCL_ERR_CUDA;
     }
     if (cudaEventRecord(c.ev[3], st) != cudaSuccess) return CCL_ERR_CUDA;
-    if (cudaLaunchHostFunc(st, on_batch_done, b) != cudaSuccess) return CCL_ERR_CUDA;
     return CCL_OK;
 }
 
 // Runs with s->mu held (released around the stream wait): a batch whose
-// enqueue failed never reaches its final callback.  Waits for what was
-// enqueued, then fails every request whose labels were not copied out.
+// enqueue failed is never given to its completion thread.  Waits for what
+// was enqueued, then fails every request of the batch.
 void fail_batch_locked(ccl_server *s, Batch *b, ccl_status st, std::unique_lock<std::mutex> &lk) {
-    b->failed = true;
     lk.unlock();
     cudaStreamSynchronize(s->streams[b->stream].s);
     cudaGetLastError();
     lk.lock();
-    for (size_t k = 0; k < b->reqs.size(); ++k) {
-        if (b->cds[k].done) continue;  // its copy-out callback completed it
-        Request *r = b->reqs[k];
+    for (Request *r : b->reqs) {
         s->arena.release(r->img_off, image_bytes(*r));
         s->arena.release(r->lab_off, label_bytes(*r));
         r->status = st;
@@ -451,7 +446,6 @@ void scheduler(ccl_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        reap_locked(s);
         if (s->stop && s->pending.empty() && s->batches_on_device == 0) break;
         bool launched = false;
         for (int i = 0; i < (int)s->streams.size() && !s->stop; ++i) {
@@ -467,7 +461,12 @@ void scheduler(ccl_server *s) {
             lk.unlock();
             const ccl_status st = launch(s, b);
             lk.lock();
-            if (st != CCL_OK) fail_batch_locked(s, b, st, lk);
+            if (st != CCL_OK) {
+                fail_batch_locked(s, b, st, lk);
+            } else {
+                s->streams[i].watch = b;
+                s->streams[i].cv.notify_one();
+            }
             launched = true;
         }
         if (s->stop && s->batches_on_device == 0) {
@@ -482,15 +481,24 @@ void scheduler(ccl_server *s) {
         }
         if (!launched) {
             // everything admissible was started: sleep until something changes
-            // (a submission or a callback); the wait releases the lock, which
-            // the callbacks need
+            // (a submission or a completion); the wait releases the lock, which
+            // the completion threads need
             const uint64_t seen = s->events;
             s->cv_sched.wait_for(lk, std::chrono::milliseconds(5), [&] { return s->events != seen; });
         }
     }
 }
 
+// Stops the completion threads (after the scheduler has ended, so no batch
+// is on the device) and frees the per-stream resources.
 void destroy_streams(ccl_server *s) {
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->quit_waiters = true;
+    }
+    for (auto &c : s->streams) c.cv.notify_all();
+    for (auto &c : s->streams)
+        if (c.waiter.joinable()) c.waiter.join();
     for (auto &c : s->streams) {
         if (c.s) {
             cudaStreamSynchronize(c.s);
@@ -498,8 +506,13 @@ void destroy_streams(ccl_server *s) {
         }
         for (auto &e : c.ev)
             if (e) cudaEventDestroy(e);
+        for (auto &e : c.req_ev)
+            if (e) cudaEventDestroy(e);
         if (c.h_table) cudaFreeHost(c.h_table);
-        c = StreamCtx{};
+        c.s = nullptr;
+        c.h_table = nullptr;
+        c.req_ev.clear();
+        for (auto &e : c.ev) e = nullptr;
     }
 }
 
@@ -529,7 +542,11 @@ ccl_status ccl_server_create(const ccl_server_config *config, ccl_server **out) 
     bool ok = cudaEventCreate(&s->t0_event) == cudaSuccess;
     for (auto &c : s->streams) {
         ok = ok && cudaStreamCreateWithFlags(&c.s, cudaStreamNonBlocking) == cudaSuccess;
-        for (auto &e : c.ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+        // the completion thread sleeps in its waits (blocking synchronisation)
+        for (auto &e : c.ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventBlockingSync) == cudaSuccess;
+        c.req_ev.assign((size_t)config->max_batch, nullptr);
+        for (auto &e : c.req_ev)
+            ok = ok && cudaEventCreateWithFlags(&e, cudaEventBlockingSync | cudaEventDisableTiming) == cudaSuccess;
         c.h_table_bytes = table_bytes((size_t)config->max_batch);
         ok = ok && cudaMallocHost(&c.h_table, c.h_table_bytes) == cudaSuccess;
     }
@@ -542,6 +559,7 @@ ccl_status ccl_server_create(const ccl_server_config *config, ccl_server **out) 
         delete s;
         return CCL_ERR_CUDA;
     }
+    for (int i = 0; i < (int)s->streams.size(); ++i) s->streams[i].waiter = std::thread(waiter, s, i);
     s->sched = std::thread(scheduler, s);
     *out = s;
     return CCL_OK;
