@@ -930,6 +930,8 @@ __global__ void __launch_bounds__(G::kThreads) k_block_write(JobTable jt, Scratc
 
 }  // namespace ccl
 
+#include "ccl_pieces.cuh"
+
 // ---------------------------------------------------------------------------
 // Host side of this translation unit.
 
@@ -981,6 +983,36 @@ using G0 = Geo<16, 16, 4>;
 using G1 = Geo<8, 16, 4>;
 using G2 = Geo<32, 8, 4>;
 using G3 = Geo<16, 8, 8>;
+
+// the piece labeller's blocks (8-connectivity): 512 x 64 pixels, 256 threads
+using P8 = PGeo<512, 64, 256, true>;
+static_assert(P8::kBW == G0::kBW && P8::kBH == G0::kBH, "the piece blocks cover the same blocks as 512x64");
+
+template <class PG>
+Layout layout_p(size_t nb) {
+    Layout l;
+    size_t off = 0;
+    l.masks = off;   off += up256(nb * PG::kBH * PG::kWords * sizeof(uint32_t));
+    l.vstream = off; off += up256(nb * PG::kMaxPieces * sizeof(uint16_t));
+    l.edges = off;   off += up256(nb * PG::kEdge * sizeof(uint16_t));
+    l.P = off;       off += up256(nb * PG::kSlots * sizeof(uint64_t));
+    l.nslots = off;  off += up256(nb * sizeof(int32_t));
+    l.total = off;
+    return l;
+}
+
+template <class PG>
+PScratch carve_p(void *ws, size_t nb) {
+    const Layout l = layout_p<PG>(nb);
+    char *p = static_cast<char *>(ws);
+    PScratch s;
+    s.masks = reinterpret_cast<uint32_t *>(p + l.masks);
+    s.values = reinterpret_cast<uint16_t *>(p + l.vstream);
+    s.edges = reinterpret_cast<uint16_t *>(p + l.edges);
+    s.P = reinterpret_cast<uint64_t *>(p + l.P);
+    s.nslots = reinterpret_cast<int32_t *>(p + l.nslots);
+    return s;
+}
 
 }  // namespace
 
@@ -1196,6 +1228,87 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
                            global_cap, bound, stream);
 }
 
+// Per-device set-up of the piece kernels (their shared memory exceeds the 48 KB
+// a launch gets without opting in) and their occupancy.
+template <class PG>
+bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
+    static std::mutex mu;
+    struct Ent {
+        bool ready = false;
+        int occ_local = 0, occ_write = 0, sms = 0;
+    };
+    static Ent per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    Ent &e = per_dev[dev];
+    if (!e.ready) {
+        const int bl = (int)sizeof(PLocalSmem<PG>), bw = (int)sizeof(PWriteSmem<PG>);
+        if (cudaFuncSetAttribute(k_piece_local<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bl) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_piece_write<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bw) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_local, k_piece_local<PG>, PG::kThreads, bl) !=
+                cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_write, k_piece_write<PG>, PG::kThreads, bw) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&e.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return false;
+        e.occ_local = std::max(1, e.occ_local);
+        e.occ_write = std::max(1, e.occ_write);
+        e.ready = true;
+    }
+    occ_local = e.occ_local;
+    occ_write = e.occ_write;
+    sms = e.sms;
+    return true;
+}
+
+// Step 1 (piece labeller), step 2 (the block merge on the border records)
+// and step 3 (piece write-out) over the jobs of `jt`.
+template <class PG>
+int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
+                       const PScratch &ps, size_t nb, int cap, cudaStream_t stream) {
+    const int local_cap = cap > 0 ? cap : PG::kMaxPieces + 16;
+    const long long slots = (long long)nb * PG::kSlots;
+    const int global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
+    const uint32_t bound = (uint32_t)slots;
+    Scratch ms{};
+    ms.edges = ps.edges;
+    ms.P = ps.P;
+    ms.nslots = ps.nslots;
+    cudaEvent_t ev = timing_mark(stream, nullptr, -1);
+    k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
+    ev = timing_mark(stream, ev, kKindLocal);
+    k_block_merge<PG, PG::kConn8><<<grid_merge, PG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap, bound);
+    ev = timing_mark(stream, ev, kKindMerge);
+    k_piece_write<PG><<<grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream>>>(jt, ps, global_cap, bound);
+    ev = timing_mark(stream, ev, kKindWrite);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <class PG>
+int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
+                        cudaStream_t stream, int cap) {
+    int occ_l = 0, occ_w = 0, sms = 0;
+    if (!piece_prepare<PG>(occ_l, occ_w, sms)) return -1;
+    JobTable jt{};
+    jt.single.img = img;
+    jt.single.labels = labels;
+    jt.single.pitch = pitch;
+    jt.single.H = H;
+    jt.single.W = W;
+    jt.single.nbx = (W + PG::kBW - 1) / PG::kBW;
+    jt.single.nby = (H + PG::kBH - 1) / PG::kBH;
+    jt.single.block0 = 0;
+    jt.single.flags = ((((uintptr_t)img | pitch) & 15) == 0 ? kJobVecIn : 0u) |
+                      ((((uintptr_t)labels & 15) == 0 && (W & 3) == 0) ? kJobVecOut : 0u);
+    const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
+    jt.total = (unsigned)nb;
+    return launch_piece_table<PG>(jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve_p<PG>(ws, nb), nb, cap,
+                                  stream);
+}
+
 template <class G>
 int launch_batch(int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t capacity, cudaStream_t stream,
                  int cap) {
@@ -1292,26 +1405,20 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
     }
 }
 
-// A single image runs on 512x64 blocks: 32x4 lane tiles while the image has
-// fewer blocks than fill the GPU several times over (short per-thread chains
-// keep more warps busy per SM); under 8-connectivity 32x8 lane tiles from
-// 1024 blocks on (about 5800x5800 pixels; fewer seams and instructions once
-// every SM is full).  Under 4-connectivity 32x8 lane tiles hold only 5 CTAs
-// of 128 threads per SM (shared memory), and 32x4 stays faster at every size
-// measured (up to 8192x8192).
-constexpr size_t kTallFromBlocks = 1024;
-static_assert(G0::kBW == G3::kBW && G0::kBH == G3::kBH, "both single-image shapes cover the same blocks");
-
+// A single image under 8-connectivity runs on the piece labeller
+// (ccl_pieces.cuh) on 512x64 blocks: its pieces span the block width, so a
+// block has no inner seams, and the contacts between bands are found for 32
+// columns at a time by bit operations.  Under 4-connectivity a single image
+// runs on the lane-tile kernels above: 32x4 lane tiles at every size measured
+// (32x8 lane tiles hold only 5 CTAs of 128 threads per SM there).
 size_t workspace_bytes(int H, int W) {
     const size_t nb = blocks_of<G0>(H, W);
-    const size_t a = layout_for<G0>(nb).total, b = layout_for<G3>(nb).total;
-    return a > b ? a : b;
+    return std::max(layout_p<P8>(nb).total, std::max(layout_for<G0>(nb).total, layout_for<G3>(nb).total));
 }
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap) {
-    if (conn == 8 && blocks_of<G3>(H, W) >= kTallFromBlocks)
-        return launch_single<G3>(img, H, W, pitch, conn, labels, ws, stream, cap);
+    if (conn == 8) return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap);
     return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
 }
 
