@@ -1280,7 +1280,16 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
     ev = timing_mark(stream, ev, kKindLocal);
-    k_block_merge<PG, PG::kConn8><<<grid_merge, PG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap, bound);
+    // the merge of many blocks runs on 128 threads per block (more blocks
+    // per SM for its latency-bound unions), that of fewer on 256 (a shorter
+    // chain per block)
+    if (nb >= 1024) {
+        using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
+        k_block_merge<MG, PG::kConn8><<<grid_merge, MG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap, bound);
+    } else {
+        k_block_merge<PG, PG::kConn8><<<grid_merge, PG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap,
+                                                                                  bound);
+    }
     ev = timing_mark(stream, ev, kKindMerge);
     k_piece_write<PG><<<grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream>>>(jt, ps, global_cap, bound);
     ev = timing_mark(stream, ev, kKindWrite);

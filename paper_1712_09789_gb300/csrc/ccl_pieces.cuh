@@ -292,7 +292,7 @@ struct PLocalSmem {
     uint16_t pb[PG::kBands][PG::kWords];  // pieces of the band in earlier words
     uint16_t bandcnt[PG::kBands];
     uint16_t bb[PG::kBands + 1];          // pieces in earlier bands
-    uint16_t st[PG::kMaxPieces];          // band << kBWLog2 | first column of each piece
+    alignas(16) uint16_t st[PG::kMaxPieces];  // band << kBWLog2 | first column of each piece
     uint16_t par[PG::kMaxPieces];         // label-equivalence list entries
     uint32_t border[PG::kMaxPieces / 32]; // bit per entry: root owning a block-border pixel
     uint32_t prefix[PG::kMaxPieces / 32]; // border roots in the words before
@@ -518,39 +518,77 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
         __syncthreads();
     }
     // -- refinement: every other event joins its two pieces; the CAS union
-    // runs only where the roots their entries name differ
+    // runs only where the roots their entries name differ.  The events are
+    // first packed into a list of (piece, piece above) pairs (in the space of
+    // the piece starts, no longer needed), so that every lane takes one per
+    // step.
+    {
+        constexpr int kCand = PG::kMaxPieces / 2;  // pairs per pass
+        uint32_t* const cand = reinterpret_cast<uint32_t*>(sm.st);
+        uint32_t cnt[kItems], sum = 0;
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int item = t + j * T;
-        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        const uint32_t fe = sm.FE[k][w], el = sm.EL[k][w];
-        uint32_t ud = sm.D1[k][w] & ~fe, ul = el & ~fe, ur = sm.ER[k][w] & ~(fe & ~el);
-        while (__any_sync(kFull, (ud | ul | ur) != 0u)) {
-            bool need = false;
-            int q = 0, iu = 0;
-            if (ud | ul | ur) {
-                int c, uc;
-                if (ud) {
-                    c = lobit(ud);
-                    ud &= ud - 1u;
-                    uc = 32 * w + c;
-                } else if (ul) {
-                    c = lobit(ul);
-                    ul &= ul - 1u;
-                    uc = 32 * w + c - 1;
-                } else {
-                    c = lobit(ur);
-                    ur &= ur - 1u;
-                    uc = 32 * w + c + 1;
+        for (int j = 0; j < kItems; ++j) {
+            const int item = t + j * T;
+            const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+            const uint32_t fe = sm.FE[k][w], el = sm.EL[k][w];
+            cnt[j] = __popc(sm.D1[k][w] & ~fe) + __popc(el & ~fe) + __popc(sm.ER[k][w] & ~(fe & ~el));
+            sum += cnt[j];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t v = __shfl_up_sync(kFull, incl, d);
+            if (lane >= d) incl += v;
+        }
+        if (lane == 31) sm.warp_tot[warp] = incl;
+        __syncthreads();
+        uint32_t base = 0, total = 0;
+        for (int q = 0; q < PG::kWarps; ++q) {
+            if (q < warp) base += sm.warp_tot[q];
+            total += sm.warp_tot[q];
+        }
+        base += incl - sum;
+        for (uint32_t lo = 0; lo < total; lo += kCand) {
+            const uint32_t hi = lo + kCand;
+            uint32_t at = base;
+#pragma unroll
+            for (int j = 0; j < kItems; ++j) {
+                const int item = t + j * T;
+                const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+                if (at + cnt[j] > lo && at < hi) {
+                    const uint32_t fe = sm.FE[k][w], el = sm.EL[k][w];
+                    uint32_t ud = sm.D1[k][w] & ~fe, ul = el & ~fe, ur = sm.ER[k][w] & ~(fe & ~el);
+                    uint32_t idx = at;
+                    const int qb = (int)sm.bb[k] + (int)sm.pb[k][w] - 1;
+                    for (; (ud | ul | ur) && idx < hi; ++idx) {
+                        int c, uc;
+                        if (ud) { c = lobit(ud); ud &= ud - 1u; uc = 32 * w + c; }
+                        else if (ul) { c = lobit(ul); ul &= ul - 1u; uc = 32 * w + c - 1; }
+                        else { c = lobit(ur); ur &= ur - 1u; uc = 32 * w + c + 1; }
+                        if (idx < lo) continue;
+                        const int q = qb + __popc(sm.S[k][w] & upto(c));
+                        cand[idx - lo] = ((uint32_t)q << 16) | (uint32_t)piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
+                    }
                 }
-                q = piece_at<PG>(sm.S, sm.pb, sm.bb, k, 32 * w + c);
-                iu = piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
-                need = proot2(vpar, q) != proot2(vpar, iu);
+                at += cnt[j];
             }
-            punion_sync(par, need, q, iu, cap, err);
+            __syncthreads();
+            const uint32_t nc = total - lo < (uint32_t)kCand ? total - lo : (uint32_t)kCand;
+            for (uint32_t j0 = 0; j0 < nc; j0 += T) {
+                const uint32_t j = j0 + t;
+                int q = 0, iu = 0;
+                bool need = false;
+                if (j < nc) {
+                    const uint32_t e = cand[j];
+                    q = (int)(e >> 16);
+                    iu = (int)(e & 0xFFFFu);
+                    need = proot2(vpar, q) != proot2(vpar, iu);
+                }
+                punion_sync(par, need, q, iu, cap, err);
+            }
+            __syncthreads();
         }
     }
-    __syncthreads();
     // -- compress: every entry points straight at its root (the finds only
     // read, so every store here is a final root)
     for (int i = t; i < n; i += T) {
@@ -708,6 +746,14 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     __syncthreads();
     band_prefix<PG>(sm.bandcnt, sm.bb);
     __syncthreads();
+    // pb[k][w] becomes the index of the first piece of band k starting in word w or later
+#pragma unroll
+    for (int j = 0; j < PG::kBands * W / T; ++j) {
+        const int item = t + j * T;
+        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+        sm.pb[k][w] = (uint16_t)(sm.pb[k][w] + sm.bb[k]);
+    }
+    __syncthreads();
 
     const uint16_t *const vin = s.values + (size_t)b * PG::kMaxPieces;
     for (int k0 = 0; k0 < PG::kBands;) {
@@ -723,41 +769,50 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
                                                   (uint32_t)(x0 + (int)(v & (PG::kBW - 1)))) + 1;
         }
         __syncthreads();
-        // every pixel takes the label of its piece; a thread writes 4
-        // columns of both rows of a band per step, a warp 128 columns
-        const int nitems = (k1 - k0) * kChunks;
-        for (int it = t; it < nitems; it += T) {
-            const int k = k0 + it / kChunks;
-            const int q = it % kChunks;
+        // every pixel takes the label of its piece: a thread keeps one
+        // 4-column chunk and walks down the bands of the window (a warp
+        // writes 128 consecutive columns of two rows per step)
+        {
+            constexpr int kStep = T / kChunks;  // bands per step
+            const int q = t & (kChunks - 1);
             const int w = q >> 3, c0 = (q & 7) * 4;
             const int x = x0 + 4 * q;
-            if (x >= Wd) continue;
-            const uint32_t A4 = (sm.m[2 * k][w] >> c0) & 15u, B4 = (sm.m[2 * k + 1][w] >> c0) & 15u;
-            int l[4] = {0, 0, 0, 0};
-            if (A4 | B4) {
-                const uint32_t Sw = sm.S[k][w];
-                int idx = (int)sm.bb[k] + (int)sm.pb[k][w] - p0 - 1 + __popc(Sw & ((1u << c0) - 1u));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    idx += (int)((Sw >> (c0 + j)) & 1u);
-                    if (((A4 | B4) >> j) & 1u) l[j] = sm.lab[idx];
-                }
-            }
-#pragma unroll
-            for (int rr = 0; rr < 2; ++rr) {
-                const int y = y0 + 2 * k + rr;
-                if (y >= H) break;
-                const uint32_t m4 = rr == 0 ? A4 : B4;
-                const int v0 = (m4 & 1u) ? l[0] : 0, v1 = (m4 & 2u) ? l[1] : 0;
-                const int v2 = (m4 & 4u) ? l[2] : 0, v3 = (m4 & 8u) ? l[3] : 0;
-                int32_t *dst = labels + (size_t)y * Wd + x;
-                if (vec_out && x + 4 <= Wd) {
-                    __stcs(reinterpret_cast<int4 *>(dst), make_int4(v0, v1, v2, v3));
-                } else {
-                    __stcs(dst, v0);
-                    if (x + 1 < Wd) __stcs(dst + 1, v1);
-                    if (x + 2 < Wd) __stcs(dst + 2, v2);
-                    if (x + 3 < Wd) __stcs(dst + 3, v3);
+            const bool vec = vec_out && x + 4 <= Wd;
+            const uint32_t below = (1u << c0) - 1u;
+            if (x < Wd) {
+                for (int k = k0 + t / kChunks; k < k1; k += kStep) {
+                    const int y = y0 + 2 * k;
+                    if (y >= H) break;
+                    const uint32_t A4 = (sm.m[2 * k][w] >> c0) & 15u, B4 = (sm.m[2 * k + 1][w] >> c0) & 15u;
+                    const uint32_t O4 = A4 | B4;
+                    int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
+                    if (O4) {
+                        const uint32_t Sw = sm.S[k][w] >> c0;
+                        const int idx = (int)sm.pb[k][w] - p0 - 1 + __popc(sm.S[k][w] & below);
+                        const int i0 = idx + (int)(Sw & 1u), i1 = i0 + (int)((Sw >> 1) & 1u);
+                        const int i2 = i1 + (int)((Sw >> 2) & 1u), i3 = i2 + (int)((Sw >> 3) & 1u);
+                        if (O4 & 1u) l0 = sm.lab[i0];
+                        if (O4 & 2u) l1 = sm.lab[i1];
+                        if (O4 & 4u) l2 = sm.lab[i2];
+                        if (O4 & 8u) l3 = sm.lab[i3];
+                    }
+                    int32_t *dst = labels + (size_t)y * Wd + x;
+                    const int4 va = make_int4((A4 & 1u) ? l0 : 0, (A4 & 2u) ? l1 : 0, (A4 & 4u) ? l2 : 0,
+                                              (A4 & 8u) ? l3 : 0);
+                    const int4 vb = make_int4((B4 & 1u) ? l0 : 0, (B4 & 2u) ? l1 : 0, (B4 & 4u) ? l2 : 0,
+                                              (B4 & 8u) ? l3 : 0);
+                    const bool row2 = y + 1 < H;
+                    if (vec) {
+                        __stcs(reinterpret_cast<int4 *>(dst), va);
+                        if (row2) __stcs(reinterpret_cast<int4 *>(dst + Wd), vb);
+                    } else {
+                        const int n = Wd - x < 4 ? Wd - x : 4;
+                        const int a[4] = {va.x, va.y, va.z, va.w}, bq[4] = {vb.x, vb.y, vb.z, vb.w};
+                        for (int e = 0; e < n; ++e) {
+                            __stcs(dst + e, a[e]);
+                            if (row2) __stcs(dst + Wd + e, bq[e]);
+                        }
+                    }
                 }
             }
         }
