@@ -55,9 +55,11 @@ METRIC = "Gpixel/s & % HBM roofline, plain vs batched persistent; serving p50/p9
 UNIT = "Gpixel/s"
 BYTES_PER_PIXEL = 5          # 1 B image read + 4 B label written
 KERNEL_BYTES_PER_PIXEL = {   # the path's algorithmic bytes each kernel moves, per pixel
-    "k_block_local": 1,      # reads the image once
+    "k_block_local": 1,      # reads the image once (lane-tile kernels: 4-connected images)
     "k_block_merge": 0,      # block border records only
     "k_block_write": 4,      # writes every label once
+    "k_piece_local": 1,      # reads the image once (piece labeller: 8-connected images)
+    "k_piece_write": 4,      # writes every label once
 }
 SIDE = 4096                  # the 4096x4096 noise set (an extra)
 CONNS = (4, 8)
@@ -80,7 +82,7 @@ def load_peaks():
 
 
 # the sources that define the three labelling kernels of the step
-KERNEL_SOURCES = ("ccl_block.cuh", "ccl_internal.h", "ccl_kernels.cu")
+KERNEL_SOURCES = ("ccl_block.cuh", "ccl_internal.h", "ccl_kernels.cu", "ccl_pieces.cuh")
 
 
 def csrc_digest():
@@ -326,7 +328,7 @@ def run_ours(args):
     for _ in range(args.steps):
         step()
     torch.cuda.synchronize()
-    ktimes = ccl.ccl_debug_kernel_times()
+    ktimes = {k: v for k, v in ccl.ccl_debug_kernel_times().items() if v[1]}
     ccl.ccl_debug_kernel_timing(False)
 
     hbm_gbs, peak_kind, _ = load_peaks()
@@ -493,7 +495,7 @@ def bench_noise_4096(torch, ccl, hbm_gbs, reps=5):
     ccl.ccl_debug_kernel_timing(True)
     one_pass()
     torch.cuda.synchronize()
-    kt = ccl.ccl_debug_kernel_times()
+    kt = {k: v for k, v in ccl.ccl_debug_kernel_times().items() if v[1]}
     ccl.ccl_debug_kernel_timing(False)
     if ccl.ccl_get_device_status() != ccl.CCL_OK:
         raise RuntimeError("4096x4096 noise set reported a device error")

@@ -392,9 +392,13 @@ void ccl_debug_set_iteration_cap(int cap);
 
 /*
  * Benchmark hook.  While enabled, every call records CUDA events on its own
- * stream around each of its kernels (kind 0: block-local labelling, 1: block
- * merge, 2: root-find and label write-out) and their durations accumulate per
- * kind.  Enabling or disabling waits for pending events and clears the sums.
+ * stream around each of its kernels and their durations accumulate per kind:
+ * 0 block-local labelling, 1 block merge, 2 root-find and label write-out
+ * (lane-tile kernels: 4-connected single images, batches, variants), 3 and 4
+ * the piece labeller's local labelling and write-out (8-connected single
+ * images; its merge is kind 1).  While enabled the kernels of a call run one
+ * after another (no programmatic overlap).  Enabling or disabling waits for
+ * pending events and clears the sums.
  */
 void ccl_debug_kernel_timing(int enable);
 

@@ -117,6 +117,15 @@ __device__ __forceinline__ uint4 ldg_nc16(const void *p) {
     return v;
 }
 
+// Programmatic dependent launch (griddepcontrol): a kernel launched with
+// programmatic stream serialisation may start while the kernel before it on
+// the stream still runs.  grid_dependency_wait() blocks until that kernel has
+// completed and its memory is visible (a no-op for a kernel launched without
+// the attribute); grid_launch_dependents() lets the next such kernel start
+// once every CTA of this grid has called it or exited.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 // Run mask of bits a0..a1.  a1 == 31 wraps 2u << 31 to 0, which still gives
 // the bits a0..31.
 __device__ __forceinline__ uint32_t run_bits(int a0, int a1) { return (2u << a1) - (1u << a0); }

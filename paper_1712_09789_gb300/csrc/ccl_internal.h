@@ -106,8 +106,12 @@ ccl_status check_image_args_api(const void *img, int H, int W, size_t pitch, int
 int iteration_cap_api();
 
 // Benchmark timing of the kernels enqueued by launch_label().
-constexpr int kKindLocal = 0, kKindMerge = 1, kKindWrite = 2;
-constexpr int kKernelKinds = 3;
+// (kinds 0-2: the lane-tile kernels; 3 and 4: the piece labeller's step 1
+// and step 3, whose step 2 is kind 1)
+constexpr int kKindLocal = 0, kKindMerge = 1, kKindWrite = 2, kKindPieceLocal = 3, kKindPieceWrite = 4;
+constexpr int kKernelKinds = 5;
+// a record of this kind closes the timing of one call
+constexpr bool kind_closes_call(int k) { return k == kKindWrite || k == kKindPieceWrite; }
 void timing_enable(bool on);
 int timing_read(double *ms, long long *count, int n);
 const char *kernel_kind_name(int k);

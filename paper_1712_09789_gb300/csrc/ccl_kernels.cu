@@ -776,6 +776,11 @@ template <class G, bool kConn8>
 __global__ void __launch_bounds__(G::kThreads) k_block_merge(JobTable jt, Scratch s, int lcap, int gcap,
                                                              uint32_t bound) {
     __shared__ MergeSmem<G> sm;
+    // launched after step 1, possibly before it has finished (programmatic
+    // dependent launch): wait for it, then let the write-out start its
+    // prologue while the merge runs
+    grid_dependency_wait();
+    grid_launch_dependents();
     for (unsigned iter = 0; claim_item(jt, 1, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         const unsigned lb = sm.item.lb, gb = sm.item.gb;
@@ -1069,7 +1074,7 @@ void timing_fold(bool wait) {
         // r.b opens the next record of the same call, so only r.a is free
         // now; the last record of a call frees its closing event as well.
         g_timing.pool.push_back(r.a);
-        if (r.kind == kKernelKinds - 1) g_timing.pool.push_back(r.b);
+        if (kind_closes_call(r.kind)) g_timing.pool.push_back(r.b);
     }
 }
 
@@ -1114,7 +1119,8 @@ int timing_read(double *ms, long long *count, int n) {
 }
 
 const char *kernel_kind_name(int k) {
-    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write"};
+    static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write", "k_piece_local",
+                                              "k_piece_write"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
 }
 
@@ -1228,6 +1234,25 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
                            global_cap, bound, stream);
 }
 
+// Launches `kernel` on `stream`; with `pdl` as a programmatic dependent
+// launch (it may start before the previous kernel on the stream ends and
+// waits for it with griddepcontrol.wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t stream,
+                      bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Per-device set-up of the piece kernels (their shared memory exceeds the 48 KB
 // a launch gets without opting in) and their occupancy.
 template <class PG>
@@ -1278,22 +1303,28 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
     ms.P = ps.P;
     ms.nslots = ps.nslots;
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
+    // per-kernel timing records events between the kernels, which a
+    // programmatic (overlapping) launch would blur: off while timing
+    const bool pdl = ev == nullptr;
     k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
-    ev = timing_mark(stream, ev, kKindLocal);
+    ev = timing_mark(stream, ev, kKindPieceLocal);
     // the merge of many blocks runs on 128 threads per block (more blocks
     // per SM for its latency-bound unions), that of fewer on 256 (a shorter
     // chain per block)
+    bool ok = true;
     if (nb >= 1024) {
         using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
-        k_block_merge<MG, PG::kConn8><<<grid_merge, MG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap, bound);
+        ok = launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms, local_cap,
+                       global_cap, bound) == cudaSuccess;
     } else {
-        k_block_merge<PG, PG::kConn8><<<grid_merge, PG::kThreads, 0, stream>>>(jt, ms, local_cap, global_cap,
-                                                                                  bound);
+        ok = launch_ex(k_block_merge<PG, PG::kConn8>, grid_merge, PG::kThreads, 0, stream, pdl, jt, ms, local_cap,
+                       global_cap, bound) == cudaSuccess;
     }
     ev = timing_mark(stream, ev, kKindMerge);
-    k_piece_write<PG><<<grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream>>>(jt, ps, global_cap, bound);
-    ev = timing_mark(stream, ev, kKindWrite);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    ok = ok && launch_ex(k_piece_write<PG>, grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream, pdl, jt, ps,
+                         global_cap, bound) == cudaSuccess;
+    ev = timing_mark(stream, ev, kKindPieceWrite);
+    return ok && cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class PG>

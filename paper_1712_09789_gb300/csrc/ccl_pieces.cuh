@@ -696,6 +696,8 @@ __global__ void __launch_bounds__(PG::kThreads) k_piece_local(JobTable jt, PScra
         process_plocal<PG>(job, sm.item.lb, sm.item.gb, s, sm, cap);
         __syncthreads();
     }
+    // the merge may be launched now (it waits for this grid's completion)
+    grid_launch_dependents();
 }
 
 // ---------------------------------------------------------------------------
@@ -731,16 +733,8 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
         uint4 *mo = reinterpret_cast<uint4 *>(&sm.m[0][0]);
         for (int q = t; q < PG::kBH * W / 4; q += T) mo[q] = mi[q];
     }
-    // final label of each border slot: root-find in the merged union-find
-    // (read-only; every union is complete when this kernel starts)
-    const int ns = s.nslots[b];
-    int err = 0;
-    for (int k = t; k < ns; k += T) {
-        uint32_t key;
-        find_global_ro(s.P, b * (uint32_t)PG::kSlots + (uint32_t)k, key, cap, err, bound);
-        sm.slot_label[k] = (int)key + 1;
-    }
-    report(err);
+    // the piece index tables, from step 1's outputs only (step 1 finished
+    // before the merge started)
     __syncthreads();
     band_tables<PG, false, false>(sm.m, sm.S, nullptr, nullptr, sm.pb, sm.bandcnt);
     __syncthreads();
@@ -753,6 +747,20 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
         sm.pb[k][w] = (uint16_t)(sm.pb[k][w] + sm.bb[k]);
     }
+    // the merge (step 2) may still be running when this kernel starts
+    // (programmatic dependent launch): wait for it before the first read of
+    // the merged union-find
+    grid_dependency_wait();
+    // final label of each border slot: root-find in the merged union-find
+    // (read-only; every union is complete after the wait)
+    const int ns = s.nslots[b];
+    int err = 0;
+    for (int k = t; k < ns; k += T) {
+        uint32_t key;
+        find_global_ro(s.P, b * (uint32_t)PG::kSlots + (uint32_t)k, key, cap, err, bound);
+        sm.slot_label[k] = (int)key + 1;
+    }
+    report(err);
     __syncthreads();
 
     const uint16_t *const vin = s.values + (size_t)b * PG::kMaxPieces;
