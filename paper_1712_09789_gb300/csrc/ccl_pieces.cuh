@@ -279,20 +279,13 @@ __device__ __forceinline__ uint32_t lowest_per_run(uint32_t R, uint32_t M, int w
 
 template <class PG>
 struct PLocalSmem {
+    static constexpr int kCandCap = 2048;  // union candidates per pass
     uint32_t m[PG::kBH][PG::kWords];      // row masks
     uint32_t S[PG::kBands][PG::kWords];   // piece starts
-    uint32_t E[PG::kBands][PG::kWords];   // piece ends
-    // contact events of band k with band k-1, at columns of band k's upper
-    // row (see band_events): D1, L and R events and the first event of
-    // every piece
-    uint32_t D1[PG::kBands][PG::kWords];
-    uint32_t EL[PG::kBands][PG::kWords];
-    uint32_t ER[PG::kBands][PG::kWords];
-    uint32_t FE[PG::kBands][PG::kWords];
     uint16_t pb[PG::kBands][PG::kWords];  // pieces of the band in earlier words
     uint16_t bandcnt[PG::kBands];
     uint16_t bb[PG::kBands + 1];          // pieces in earlier bands
-    alignas(16) uint16_t st[PG::kMaxPieces];  // band << kBWLog2 | first column of each piece
+    alignas(16) uint32_t cand[kCandCap];  // union candidates: piece << 16 | piece above
     uint16_t par[PG::kMaxPieces];         // label-equivalence list entries
     uint32_t border[PG::kMaxPieces / 32]; // bit per entry: root owning a block-border pixel
     uint32_t prefix[PG::kMaxPieces / 32]; // border roots in the words before
@@ -309,16 +302,22 @@ struct PLocalSmem {
 // the piece of band k-1 that holds c: an E1 event at c.  Otherwise the
 // touches at c-1 and c+1 are with two different pieces: L and R events at c.
 // Every E1 event of one run of (OR & ORu) joins the same two pieces, so D1
-// keeps the lowest E1 event of each such run.  FE is the first event of every
-// piece of band k (lowest bit of D1 | EL | ER per run of its OR).
-template <class PG>
-__device__ __forceinline__ void band_events(PLocalSmem<PG> &sm) {
+// keeps the lowest E1 event of each such run.  An L event at c whose column
+// c-1 holds an E1 event joins the same two pieces as that E1 event (c-1 and c
+// lie in one run of band k, c-1 in the run of band k-1 the L event names), so
+// it is dropped; likewise an R event next to an E1 event at c+1.  FE is the
+// first event of every piece of band k (lowest bit of D1 | EL | ER per run of
+// its OR), TA the first upper-row pixel of every piece (its smallest pixel,
+// when it has one).  Each thread keeps the masks of its items in registers:
+// every later pass over (band, word) items uses the same items.
+template <class PG, int kItems>
+__device__ __forceinline__ void band_events(const PLocalSmem<PG> &sm, uint32_t (&D1)[kItems], uint32_t (&EL)[kItems],
+                                            uint32_t (&ER)[kItems], uint32_t (&FE)[kItems], uint32_t (&TA)[kItems]) {
     constexpr int W = PG::kWords;
 #pragma unroll
-    for (int j = 0; j < PG::kBands * W / PG::kThreads; ++j) {
+    for (int j = 0; j < kItems; ++j) {
         const int item = threadIdx.x + j * PG::kThreads;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        uint32_t d1, el, er, fe;
         const int ku = k > 0 ? k - 1 : 0;
         const uint32_t A = sm.m[2 * k][w], B = sm.m[2 * k + 1][w], OR = A | B;
         const uint32_t Bu = k > 0 ? sm.m[2 * ku + 1][w] : 0u;
@@ -330,20 +329,18 @@ __device__ __forceinline__ void band_events(PLocalSmem<PG> &sm) {
         const uint32_t E1 = A & ORu & (Bu | BuL | BuR);
         // E1 of the neighbouring columns (bits from the neighbouring words)
         const uint32_t Al = w > 0 ? sm.m[2 * k][w - 1] : 0u, Ar = w + 1 < W ? sm.m[2 * k][w + 1] : 0u;
-        const uint32_t ORul = (k > 0 && w > 0) ? (sm.m[2 * ku][w - 1] | Bul) : 0u;
         const uint32_t ORur = (k > 0 && w + 1 < W) ? (sm.m[2 * ku][w + 1] | Bur) : 0u;
-        const uint32_t e1l = (Al >> 31) & (ORul >> 31) & 1u;   // E1 at column 32w-1 (Bu[32w-1] there: BuL bit 0)
+        // E1 at column 32w-1 under an L event at 32w (Bu there is set): A there
+        const uint32_t e1l = (Al >> 31) & (Bul >> 31) & 1u;
+        // E1 at column 32w+32 under an R event at 32w+31 (Bu there is set)
         const uint32_t e1r = Ar & ORur & 1u & (((Bur & 1u) | (Bu >> 31) | ((Bur >> 1) & 1u)) ? 1u : 0u);
-        const uint32_t E1l = (E1 << 1) | ((Bul >> 31) & e1l);   // bit c: E1[c-1] (an L event's upper column is c-1)
-        const uint32_t E1r = (E1 >> 1) | (e1r << 31);            // bit c: E1[c+1]
-        el = A & ~ORu & BuL & ~E1l;
-        er = A & ~ORu & BuR & ~E1r;
-        d1 = lowest_per_run<W>(OR & ORu, E1, w);
-        fe = lowest_per_run<W>(OR, d1 | el | er, w);
-        sm.D1[k][w] = d1;
-        sm.EL[k][w] = el;
-        sm.ER[k][w] = er;
-        sm.FE[k][w] = fe;
+        const uint32_t E1l = (E1 << 1) | e1l;         // bit c: E1[c-1]
+        const uint32_t E1r = (E1 >> 1) | (e1r << 31); // bit c: E1[c+1]
+        EL[j] = A & ~ORu & BuL & ~E1l;
+        ER[j] = A & ~ORu & BuR & ~E1r;
+        D1[j] = lowest_per_run<W>(OR & ORu, E1, w);
+        FE[j] = lowest_per_run<W>(OR, D1[j] | EL[j] | ER[j], w);
+        TA[j] = lowest_per_run<W>(OR, A, w);
     }
 }
 
@@ -459,25 +456,25 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
     __syncthreads();
     // -- row connection (the pieces, by bit operations) and the contact
     // events of every band with the band above
-    band_tables<PG, true, false>(sm.m, sm.S, sm.E, nullptr, sm.pb, sm.bandcnt);
-    band_events<PG>(sm);
+    band_tables<PG, false, false>(sm.m, sm.S, nullptr, nullptr, sm.pb, sm.bandcnt);
+    uint32_t evD1[kItems], evEL[kItems], evER[kItems], evFE[kItems], evTA[kItems];
+    band_events<PG, kItems>(sm, evD1, evEL, evER, evFE, evTA);
     __syncthreads();
     band_prefix<PG>(sm.bandcnt, sm.bb);
     __syncthreads();
     const int n = sm.bb[PG::kBands];
     volatile uint16_t *const vpar = sm.par;
     uint16_t *const par = sm.par;
-    // -- first column of every piece, and every entry a placeholder root
+    // -- every piece a root keyed by its first column in the band's lower row
+    // (its smallest pixel when it has none in the upper row)
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int item = t + j * T;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
         uint32_t sb = sm.S[k][w];
         int at = (int)sm.bb[k] + (int)sm.pb[k][w];
-        for (; sb; sb &= sb - 1u) {
-            sm.st[at] = (uint16_t)((k << PG::kBWLog2) | (32 * w + lobit(sb)));
-            vpar[at++] = 0xFFFFu;
-        }
+        const int rowkey = (2 * k + 1) << PG::kBWLog2;
+        for (; sb; sb &= sb - 1u) vpar[at++] = (uint16_t)(kRoot | (rowkey + 32 * w + lobit(sb)));
     }
     __syncthreads();
     // -- column connection (coarse labelling): the first event of a piece
@@ -487,10 +484,8 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
     for (int j = 0; j < kItems; ++j) {
         const int item = t + j * T;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        uint32_t fe = sm.FE[k][w];
-        if (!fe) continue;
-        const uint32_t d1 = sm.D1[k][w], el = sm.EL[k][w];
-        for (; fe; fe &= fe - 1u) {
+        const uint32_t d1 = evD1[j], el = evEL[j];
+        for (uint32_t fe = evFE[j]; fe; fe &= fe - 1u) {
             const int c = lobit(fe), col = 32 * w + c;
             const int q = piece_at<PG>(sm.S, sm.pb, sm.bb, k, col);
             const int uc = event_upper_col(col, (d1 >> c) & 1u, (el >> c) & 1u);
@@ -498,40 +493,40 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
         }
     }
     __syncthreads();
-    // -- pieces without any event are roots, keyed by their smallest pixel
-    for (int i = t; i < n; i += T) {
-        if (vpar[i] == 0xFFFFu) {
-            const int k = sm.st[i] >> PG::kBWLog2, a0 = sm.st[i] & (PG::kBW - 1);
-            vpar[i] = (uint16_t)(kRoot | pkey<PG>(sm.m, k, a0, piece_end_at<PG>(sm.E, k, a0)));
+    // -- a root with pixels in the band's upper row is keyed by the first
+    // of them
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int item = t + j * T;
+        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+        for (uint32_t ta = evTA[j]; ta; ta &= ta - 1u) {
+            const int col = 32 * w + lobit(ta);
+            const int q = piece_at<PG>(sm.S, sm.pb, sm.bb, k, col);
+            if (vpar[q] & kRoot) vpar[q] = (uint16_t)(kRoot | (((2 * k) << PG::kBWLog2) + col));
         }
     }
     __syncthreads();
-    // -- every entry to its root, in waves of T pieces in piece order (band
-    // order), so the parent of a piece has mostly been resolved by an
-    // earlier wave (read-only walks: every store is a root)
-    for (int i0 = 0; i0 < n; i0 += T) {
-        const int i = i0 + t;
-        if (i < n) {
-            const int r = pfind_ro(vpar, i, cap, err);
-            if (r != i) vpar[i] = (uint16_t)r;
-        }
-        __syncthreads();
+    // -- every entry to its root: finds with path halving (a halving store
+    // writes an ancestor, and every store after a find is a root of the
+    // forest of coarse links, which nothing else changes in this pass)
+    for (int i = t; i < n; i += T) {
+        uint16_t re;
+        const int r = pfind(vpar, i, re, cap, err);
+        if (r != i) vpar[i] = (uint16_t)r;
     }
+    __syncthreads();
     // -- refinement: every other event joins its two pieces; the CAS union
     // runs only where the roots their entries name differ.  The events are
-    // first packed into a list of (piece, piece above) pairs (in the space of
-    // the piece starts, no longer needed), so that every lane takes one per
-    // step.
+    // first packed into a list of (piece, piece above) pairs, so that every
+    // lane takes one per step.
     {
-        constexpr int kCand = PG::kMaxPieces / 2;  // pairs per pass
-        uint32_t* const cand = reinterpret_cast<uint32_t*>(sm.st);
+        constexpr int kCand = PLocalSmem<PG>::kCandCap;
+        uint32_t *const cand = sm.cand;
         uint32_t cnt[kItems], sum = 0;
 #pragma unroll
         for (int j = 0; j < kItems; ++j) {
-            const int item = t + j * T;
-            const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-            const uint32_t fe = sm.FE[k][w], el = sm.EL[k][w];
-            cnt[j] = __popc(sm.D1[k][w] & ~fe) + __popc(el & ~fe) + __popc(sm.ER[k][w] & ~(fe & ~el));
+            const uint32_t fe = evFE[j], el = evEL[j];
+            cnt[j] = __popc(evD1[j] & ~fe) + __popc(el & ~fe) + __popc(evER[j] & ~(fe & ~el));
             sum += cnt[j];
         }
         uint32_t incl = sum;
@@ -556,8 +551,8 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
                 const int item = t + j * T;
                 const int k = item >> PG::kWordsLog2, w = item & (W - 1);
                 if (at + cnt[j] > lo && at < hi) {
-                    const uint32_t fe = sm.FE[k][w], el = sm.EL[k][w];
-                    uint32_t ud = sm.D1[k][w] & ~fe, ul = el & ~fe, ur = sm.ER[k][w] & ~(fe & ~el);
+                    const uint32_t fe = evFE[j], el = evEL[j];
+                    uint32_t ud = evD1[j] & ~fe, ul = el & ~fe, ur = evER[j] & ~(fe & ~el);
                     uint32_t idx = at;
                     const int qb = (int)sm.bb[k] + (int)sm.pb[k][w] - 1;
                     for (; (ud | ul | ur) && idx < hi; ++idx) {
@@ -688,7 +683,7 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
 }
 
 template <class PG>
-__global__ void __launch_bounds__(PG::kThreads) k_piece_local(JobTable jt, PScratch s, int cap) {
+__global__ void __launch_bounds__(PG::kThreads, 5) k_piece_local(JobTable jt, PScratch s, int cap) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PLocalSmem<PG> &sm = *reinterpret_cast<PLocalSmem<PG> *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 0, iter, sm.item); ++iter) {
