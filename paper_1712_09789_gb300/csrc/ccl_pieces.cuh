@@ -480,16 +480,34 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
     // -- column connection (coarse labelling): the first event of a piece
     // names the piece above that becomes its parent (a smaller key, so the
     // entries form a forest; a plain store of the piece's own entry)
+    // (piece indices of the item's word and of the word above come from the
+    // item's own base and start mask: one popcount per event)
+    int qbase[kItems], ubase[kItems];
+    uint32_t Sw[kItems], Suw[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int item = t + j * T;
+        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+        qbase[j] = (int)sm.bb[k] + (int)sm.pb[k][w] - 1;
+        Sw[j] = sm.S[k][w];
+        ubase[j] = k > 0 ? (int)sm.bb[k - 1] + (int)sm.pb[k - 1][w] - 1 : 0;
+        Suw[j] = k > 0 ? sm.S[k - 1][w] : 0u;
+    }
+    // index of the piece above that event bit c (class d1 / el / er) joins
+    const auto upper_piece = [&](int j, int k, int w, int c, bool d1, bool el) -> int {
+        const int uc = event_upper_col(32 * w + c, d1, el);
+        if ((uc >> 5) == w) return ubase[j] + __popc(Suw[j] & upto(uc & 31));
+        return piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
+    };
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int item = t + j * T;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
         const uint32_t d1 = evD1[j], el = evEL[j];
         for (uint32_t fe = evFE[j]; fe; fe &= fe - 1u) {
-            const int c = lobit(fe), col = 32 * w + c;
-            const int q = piece_at<PG>(sm.S, sm.pb, sm.bb, k, col);
-            const int uc = event_upper_col(col, (d1 >> c) & 1u, (el >> c) & 1u);
-            vpar[q] = (uint16_t)piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
+            const int c = lobit(fe);
+            const int q = qbase[j] + __popc(Sw[j] & upto(c));
+            vpar[q] = (uint16_t)upper_piece(j, k, w, c, (d1 >> c) & 1u, (el >> c) & 1u);
         }
     }
     __syncthreads();
@@ -500,9 +518,9 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
         const int item = t + j * T;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
         for (uint32_t ta = evTA[j]; ta; ta &= ta - 1u) {
-            const int col = 32 * w + lobit(ta);
-            const int q = piece_at<PG>(sm.S, sm.pb, sm.bb, k, col);
-            if (vpar[q] & kRoot) vpar[q] = (uint16_t)(kRoot | (((2 * k) << PG::kBWLog2) + col));
+            const int c = lobit(ta);
+            const int q = qbase[j] + __popc(Sw[j] & upto(c));
+            if (vpar[q] & kRoot) vpar[q] = (uint16_t)(kRoot | (((2 * k) << PG::kBWLog2) + 32 * w + c));
         }
     }
     __syncthreads();
@@ -554,15 +572,15 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
                     const uint32_t fe = evFE[j], el = evEL[j];
                     uint32_t ud = evD1[j] & ~fe, ul = el & ~fe, ur = evER[j] & ~(fe & ~el);
                     uint32_t idx = at;
-                    const int qb = (int)sm.bb[k] + (int)sm.pb[k][w] - 1;
                     for (; (ud | ul | ur) && idx < hi; ++idx) {
-                        int c, uc;
-                        if (ud) { c = lobit(ud); ud &= ud - 1u; uc = 32 * w + c; }
-                        else if (ul) { c = lobit(ul); ul &= ul - 1u; uc = 32 * w + c - 1; }
-                        else { c = lobit(ur); ur &= ur - 1u; uc = 32 * w + c + 1; }
+                        int c;
+                        bool isd = false, isl = false;
+                        if (ud) { c = lobit(ud); ud &= ud - 1u; isd = true; }
+                        else if (ul) { c = lobit(ul); ul &= ul - 1u; isl = true; }
+                        else { c = lobit(ur); ur &= ur - 1u; }
                         if (idx < lo) continue;
-                        const int q = qb + __popc(sm.S[k][w] & upto(c));
-                        cand[idx - lo] = ((uint32_t)q << 16) | (uint32_t)piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
+                        const int q = qbase[j] + __popc(Sw[j] & upto(c));
+                        cand[idx - lo] = ((uint32_t)q << 16) | (uint32_t)upper_piece(j, k, w, c, isd, isl);
                     }
                 }
                 at += cnt[j];
@@ -825,7 +843,7 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
 }
 
 template <class PG>
-__global__ void __launch_bounds__(PG::kThreads) k_piece_write(JobTable jt, PScratch s, int cap, uint32_t bound) {
+__global__ void __launch_bounds__(PG::kThreads, 7) k_piece_write(JobTable jt, PScratch s, int cap, uint32_t bound) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PWriteSmem<PG> &sm = *reinterpret_cast<PWriteSmem<PG> *>(smem_raw);
     for (unsigned iter = 0; claim_item(jt, 2, iter, sm.item); ++iter) {
