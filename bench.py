@@ -377,28 +377,44 @@ def run_ours(args):
 
     if rank == 0 and not args.no_extra:
         extra = line.setdefault("extra", {})
+        only = set(args.only_extra.split(",")) if args.only_extra else None
+
+        def want(name):
+            return only is None or name in only
+
         # the 4096x4096 noise set, both connectivities
-        extra["noise_4096"] = bench_noise_4096(torch, ccl, hbm_gbs)
+        if want("noise_4096"):
+            extra["noise_4096"] = bench_noise_4096(torch, ccl, hbm_gbs)
         # single 512x512 and 4096x4096 images, L2 flushed and warm
-        extra["single_512"] = bench_single(torch, ccl, 512, hbm_gbs)
-        extra["single_4096"] = bench_single(torch, ccl, 4096, hbm_gbs)
+        if want("single_512"):
+            extra["single_512"] = bench_single(torch, ccl, 512, hbm_gbs)
+        if want("single_4096"):
+            extra["single_4096"] = bench_single(torch, ccl, 4096, hbm_gbs)
         # the uneven 256-image batch, batched graph vs plain launches
-        extra["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
+        if want("batched_256"):
+            extra["batched_256"] = bench_batched(torch, ccl, hbm_gbs)
         # the serving stream (Poisson arrivals of mixed-resolution host frames
         # through the continuous-batching server); it runs before the large
         # statistics and volume workloads, which leave the host and device
         # memory in a different state
-        extra["serving"] = bench_serving(torch, ccl, args.serving_seconds)
+        if want("serving"):
+            extra["serving"] = bench_serving(torch, ccl, args.serving_seconds)
         # the coarse-labelling variants of Sec. 4.2 (time and counters)
-        extra["variants"] = bench_variants(torch, ccl)
+        if want("variants"):
+            extra["variants"] = bench_variants(torch, ccl)
         # component statistics of the 8192^2 labels
-        extra["component_stats"] = bench_stats(torch, ccl)
+        if want("component_stats"):
+            extra["component_stats"] = bench_stats(torch, ccl)
         # 3D volumes (512^3 noise, 6- and 26-connectivity)
-        extra["volume_512"] = bench_volume(torch, ccl, hbm_gbs)
+        if want("volume_512"):
+            extra["volume_512"] = bench_volume(torch, ccl, hbm_gbs)
+        # strip sharding of the 8192^2 image, emulated on one GPU
+        if want("strips_8192"):
+            extra["strips_8192"] = bench_strips(torch, ccl)
 
     # -- the CPU oracle over the whole uneven batch on every host core (after
     # the GPU extras: its worker processes load the host)
-    if rank == 0 and world == 1 and not args.no_extra and not args.no_cpu:
+    if rank == 0 and world == 1 and "batched_256" in line.get("extra", {}) and not args.no_cpu:
         try:
             cores = oracle_all_cores(synth.batch_uneven(256, seed=0), 8)
         except Exception as exc:  # the CPU baseline must not cost the GPU numbers
@@ -697,6 +713,66 @@ def bench_stats(torch, ccl):
     return res
 
 
+def bench_strips(torch, ccl):
+    """Strip sharding emulated on one GPU: the 8192x8192 Bernoulli(0.5) image,
+    8-connectivity, cut into G strips that are labelled separately and joined
+    at their seams (ccl_strip_begin per strip, edge rows to the host,
+    ccl_strip_resolve, the seam map back, ccl_strip_finish per strip).  Host
+    clock around each part with the stream synchronised, median of 7 after 2
+    warm-ups; G = 1 is one plain ccl_label call for comparison.  On G GPUs
+    each would run one strip's begin and finish; that is not measured here."""
+    import numpy as np
+
+    from paper_1712_09789_gb300 import strips, synth
+
+    N = 8192
+    img = torch.from_numpy(synth.bernoulli(N, N, 0.5, 0)).cuda()
+    labels = torch.empty((N, N), dtype=torch.int32, device="cuda")
+    res = {"workload": "8192x8192 Bernoulli p=0.5 seed 0, 8-connectivity, strips on one GPU"}
+
+    def med(xs):
+        return sorted(xs)[len(xs) // 2]
+
+    ts = []
+    for i in range(9):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ccl.ccl_label(img, 8, labels=labels)
+        torch.cuda.synchronize()
+        if i >= 2:
+            ts.append((time.perf_counter() - t0) * 1e3)
+    res["G1_plain_ms"] = med(ts)
+    want = labels.clone()
+    for G in (2, 4, 8):
+        bounds = strips.strip_bounds(N, G)
+        wss = [torch.empty(ccl.ccl_workspace_size(h, N, 8), dtype=torch.uint8, device="cuda") for _, h in bounds]
+        parts = {"begin": [], "exchange_resolve": [], "finish": [], "total": []}
+        pairs = None
+        for i in range(9):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            edges = [ccl.ccl_strip_begin(img[y0:y0 + h], y0, N, ws, 8) for (y0, h), ws in zip(bounds, wss)]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            pairs = ccl.ccl_strip_resolve(torch.stack(edges).cpu().numpy(), 8)
+            seam = torch.from_numpy(pairs.view(np.int32)).cuda() if len(pairs) else None
+            t2 = time.perf_counter()
+            for (y0, h), ws in zip(bounds, wss):
+                ccl.ccl_strip_finish(h, N, y0, N, seam, ws, 8, labels[y0:y0 + h])
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            if i >= 2:
+                parts["begin"].append((t1 - t0) * 1e3)
+                parts["exchange_resolve"].append((t2 - t1) * 1e3)
+                parts["finish"].append((t3 - t2) * 1e3)
+                parts["total"].append((t3 - t0) * 1e3)
+        status = ccl.ccl_get_device_status()
+        res[f"G{G}"] = {**{f"{k}_ms": med(v) for k, v in parts.items()}, "seam_pairs": int(len(pairs)),
+                        "same_labels_as_plain": bool(torch.equal(labels, want)),
+                        "device_status": ccl.ccl_status_string(status)}
+    return res
+
+
 def bench_volume(torch, ccl, hbm_gbs):
     """3D labelling (ccl_label_3d) of 512^3 Bernoulli volumes, seed 0: p = 0.3
     (near the 6-connected percolation threshold) and 0.5, both
@@ -871,6 +947,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-extra", action="store_true")
+    ap.add_argument("--only-extra", default="", help="comma-separated names of the extras to run")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=3.0)

@@ -383,6 +383,53 @@ ccl_status ccl_label_3d(const uint8_t *img, int D, int H, int W, size_t pitch, i
                         int32_t *labels, void *stream);
 
 /*
+ * Strip sharding of one image (Sec. 3.2's boundary analysis at the seams of
+ * horizontal strips labelled separately, e.g. one strip per GPU).  Strip g is
+ * rows [y0_g, y0_g + H_g) of an H_total x W image.  Each strip starts on a
+ * multiple of 64 rows, and every strip but the last has a multiple of 64 rows
+ * (the seams sit between block rows); H_total * W <= 2^31 - 2.  Per strip:
+ *
+ *   1. ccl_strip_begin(): step 1 and the block merge of the strip, with every
+ *      key a raster position of the whole image, then its edge rows:
+ *      edges[x] and edges[W + x] (device, uint32 [2][W]) = the smallest
+ *      position, within the strip, of the component holding pixel x of the
+ *      strip's first / last row; 0xFFFFFFFF for background.  `img` is the
+ *      strip's first row (device, u8, row stride pitch), `workspace` as for
+ *      ccl_label_ws() with the strip's H and W; it carries the strip's state
+ *      until ccl_strip_finish().
+ *   2. The caller gathers the edge rows of all strips in strip order into a
+ *      host array of uint32 [strips][2][W] (an all-gather across GPUs).
+ *   3. ccl_strip_resolve() (host only, no CUDA call): joins the keys of every
+ *      pair of foreground pixels adjacent across a seam (the last row of strip
+ *      g and the first row of strip g+1) and writes to `map` (host, uint32
+ *      pairs) every key whose component reaches a smaller key through the
+ *      seams, with the smallest such key, sorted by key.  *count = number of
+ *      pairs; CCL_ERR_INVALID_ARG when it exceeds `capacity` (pairs) -- call
+ *      with capacity 0 to size it.  At most 2 * (strips - 1) * W pairs.  Every
+ *      strip computes the same map from the same gathered rows.
+ *   4. ccl_strip_finish(): `map` (device copy of the pairs, `count` of them)
+ *      is applied to the strip's union-find roots, then the write-out fills
+ *      `labels` (device, int32 [H][W] of the strip) with the labels of the
+ *      whole image: 1 + the smallest position of the component over all strips.
+ *
+ * Arguments of begin and finish for one strip must agree (H, W,
+ * connectivity, y0, H_total, workspace).  Errors: CCL_ERR_INVALID_ARG for
+ * NULL pointers, negative sizes, a strip off the 64-row grid, a strip outside
+ * the image or a workspace that is NULL, misaligned or too small;
+ * CCL_ERR_UNSUPPORTED when H_total * W > 2^31 - 2; CCL_ERR_CUDA when a launch
+ * fails.  An iteration cap reached on the device is reported by
+ * ccl_get_device_status().
+ */
+ccl_status ccl_strip_begin(const uint8_t *img, int H, int W, size_t pitch, int connectivity, int y0,
+                           int H_total, void *workspace, size_t workspace_bytes, uint32_t *edges,
+                           void *stream);
+ccl_status ccl_strip_resolve(const uint32_t *edges, int strips, int W, int connectivity, uint32_t *map,
+                             size_t capacity, size_t *count);
+ccl_status ccl_strip_finish(int H, int W, int connectivity, int y0, int H_total, const uint32_t *map,
+                            size_t count, int32_t *labels, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/*
  * Test hook for failure detection: caps every find/union loop in the kernels
  * at `cap` iterations (cap <= 0 restores the default, which no valid input
  * can reach).  A low cap makes the loops give up, set the device error word

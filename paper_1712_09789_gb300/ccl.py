@@ -109,6 +109,12 @@ _SIGS = {
     "ccl_server_reset_stats": (_c.c_int, [_c.c_void_p]),
     "ccl_server_destroy": (None, [_c.c_void_p]),
     "ccl_tile_name": (_c.c_char_p, [_c.c_int]),
+    "ccl_strip_begin": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_size_t, _c.c_int, _c.c_int, _c.c_int,
+                                   _c.c_void_p, _c.c_size_t, _c.c_void_p, _c.c_void_p]),
+    "ccl_strip_resolve": (_c.c_int, [_c.c_void_p, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                     _c.POINTER(_c.c_size_t)]),
+    "ccl_strip_finish": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_void_p, _c.c_size_t,
+                                    _c.c_void_p, _c.c_void_p, _c.c_size_t, _c.c_void_p]),
     "ccl_debug_set_iteration_cap": (None, [_c.c_int]),
     "ccl_debug_kernel_timing": (None, [_c.c_int]),
     "ccl_debug_kernel_times": (_c.c_int, [_c.POINTER(_c.c_double), _c.POINTER(_c.c_longlong), _c.c_int]),
@@ -322,6 +328,64 @@ def ccl_label_ws(img, workspace, connectivity: int = 8, labels=None, stream=None
     st = _call("ccl_label_ws", img.device, img.data_ptr(), H, W, pitch, connectivity, labels.data_ptr(),
                              workspace.data_ptr(), nbytes, _stream_ptr(stream, img.device))
     _check(st, "ccl_label_ws")
+    return labels
+
+
+def ccl_strip_begin(img, y0: int, H_total: int, workspace, connectivity: int = 8, edges=None, stream=None):
+    """First half of a strip's labelling (``ccl_strip_begin``): `img` is rows
+    [y0, y0 + H) of an H_total-row image.  Returns the strip's edge rows, an
+    int32 device tensor [2, W] holding the uint32 keys (0xFFFFFFFF, i.e. -1,
+    for background)."""
+    import torch
+
+    H, W, pitch = _image_args(img)
+    if edges is None:
+        edges = torch.empty((2, W), dtype=torch.int32, device=img.device)
+    elif edges.dtype != torch.int32 or tuple(edges.shape) != (2, W) or not edges.is_contiguous():
+        raise ValueError("edges must be a contiguous int32 tensor [2, W]")
+    nbytes = workspace.numel() * workspace.element_size()
+    st = _call("ccl_strip_begin", img.device, img.data_ptr(), H, W, pitch, connectivity, y0, H_total,
+               workspace.data_ptr(), nbytes, edges.data_ptr(), _stream_ptr(stream, img.device))
+    _check(st, "ccl_strip_begin")
+    return edges
+
+
+def ccl_strip_resolve(edges_all: np.ndarray, connectivity: int = 8) -> np.ndarray:
+    """Seam equivalences of gathered edge rows (``ccl_strip_resolve``, host
+    only): `edges_all` is uint32 (or int32 bits) [strips, 2, W] in strip order.
+    Returns a uint32 array [n, 2] of (key, smallest key) sorted by key."""
+    e = np.ascontiguousarray(edges_all).view(np.uint32)
+    if e.ndim != 3 or e.shape[1] != 2:
+        raise ValueError("edges_all must have shape [strips, 2, W]")
+    G, _, W = e.shape
+    n = ctypes.c_size_t(0)
+    # at most one pair per pixel of the seam rows
+    out = np.empty((max(2 * (G - 1) * W, 1), 2), dtype=np.uint32)
+    st = load().ccl_strip_resolve(e.ctypes.data, G, W, connectivity, out.ctypes.data, out.shape[0],
+                                  ctypes.byref(n))
+    _check(st, "ccl_strip_resolve")
+    return out[:n.value]
+
+
+def ccl_strip_finish(H: int, W: int, y0: int, H_total: int, seam_map, workspace, connectivity: int = 8,
+                     labels=None, stream=None):
+    """Second half of a strip's labelling (``ccl_strip_finish``): `seam_map`
+    is the device copy (int32 bits, [n, 2]) of ``ccl_strip_resolve``'s pairs.
+    Writes and returns the strip's labels (labels of the whole image)."""
+    import torch
+
+    dev = workspace.device
+    if labels is None:
+        labels = torch.empty((H, W), dtype=torch.int32, device=dev)
+    elif labels.dtype != torch.int32 or tuple(labels.shape) != (H, W) or not labels.is_contiguous():
+        raise ValueError("labels must be a contiguous int32 tensor [H, W]")
+    n = 0 if seam_map is None else int(seam_map.shape[0])
+    if n and (seam_map.dtype != torch.int32 or not seam_map.is_contiguous() or seam_map.device != dev):
+        raise ValueError("seam_map must be a contiguous int32 tensor on the workspace's device")
+    nbytes = workspace.numel() * workspace.element_size()
+    st = _call("ccl_strip_finish", dev, H, W, connectivity, y0, H_total, seam_map.data_ptr() if n else None, n,
+               labels.data_ptr(), workspace.data_ptr(), nbytes, _stream_ptr(stream, dev))
+    _check(st, "ccl_strip_finish")
     return labels
 
 

@@ -298,10 +298,11 @@ const char *ccl_debug_kernel_name(int kind) { return ccl::kernel_kind_name(kind)
 
 ccl_status ccl_get_device_status(void *stream) {
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return CCL_ERR_CUDA;
-    int v = 0, vv = 0;
+    int v = 0, vv = 0, vs = 0;
     if (ccl::read_and_clear_device_error(&v) != 0) return CCL_ERR_CUDA;
     if (ccl::read_and_clear_volume_error(&vv) != 0) return CCL_ERR_CUDA;
-    return (v | vv) ? CCL_ERR_DEVICE_TIMEOUT : CCL_OK;
+    if (ccl::read_and_clear_strip_error(&vs) != 0) return CCL_ERR_CUDA;
+    return (v | vv | vs) ? CCL_ERR_DEVICE_TIMEOUT : CCL_OK;
 }
 
 ccl_status ccl_label_3d(const uint8_t *img, int D, int H, int W, size_t pitch, int connectivity, int32_t *labels,

@@ -152,6 +152,8 @@ ccl_status prepare(const ccl_image *images, int n, int conn, int geo, Prepared &
         j.nbx = (im.W + bw - 1) / bw;
         j.nby = (im.H + bh - 1) / bh;
         j.block0 = (unsigned)out.blocks;
+        j.key0 = 0;
+        j.pad = 0;
         j.flags = ((((uintptr_t)im.img | im.pitch) & 15) == 0 ? ccl::kJobVecIn : 0u) |
                   ((((uintptr_t)im.labels & 15) == 0 && (im.W & 3) == 0) ? ccl::kJobVecOut : 0u);
         out.blocks += (size_t)j.nbx * (size_t)j.nby;

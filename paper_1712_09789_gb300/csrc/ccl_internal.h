@@ -21,6 +21,10 @@ struct Job {
     int nbx, nby;
     unsigned block0;
     unsigned flags;
+    // raster position of the image's pixel (0, 0) within a larger image: 0
+    // for a whole image, y0 * W for a strip whose first row is row y0
+    unsigned key0;
+    unsigned pad;
 };
 
 // Device header in front of a batch's job array.  The counters are the work
@@ -69,6 +73,27 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap);
 
+// Strip sharding (ccl_strip.cu).  launch_label_phases() runs the kernels of
+// launch_label() selected by `phases` on an image whose pixel (0, 0) has
+// raster position key0 in the whole image: kPhaseLocalMerge = step 1 and the
+// block merge, kPhaseWrite = the write-out (on the same `ws`, later).
+constexpr int kPhaseLocalMerge = 1, kPhaseWrite = 2;
+int launch_label_phases(const uint8_t *img, int H, int W, size_t pitch, int conn, uint32_t key0, int32_t *labels,
+                        void *ws, cudaStream_t stream, int cap, int phases);
+// Blocks of 512 x 64 pixels; each keeps a border record of kStripEdge slot
+// numbers (top row, bottom row, left column, right column; kStripNoSlot for
+// background) and kStripSlots union-find entries (key << 32 | parent).
+constexpr int kStripBW = 512, kStripBH = 64, kStripSlots = 576, kStripEdge = 1152, kStripEdgeBottom = 512;
+constexpr uint16_t kStripNoSlot = 0xFFFF;
+struct ScratchView {
+    uint16_t *edges;   // [blocks][kStripEdge]
+    uint64_t *P;       // [blocks][kStripSlots]
+    int32_t *nslots;   // [blocks]
+    unsigned nbx, nby;
+};
+// Where launch_label() keeps those records in `ws` for an H x W image.
+int label_scratch_view(int H, int W, int conn, void *ws, ScratchView *v);
+
 // The coarse-labelling variants of Sec. 4.2 (mode 0 C2FL, 1 RC2FL, 2 CC2FL,
 // 3 NC2FL) with counters, on 512x64 blocks; scratch of
 // variant_workspace_bytes(H, W).  variant_counters reads the accumulated
@@ -99,6 +124,7 @@ int release_batched_stream(int dev, cudaStream_t stream);
 // Reads the current device's error word and clears it.  Returns 0 or -1.
 int read_and_clear_device_error(int *value);
 int read_and_clear_volume_error(int *value);
+int read_and_clear_strip_error(int *value);
 
 // Argument checks and iteration cap of the C ABI, for entry points that live
 // in other translation units (same rules as ccl_label()).

@@ -524,7 +524,7 @@ __device__ __forceinline__ void process_local(const Job &job, unsigned lb, unsig
             for (; bits && slot < (uint32_t)G::kSlots; bits &= bits - 1, ++slot) {
                 const int at = word * 32 + lobit(bits);
                 const int key = vpar[at] & 0x7FFF;
-                const uint32_t g = (uint32_t)(y0 + (key >> G::kBWLog2)) * (uint32_t)W +
+                const uint32_t g = job.key0 + (uint32_t)(y0 + (key >> G::kBWLog2)) * (uint32_t)W +
                                    (uint32_t)(x0 + (key & (G::kBW - 1)));
                 s.P[sbase + slot] = pack_slot(g, sbase + slot);
                 // from here on the root's entry is its slot (kBorderRoot | slot)
@@ -817,6 +817,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
     const int H = job.H, W = job.W;
     int32_t *const labels = job.labels;
     const bool vec_out = (job.flags & kJobVecOut) != 0;
+    const uint32_t key0 = job.key0;
     const int x0 = bx * G::kBW, y0 = by * G::kBH;
     const int t = threadIdx.x;
     const int tx = t & (G::BLX - 1), ty = t >> G::kBLXLog2;
@@ -875,7 +876,7 @@ __device__ __forceinline__ void process_write(const Job &job, unsigned lb, unsig
             ++vi;
             const uint32_t slot = v & 0x7FFFu;
             const int lab = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
-                                               : (int)((uint32_t)(y0 + (int)(v >> G::kBWLog2)) * (uint32_t)W +
+                                               : (int)(key0 + (uint32_t)(y0 + (int)(v >> G::kBWLog2)) * (uint32_t)W +
                                                        (uint32_t)(x0 + (int)(v & (G::kBW - 1)))) + 1;
             sm.runlab[ty][runlab_index<G>(tx, a0)] = lab;
         }
@@ -1183,33 +1184,39 @@ void caps_for(size_t nb, int cap, int &local_cap, int &global_cap, uint32_t &bou
     bound = (uint32_t)slots;
 }
 
-// The labelling kernel (step 1), the merge (step 2) and the write-out (step 3).
+// The labelling kernel (step 1), the merge (step 2) and the write-out (step
+// 3); `phases` selects kPhaseLocalMerge and/or kPhaseWrite.
 template <class G>
 int launch_table(int conn, const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
-                 const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream) {
+                 const Scratch &s, int local_cap, int global_cap, uint32_t bound, cudaStream_t stream,
+                 int phases = kPhaseLocalMerge | kPhaseWrite) {
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     if (conn == 8) {
-        k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<true, 0, G::kLH>::kCap>), stream>>>(
-            jt, s, local_cap);
-        ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<G, true><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
-        ev = timing_mark(stream, ev, kKindMerge);
-        k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
+        if (phases & kPhaseLocalMerge) {
+            k_block_local<G, true><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<true, 0, G::kLH>::kCap>),
+                                     stream>>>(jt, s, local_cap);
+            ev = timing_mark(stream, ev, kKindLocal);
+            k_block_merge<G, true><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
+            ev = timing_mark(stream, ev, kKindMerge);
+        }
+        if (phases & kPhaseWrite) k_block_write<G, true><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     } else {
-        k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<false, 0, G::kLH>::kCap>), stream>>>(
-            jt, s, local_cap);
-        ev = timing_mark(stream, ev, kKindLocal);
-        k_block_merge<G, false><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
-        ev = timing_mark(stream, ev, kKindMerge);
-        k_block_write<G, false><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
+        if (phases & kPhaseLocalMerge) {
+            k_block_local<G, false><<<grid_local, G::kThreads, sizeof(LocalSmem<G, Variant<false, 0, G::kLH>::kCap>),
+                                      stream>>>(jt, s, local_cap);
+            ev = timing_mark(stream, ev, kKindLocal);
+            k_block_merge<G, false><<<grid_merge, G::kThreads, 0, stream>>>(jt, s, local_cap, global_cap, bound);
+            ev = timing_mark(stream, ev, kKindMerge);
+        }
+        if (phases & kPhaseWrite) k_block_write<G, false><<<grid_write, G::kThreads, 0, stream>>>(jt, s, global_cap, bound);
     }
-    ev = timing_mark(stream, ev, kKindWrite);
+    if (phases & kPhaseWrite) ev = timing_mark(stream, ev, kKindWrite);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class G>
 int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
-                  cudaStream_t stream, int cap) {
+                  cudaStream_t stream, int cap, uint32_t key0 = 0, int phases = kPhaseLocalMerge | kPhaseWrite) {
     GeoLaunch gl;
     if (!geo_launch<G>(gl)) return -1;
     JobTable jt{};
@@ -1223,6 +1230,7 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
     jt.single.nbx = (W + G::kBW - 1) / G::kBW;
     jt.single.nby = (H + G::kBH - 1) / G::kBH;
     jt.single.block0 = 0;
+    jt.single.key0 = key0;
     jt.single.flags = ((((uintptr_t)img | pitch) & 15) == 0 ? kJobVecIn : 0u) |
                       ((((uintptr_t)labels & 15) == 0 && (W & 3) == 0) ? kJobVecOut : 0u);
     const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
@@ -1231,7 +1239,7 @@ int launch_single(const uint8_t *img, int H, int W, size_t pitch, int conn, int3
     uint32_t bound;
     caps_for<G>(nb, cap, local_cap, global_cap, bound);
     return launch_table<G>(conn, jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve<G>(ws, nb), local_cap,
-                           global_cap, bound, stream);
+                           global_cap, bound, stream, phases);
 }
 
 // Launches `kernel` on `stream`; with `pdl` as a programmatic dependent
@@ -1293,7 +1301,8 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
 // and step 3 (piece write-out) over the jobs of `jt`.
 template <class PG>
 int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
-                       const PScratch &ps, size_t nb, int cap, cudaStream_t stream) {
+                       const PScratch &ps, size_t nb, int cap, cudaStream_t stream,
+                       int phases = kPhaseLocalMerge | kPhaseWrite) {
     const int local_cap = cap > 0 ? cap : PG::kMaxPieces + 16;
     const long long slots = (long long)nb * PG::kSlots;
     const int global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
@@ -1305,31 +1314,37 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
     cudaEvent_t ev = timing_mark(stream, nullptr, -1);
     // per-kernel timing records events between the kernels, which a
     // programmatic (overlapping) launch would blur: off while timing
-    const bool pdl = ev == nullptr;
-    k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
-    ev = timing_mark(stream, ev, kKindPieceLocal);
-    // the merge of many blocks runs on 128 threads per block (more blocks
-    // per SM for its latency-bound unions), that of fewer on 256 (a shorter
-    // chain per block)
+    // (and only between kernels of one call)
+    const bool pdl = ev == nullptr && phases == (kPhaseLocalMerge | kPhaseWrite);
     bool ok = true;
-    if (nb >= 1024) {
-        using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
-        ok = launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms, local_cap,
-                       global_cap, bound) == cudaSuccess;
-    } else {
-        ok = launch_ex(k_block_merge<PG, PG::kConn8>, grid_merge, PG::kThreads, 0, stream, pdl, jt, ms, local_cap,
-                       global_cap, bound) == cudaSuccess;
+    if (phases & kPhaseLocalMerge) {
+        k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
+        ev = timing_mark(stream, ev, kKindPieceLocal);
+        // the merge of many blocks runs on 128 threads per block (more blocks
+        // per SM for its latency-bound unions), that of fewer on 256 (a shorter
+        // chain per block)
+        if (nb >= 1024) {
+            using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
+            ok = launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms,
+                           local_cap, global_cap, bound) == cudaSuccess;
+        } else {
+            ok = launch_ex(k_block_merge<PG, PG::kConn8>, grid_merge, PG::kThreads, 0, stream, pdl, jt, ms,
+                           local_cap, global_cap, bound) == cudaSuccess;
+        }
+        ev = timing_mark(stream, ev, kKindMerge);
     }
-    ev = timing_mark(stream, ev, kKindMerge);
-    ok = ok && launch_ex(k_piece_write<PG>, grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream, pdl, jt, ps,
-                         global_cap, bound) == cudaSuccess;
-    ev = timing_mark(stream, ev, kKindPieceWrite);
+    if (phases & kPhaseWrite) {
+        ok = ok && launch_ex(k_piece_write<PG>, grid_write, PG::kThreads, sizeof(PWriteSmem<PG>), stream, pdl, jt,
+                             ps, global_cap, bound) == cudaSuccess;
+        ev = timing_mark(stream, ev, kKindPieceWrite);
+    }
     return ok && cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 template <class PG>
 int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
-                        cudaStream_t stream, int cap) {
+                        cudaStream_t stream, int cap, uint32_t key0 = 0,
+                        int phases = kPhaseLocalMerge | kPhaseWrite) {
     int occ_l = 0, occ_w = 0, sms = 0;
     if (!piece_prepare<PG>(occ_l, occ_w, sms)) return -1;
     JobTable jt{};
@@ -1341,12 +1356,13 @@ int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t 
     jt.single.nbx = (W + PG::kBW - 1) / PG::kBW;
     jt.single.nby = (H + PG::kBH - 1) / PG::kBH;
     jt.single.block0 = 0;
+    jt.single.key0 = key0;
     jt.single.flags = ((((uintptr_t)img | pitch) & 15) == 0 ? kJobVecIn : 0u) |
                       ((((uintptr_t)labels & 15) == 0 && (W & 3) == 0) ? kJobVecOut : 0u);
     const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
     jt.total = (unsigned)nb;
     return launch_piece_table<PG>(jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve_p<PG>(ws, nb), nb, cap,
-                                  stream);
+                                  stream, phases);
 }
 
 template <class G>
@@ -1460,6 +1476,29 @@ int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32
                  cudaStream_t stream, int cap) {
     if (conn == 8) return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap);
     return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
+}
+
+int launch_label_phases(const uint8_t *img, int H, int W, size_t pitch, int conn, uint32_t key0, int32_t *labels,
+                        void *ws, cudaStream_t stream, int cap, int phases) {
+    if (conn == 8) return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, key0, phases);
+    return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap, key0, phases);
+}
+
+int label_scratch_view(int H, int W, int conn, void *ws, ScratchView *v) {
+    const size_t nb = blocks_of<G0>(H, W);
+    char *p = static_cast<char *>(ws);
+    const Layout l = conn == 8 ? layout_p<P8>(nb) : layout_for<G0>(nb);
+    v->edges = reinterpret_cast<uint16_t *>(p + l.edges);
+    v->P = reinterpret_cast<uint64_t *>(p + l.P);
+    v->nslots = reinterpret_cast<int32_t *>(p + l.nslots);
+    v->nbx = (unsigned)((W + G0::kBW - 1) / G0::kBW);
+    v->nby = (unsigned)((H + G0::kBH - 1) / G0::kBH);
+    static_assert(P8::kSlots == G0::kSlots && P8::kEdge == G0::kEdge && P8::kEdgeBottom == G0::kEdgeBottom,
+                  "both block kinds keep the same border records");
+    static_assert(G0::kBW == kStripBW && G0::kBH == kStripBH && G0::kSlots == kStripSlots &&
+                      G0::kEdge == kStripEdge && G0::kEdgeBottom == kStripEdgeBottom,
+                  "strip constants");
+    return 0;
 }
 
 int prepare_geo(int geo) {

@@ -666,7 +666,7 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
             for (; bits && slot < (uint32_t)PG::kSlots; bits &= bits - 1, ++slot) {
                 const int at = word * 32 + lobit(bits);
                 const int key = vpar[at] & 0x7FFF;
-                const uint32_t g = (uint32_t)(y0 + (key >> PG::kBWLog2)) * (uint32_t)Wd +
+                const uint32_t g = job.key0 + (uint32_t)(y0 + (key >> PG::kBWLog2)) * (uint32_t)Wd +
                                    (uint32_t)(x0 + (key & (PG::kBW - 1)));
                 s.P[sbase + slot] = pack_slot(g, sbase + slot);
                 // from here on the root's entry is its slot (kBorderRoot | slot)
@@ -738,6 +738,7 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     const int H = job.H, Wd = job.W;
     int32_t *const labels = job.labels;
     const bool vec_out = (job.flags & kJobVecOut) != 0;
+    const uint32_t key0 = job.key0;
     const int x0 = bx * PG::kBW, y0 = by * PG::kBH;
     const int t = threadIdx.x;
 
@@ -786,7 +787,7 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
             const uint32_t v = vin[p0 + i];
             const uint32_t slot = v & 0x7FFFu;
             sm.lab[i] = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
-                                          : (int)((uint32_t)(y0 + (int)(v >> PG::kBWLog2)) * (uint32_t)Wd +
+                                          : (int)(key0 + (uint32_t)(y0 + (int)(v >> PG::kBWLog2)) * (uint32_t)Wd +
                                                   (uint32_t)(x0 + (int)(v & (PG::kBW - 1)))) + 1;
         }
         __syncthreads();

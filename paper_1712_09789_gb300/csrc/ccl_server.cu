@@ -390,6 +390,8 @@ ccl_status launch(ccl_server *s, Batch *b) {
         j.nbx = (r->W + bw - 1) / bw;
         j.nby = (r->H + bh - 1) / bh;
         j.block0 = block0;
+        j.key0 = 0;
+        j.pad = 0;
         // arena ranges are 256-byte aligned and dpitch a multiple of 16
         j.flags = ccl::kJobVecIn | ((r->W & 3) == 0 ? ccl::kJobVecOut : 0u);
         block0 += (unsigned)j.nbx * (unsigned)j.nby;
