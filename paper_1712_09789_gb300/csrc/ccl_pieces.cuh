@@ -13,18 +13,18 @@
 // Step 1 (Kernel 1, Sec. 3.1).  The label-equivalence list of the block has
 // one 16-bit entry per piece: kRoot | key for a root (key = block raster
 // position of the component's smallest pixel), else the index of its parent.
-// Each warp owns a group of consecutive bands and places them in order; its
-// lanes stride over a band's pieces.  Column connection: a piece touching
-// the band above takes the root of the first piece it touches there as its
-// parent (plain store: no other thread writes that entry).  Refinement: every
-// further piece above that it touches is merged with a warp-synchronous CAS
-// union (links from the larger key to the smaller, Sec. 3.1.3).  The first
-// band of each group is linked to the group above only after every group is
-// placed (the same unions), then every entry is compressed to its root.
-// Roots owning a block-border pixel get a border slot and a global union-find
-// entry keyed by their minimum global raster position (ID conversion,
-// Sec. 3.1.4).  Outputs: the row masks, one 16-bit value per piece (border
-// slot or block key of its root), the border record and the slot entries.
+// Every thread keeps two (band, word) items.  The contact events of each band
+// with the band above are found for 32 columns at once by bit operations, one
+// event per (piece, piece above) pair.  Column connection: the first event of
+// a piece makes the piece above its parent (plain store: no other thread
+// writes that entry); a piece without events is a root keyed by its smallest
+// pixel.  Refinement: every further event joins its two pieces with a
+// warp-synchronous CAS union (links from the larger key to the smaller, Sec.
+// 3.1.3), then every entry is compressed to its root.  Roots owning a
+// block-border pixel get a border slot and a global union-find entry keyed by
+// their minimum global raster position (ID conversion, Sec. 3.1.4).
+// Outputs: the row masks, one 16-bit value per piece (border slot or block
+// key of its root), the border record and the slot entries.
 //
 // Step 3 (Sec. 3.3).  The write-out rebuilds the piece index of every column
 // from the masks, decodes the piece values into labels in shared memory
@@ -192,11 +192,18 @@ __device__ __forceinline__ int pfind(volatile uint16_t *par, int x, uint16_t &re
     return x;
 }
 
-__device__ __forceinline__ int pfind_ro(const volatile uint16_t *par, int x, int cap, int &err) {
+// Root of x with path halving by CAS: a halving store lands only while the
+// entry still holds the parent the walk read, so it never overwrites a later
+// store of the entry's root.
+__device__ __forceinline__ int pfind_cas(uint16_t *par, int x, int cap, int &err) {
+    volatile uint16_t *vp = par;
     for (int i = 0; i < cap; ++i) {
-        const uint16_t e = par[x];
-        if (e & (kRoot | kBorderRoot)) return x;
-        x = e;
+        const uint16_t e = vp[x];
+        if (e & kRoot) return x;
+        const uint16_t g = vp[e];
+        if (g & kRoot) return e;
+        atomicCAS(reinterpret_cast<unsigned short *>(par + x), (unsigned short)e, (unsigned short)g);
+        x = g;
     }
     err |= kErrLocalCap;
     return x;
@@ -305,14 +312,25 @@ struct PLocalSmem {
 // keeps the lowest E1 event of each such run.  An L event at c whose column
 // c-1 holds an E1 event joins the same two pieces as that E1 event (c-1 and c
 // lie in one run of band k, c-1 in the run of band k-1 the L event names), so
-// it is dropped; likewise an R event next to an E1 event at c+1.  FE is the
-// first event of every piece of band k (lowest bit of D1 | EL | ER per run of
-// its OR), TA the first upper-row pixel of every piece (its smallest pixel,
-// when it has one).  Each thread keeps the masks of its items in registers:
+// it is dropped; likewise an R event next to an E1 event at c+1.
+//
+// A piece P of band k and a piece U of band k-1 meet in at most one run of
+// (OR & ORu) (the overlap of two intervals), and an R event names U only at
+// the column before U's first column, an L event only after its last.  So one
+// event per (P, U) pair remains when (a) the D1 event of a run is dropped if
+// an R event seeds the run's first column, and (b) an L event is dropped if
+// the run of (OR & ORu) ending next to it holds a kept D1 or R seed (the fill
+// R & ~(R + seed) marks a run from its seed to its last column).
+//
+// FE is the first event of every piece of band k (lowest bit of D1 | EL | ER
+// per run of its OR), TA the first upper-row pixel of every piece (its
+// smallest pixel, when it has one) and RE the last column of every piece
+// without events.  Each thread keeps the masks of its items in registers:
 // every later pass over (band, word) items uses the same items.
 template <class PG, int kItems>
 __device__ __forceinline__ void band_events(const PLocalSmem<PG> &sm, uint32_t (&D1)[kItems], uint32_t (&EL)[kItems],
-                                            uint32_t (&ER)[kItems], uint32_t (&FE)[kItems], uint32_t (&TA)[kItems]) {
+                                            uint32_t (&ER)[kItems], uint32_t (&FE)[kItems], uint32_t (&TA)[kItems],
+                                            uint32_t (&RE)[kItems]) {
     constexpr int W = PG::kWords;
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
@@ -336,11 +354,25 @@ __device__ __forceinline__ void band_events(const PLocalSmem<PG> &sm, uint32_t (
         const uint32_t e1r = Ar & ORur & 1u & (((Bur & 1u) | (Bu >> 31) | ((Bur >> 1) & 1u)) ? 1u : 0u);
         const uint32_t E1l = (E1 << 1) | e1l;         // bit c: E1[c-1]
         const uint32_t E1r = (E1 >> 1) | (e1r << 31); // bit c: E1[c+1]
-        EL[j] = A & ~ORu & BuL & ~E1l;
+        const uint32_t el0 = A & ~ORu & BuL & ~E1l;
         ER[j] = A & ~ORu & BuR & ~E1r;
-        D1[j] = lowest_per_run<W>(OR & ORu, E1, w);
+        const uint32_t R = OR & ORu;
+        const uint32_t d1 = lowest_per_run<W>(R, E1, w);
+        // runs of R whose first column follows an R event: (a)
+        const uint32_t erp = __shfl_up_sync(kFull, ER[j], 1, W);
+        const uint32_t ers = ((ER[j] << 1) | (w > 0 ? erp >> 31 : 0u)) & R;
+        const uint32_t G = R & ~row_add<W>(R, ers, w);
+        D1[j] = d1 & ~G;
+        // runs of R holding a kept seed, from the seed on: (b)
+        const uint32_t F2 = R & ~row_add<W>(R, D1[j] | ers, w);
+        const uint32_t f2p = __shfl_up_sync(kFull, F2, 1, W);
+        EL[j] = el0 & ~((F2 << 1) | (w > 0 ? f2p >> 31 : 0u));
         FE[j] = lowest_per_run<W>(OR, D1[j] | EL[j] | ER[j], w);
         TA[j] = lowest_per_run<W>(OR, A, w);
+        // last columns of the runs without an event
+        const uint32_t orn = __shfl_down_sync(kFull, OR, 1, W);
+        const uint32_t endm = OR & ~((OR >> 1) | ((w + 1 < W ? orn : 0u) << 31));
+        RE[j] = endm & row_add<W>(OR, FE[j], w);
     }
 }
 
@@ -457,31 +489,14 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
     // -- row connection (the pieces, by bit operations) and the contact
     // events of every band with the band above
     band_tables<PG, false, false>(sm.m, sm.S, nullptr, nullptr, sm.pb, sm.bandcnt);
-    uint32_t evD1[kItems], evEL[kItems], evER[kItems], evFE[kItems], evTA[kItems];
-    band_events<PG, kItems>(sm, evD1, evEL, evER, evFE, evTA);
+    uint32_t evD1[kItems], evEL[kItems], evER[kItems], evFE[kItems], evTA[kItems], evRE[kItems];
+    band_events<PG, kItems>(sm, evD1, evEL, evER, evFE, evTA, evRE);
     __syncthreads();
     band_prefix<PG>(sm.bandcnt, sm.bb);
     __syncthreads();
     const int n = sm.bb[PG::kBands];
     volatile uint16_t *const vpar = sm.par;
     uint16_t *const par = sm.par;
-    // -- every piece a root keyed by its first column in the band's lower row
-    // (its smallest pixel when it has none in the upper row)
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int item = t + j * T;
-        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        uint32_t sb = sm.S[k][w];
-        int at = (int)sm.bb[k] + (int)sm.pb[k][w];
-        const int rowkey = (2 * k + 1) << PG::kBWLog2;
-        for (; sb; sb &= sb - 1u) vpar[at++] = (uint16_t)(kRoot | (rowkey + 32 * w + lobit(sb)));
-    }
-    __syncthreads();
-    // -- column connection (coarse labelling): the first event of a piece
-    // names the piece above that becomes its parent (a smaller key, so the
-    // entries form a forest; a plain store of the piece's own entry)
-    // (piece indices of the item's word and of the word above come from the
-    // item's own base and start mask: one popcount per event)
     int qbase[kItems], ubase[kItems];
     uint32_t Sw[kItems], Suw[kItems];
 #pragma unroll
@@ -499,6 +514,11 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
         if ((uc >> 5) == w) return ubase[j] + __popc(Suw[j] & upto(uc & 31));
         return piece_at<PG>(sm.S, sm.pb, sm.bb, k - 1, uc);
     };
+    // -- one entry per piece.  Column connection (coarse labelling): the first
+    // event of a piece names the piece above that becomes its parent (a
+    // smaller key, so the entries form a forest).  A piece without events is
+    // a root keyed by its smallest pixel: its first upper-row pixel, else the
+    // first column of its lower row.
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const int item = t + j * T;
@@ -509,30 +529,37 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
             const int q = qbase[j] + __popc(Sw[j] & upto(c));
             vpar[q] = (uint16_t)upper_piece(j, k, w, c, (d1 >> c) & 1u, (el >> c) & 1u);
         }
-    }
-    __syncthreads();
-    // -- a root with pixels in the band's upper row is keyed by the first
-    // of them
-#pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int item = t + j * T;
-        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        for (uint32_t ta = evTA[j]; ta; ta &= ta - 1u) {
-            const int c = lobit(ta);
+        for (uint32_t re = evRE[j]; re; re &= re - 1u) {
+            const int c = lobit(re);
             const int q = qbase[j] + __popc(Sw[j] & upto(c));
-            if (vpar[q] & kRoot) vpar[q] = (uint16_t)(kRoot | (((2 * k) << PG::kBWLog2) + 32 * w + c));
+            const uint32_t sb = Sw[j] & upto(c);
+            int key;
+            if (sb) {
+                const int s0 = 31 - __clz(sb);
+                const uint32_t tab = evTA[j] & upto(c) & ~((1u << s0) - 1u);
+                key = tab ? (((2 * k) << PG::kBWLog2) + 32 * w + lobit(tab))
+                          : (((2 * k + 1) << PG::kBWLog2) + 32 * w + s0);
+            } else {
+                // the run began in an earlier word: its first column is the
+                // last start of the nearest earlier word that holds one
+                int a0 = 0;
+                for (int w2 = w - 1; w2 >= 0; --w2) {
+                    const uint32_t s2 = sm.S[k][w2];
+                    if (s2) {
+                        a0 = 32 * w2 + 31 - __clz(s2);
+                        break;
+                    }
+                }
+                key = pkey<PG>(sm.m, k, a0, 32 * w + c);
+            }
+            vpar[q] = (uint16_t)(kRoot | key);
         }
     }
     __syncthreads();
     // -- every entry to its root: finds with path halving (a halving store
     // writes an ancestor, and every store after a find is a root of the
     // forest of coarse links, which nothing else changes in this pass)
-    for (int i = t; i < n; i += T) {
-        uint16_t re;
-        const int r = pfind(vpar, i, re, cap, err);
-        if (r != i) vpar[i] = (uint16_t)r;
-    }
-    __syncthreads();
+
     // -- refinement: every other event joins its two pieces; the CAS union
     // runs only where the roots their entries name differ.  The events are
     // first packed into a list of (piece, piece above) pairs, so that every
@@ -602,10 +629,11 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
             __syncthreads();
         }
     }
-    // -- compress: every entry points straight at its root (the finds only
-    // read, so every store here is a final root)
+    // -- compress: every entry points straight at its root (each entry's
+    // final store is made by its own thread; the halving stores of the
+    // other walks are CAS and cannot undo it)
     for (int i = t; i < n; i += T) {
-        const int r = pfind_ro(vpar, i, cap, err);
+        const int r = pfind_cas(par, i, cap, err);
         if (r != i) vpar[i] = (uint16_t)r;
     }
     __syncthreads();
