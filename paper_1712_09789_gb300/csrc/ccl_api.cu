@@ -29,6 +29,22 @@ std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_lab;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_stats;  // component statistics scratch
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_volume; // face records of the 3D labelling
 
+// ccl_label() alternates between two halves of its scratch per (device,
+// stream), so that a labelling's step 1 may start (chained) while the
+// previous labelling's write-out, which reads the other half, still runs.
+// The labels range of the previous call guards against an image that
+// overlaps it.
+struct Chain {
+    int half = 0;
+    uintptr_t lab0 = 0, lab1 = 0;
+};
+std::map<std::pair<int, cudaStream_t>, Chain> g_chain;
+
+// Offset of the second half of a chained scratch buffer: the buffer's own
+// middle, whatever image the call labels, so that calls of different sizes
+// keep to their halves.
+size_t split(const DevBuf &b) { return (b.bytes / 2) & ~(size_t)255; }
+
 ccl_status grow(DevBuf &b, size_t need) {
     if (b.bytes >= need) return CCL_OK;
     if (b.ptr) {
@@ -92,18 +108,25 @@ ccl_status enqueue_host(const uint8_t *host_img, int H, int W, size_t pitch, int
     DevBuf &b = g_scratch[{dev, s}];
     DevBuf &bi = g_host_img[{dev, s}];
     DevBuf &bl = g_host_lab[{dev, s}];
-    if (b.bytes < need || bi.bytes < img_bytes || bl.bytes < lab_bytes) {
+    // the scratch halves alternate with ccl_label's on the same stream
+    const size_t half = (need + 255) & ~(size_t)255;
+    if (b.bytes < 2 * half || bi.bytes < img_bytes || bl.bytes < lab_bytes) {
         if (cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-        if ((st = grow(b, need)) != CCL_OK) return st;
+        if ((st = grow(b, 2 * half)) != CCL_OK) return st;
         if ((st = grow(bi, img_bytes)) != CCL_OK) return st;
         if ((st = grow(bl, lab_bytes)) != CCL_OK) return st;
     }
     if (cudaMemcpy2DAsync(bi.ptr, dpitch, host_img, pitch, (size_t)W, (size_t)H, cudaMemcpyHostToDevice, s) !=
         cudaSuccess)
         return CCL_ERR_CUDA;
+    Chain &c = g_chain[{dev, s}];
     if (ccl::launch_label(static_cast<const uint8_t *>(bi.ptr), H, W, dpitch, connectivity,
-                          static_cast<int32_t *>(bl.ptr), b.ptr, s, g_cap) != 0)
+                          static_cast<int32_t *>(bl.ptr), static_cast<char *>(b.ptr) + (c.half ? split(b) : 0), s,
+                          g_cap) != 0)
         return CCL_ERR_CUDA;
+    c.half ^= 1;
+    c.lab0 = reinterpret_cast<uintptr_t>(bl.ptr);
+    c.lab1 = c.lab0 + lab_bytes;
     if (cudaMemcpyAsync(host_labels, bl.ptr, lab_bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return CCL_ERR_CUDA;
     return CCL_OK;
@@ -178,13 +201,21 @@ ccl_status ccl_label(const uint8_t *img, int H, int W, size_t pitch, int connect
     // stream.
     std::lock_guard<std::mutex> lk(g_mu);
     DevBuf &b = g_scratch[{dev, s}];
-    if (b.bytes < need) {
+    const size_t half = (need + 255) & ~(size_t)255;
+    if (b.bytes < 2 * half) {
         // the old buffer may still be in use by earlier work on this stream
         if (b.ptr && cudaStreamSynchronize(s) != cudaSuccess) return CCL_ERR_CUDA;
-        st = grow(b, need);
+        st = grow(b, 2 * half);
         if (st != CCL_OK) return st;
     }
-    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, b.ptr, s, g_cap) != 0) return CCL_ERR_CUDA;
+    Chain &c = g_chain[{dev, s}];
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(img), i1 = i0 + (size_t)(H - 1) * pitch + (size_t)W;
+    const bool chain = !(i0 < c.lab1 && c.lab0 < i1);
+    void *ws = static_cast<char *>(b.ptr) + (c.half ? split(b) : 0);
+    if (ccl::launch_label(img, H, W, pitch, connectivity, labels, ws, s, g_cap, chain) != 0) return CCL_ERR_CUDA;
+    c.half ^= 1;
+    c.lab0 = reinterpret_cast<uintptr_t>(labels);
+    c.lab1 = c.lab0 + (size_t)H * (size_t)W * sizeof(int32_t);
     return CCL_OK;
 }
 
@@ -282,6 +313,7 @@ ccl_status ccl_release_stream(void *stream) {
             if (it->second.ptr) cudaFree(it->second.ptr);
             m->erase(it);
         }
+        g_chain.erase({dev, s});
     }
     ccl::release_batched_stream(dev, s);
     return CCL_OK;

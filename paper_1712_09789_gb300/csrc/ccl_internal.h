@@ -69,9 +69,13 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
 
 // Enqueues the whole labelling of one image on `stream`.  `ws` must hold
 // workspace_bytes(H, W) bytes, 256-byte aligned.  `cap` <= 0 selects the
-// default iteration caps.  Returns 0, or -1 when a launch failed.
+// default iteration caps.  `chain` lets the first kernel start while the
+// kernel before it on the stream finishes (programmatic dependent launch;
+// the piece labeller only): allowed only when that kernel may be the
+// write-out of an earlier labelling whose scratch is not `ws` and whose
+// labels do not overlap `img`.  Returns 0, or -1 when a launch failed.
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
-                 cudaStream_t stream, int cap);
+                 cudaStream_t stream, int cap, bool chain = false);
 
 // Strip sharding (ccl_strip.cu).  launch_label_phases() runs the kernels of
 // launch_label() selected by `phases` on an image whose pixel (0, 0) has

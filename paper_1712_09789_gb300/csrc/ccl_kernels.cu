@@ -1302,7 +1302,7 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
 template <class PG>
 int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
                        const PScratch &ps, size_t nb, int cap, cudaStream_t stream,
-                       int phases = kPhaseLocalMerge | kPhaseWrite) {
+                       int phases = kPhaseLocalMerge | kPhaseWrite, bool chain = false) {
     const int local_cap = cap > 0 ? cap : PG::kMaxPieces + 16;
     const long long slots = (long long)nb * PG::kSlots;
     const int global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
@@ -1318,17 +1318,20 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
     const bool pdl = ev == nullptr && phases == (kPhaseLocalMerge | kPhaseWrite);
     bool ok = true;
     if (phases & kPhaseLocalMerge) {
-        k_piece_local<PG><<<grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream>>>(jt, ps, local_cap);
+        // chained: step 1 may start while the previous call's write-out on
+        // this stream still runs (it finishes only after that kernel)
+        ok = launch_ex(k_piece_local<PG>, grid_local, PG::kThreads, sizeof(PLocalSmem<PG>), stream,
+                       chain && ev == nullptr, jt, ps, local_cap) == cudaSuccess;
         ev = timing_mark(stream, ev, kKindPieceLocal);
         // the merge of many blocks runs on 128 threads per block (more blocks
         // per SM for its latency-bound unions), that of fewer on 256 (a shorter
         // chain per block)
         if (nb >= 1024) {
             using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
-            ok = launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms,
+            ok = ok && launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms,
                            local_cap, global_cap, bound) == cudaSuccess;
         } else {
-            ok = launch_ex(k_block_merge<PG, PG::kConn8>, grid_merge, PG::kThreads, 0, stream, pdl, jt, ms,
+            ok = ok && launch_ex(k_block_merge<PG, PG::kConn8>, grid_merge, PG::kThreads, 0, stream, pdl, jt, ms,
                            local_cap, global_cap, bound) == cudaSuccess;
         }
         ev = timing_mark(stream, ev, kKindMerge);
@@ -1344,7 +1347,7 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
 template <class PG>
 int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
                         cudaStream_t stream, int cap, uint32_t key0 = 0,
-                        int phases = kPhaseLocalMerge | kPhaseWrite) {
+                        int phases = kPhaseLocalMerge | kPhaseWrite, bool chain = false) {
     int occ_l = 0, occ_w = 0, sms = 0;
     if (!piece_prepare<PG>(occ_l, occ_w, sms)) return -1;
     JobTable jt{};
@@ -1362,7 +1365,7 @@ int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t 
     const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
     jt.total = (unsigned)nb;
     return launch_piece_table<PG>(jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve_p<PG>(ws, nb), nb, cap,
-                                  stream, phases);
+                                  stream, phases, chain);
 }
 
 template <class G>
@@ -1473,8 +1476,10 @@ size_t workspace_bytes(int H, int W) {
 }
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
-                 cudaStream_t stream, int cap) {
-    if (conn == 8) return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap);
+                 cudaStream_t stream, int cap, bool chain) {
+    if (conn == 8)
+        return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, 0,
+                                       kPhaseLocalMerge | kPhaseWrite, chain);
     return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
 }
 

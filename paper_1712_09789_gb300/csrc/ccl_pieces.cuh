@@ -737,6 +737,10 @@ __global__ void __launch_bounds__(PG::kThreads, 5) k_piece_local(JobTable jt, PS
         process_plocal<PG>(job, sm.item.lb, sm.item.gb, s, sm, cap);
         __syncthreads();
     }
+    // when this grid was chained behind the previous labelling's write-out,
+    // it ends only after that kernel (no-op otherwise): whatever runs after
+    // this grid also runs after it
+    grid_dependency_wait();
     // the merge may be launched now (it waits for this grid's completion)
     grid_launch_dependents();
 }
@@ -875,6 +879,9 @@ template <class PG>
 __global__ void __launch_bounds__(PG::kThreads, 7) k_piece_write(JobTable jt, PScratch s, int cap, uint32_t bound) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PWriteSmem<PG> &sm = *reinterpret_cast<PWriteSmem<PG> *>(smem_raw);
+    // a chained step 1 of the next labelling on the stream may start now: it
+    // writes another scratch and finishes only after this grid
+    grid_launch_dependents();
     for (unsigned iter = 0; claim_item(jt, 2, iter, sm.item); ++iter) {
         const Job &job = sm.item.job;
         process_pwrite<PG>(job, sm.item.lb, sm.item.gb, s, sm, cap, bound);
