@@ -992,6 +992,11 @@ using G3 = Geo<16, 8, 8>;
 
 // the piece labeller's blocks (8-connectivity): 512 x 64 pixels, 256 threads
 using P8 = PGeo<512, 64, 256, true>;
+// and for images of few 512 x 64 blocks: 256 x 32 pixels, 128 threads (four
+// times the blocks, each a quarter of the work: a shorter chain per block
+// while the grid cannot fill the GPU)
+using P8s = PGeo<256, 32, 128, true>;
+constexpr size_t kSmallPieceMaxBlocks = 384;  // 512 x 64 blocks (up to about 3500^2 pixels)
 static_assert(P8::kBW == G0::kBW && P8::kBH == G0::kBH, "the piece blocks cover the same blocks as 512x64");
 
 template <class PG>
@@ -1472,11 +1477,16 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
 // (32x8 lane tiles hold only 5 CTAs of 128 threads per SM there).
 size_t workspace_bytes(int H, int W) {
     const size_t nb = blocks_of<G0>(H, W);
-    return std::max(layout_p<P8>(nb).total, std::max(layout_for<G0>(nb).total, layout_for<G3>(nb).total));
+    const size_t small = blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks ? layout_p<P8s>(blocks_of<P8s>(H, W)).total : 0;
+    return std::max(std::max(layout_p<P8>(nb).total, small),
+                    std::max(layout_for<G0>(nb).total, layout_for<G3>(nb).total));
 }
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap, bool chain) {
+    if (conn == 8 && blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks)
+        return launch_piece_single<P8s>(img, H, W, pitch, labels, ws, stream, cap, 0,
+                                        kPhaseLocalMerge | kPhaseWrite, chain);
     if (conn == 8)
         return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, 0,
                                        kPhaseLocalMerge | kPhaseWrite, chain);

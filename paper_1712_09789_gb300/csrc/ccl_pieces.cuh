@@ -556,12 +556,20 @@ __device__ __forceinline__ void process_plocal(const Job &job, unsigned lb, unsi
         }
     }
     __syncthreads();
-    // -- every entry to its root: finds with path halving (a halving store
-    // writes an ancestor, and every store after a find is a root of the
-    // forest of coarse links, which nothing else changes in this pass)
-
+    // -- one round of pointer jumping: every link to its grandparent (an
+    // ancestor either way when another thread's store races with the read),
+    // halving the coarse links' chains before the unions walk them
+    for (int i = t; i < n; i += T) {
+        const uint16_t e = vpar[i];
+        if (!(e & kRoot)) {
+            const uint16_t g = vpar[e];
+            if (!(g & kRoot)) vpar[i] = g;
+        }
+    }
+    __syncthreads();
     // -- refinement: every other event joins its two pieces; the CAS union
-    // runs only where the roots their entries name differ.  The events are
+    // runs only where the roots their entries name differ (the finds of the
+    // unions halve the paths of the coarse links as they go).  The events are
     // first packed into a list of (piece, piece above) pairs, so that every
     // lane takes one per step.
     {
