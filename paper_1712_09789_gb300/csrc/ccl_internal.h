@@ -138,10 +138,11 @@ int iteration_cap_api();
 // Benchmark timing of the kernels enqueued by launch_label().
 // (kinds 0-2: the lane-tile kernels; 3 and 4: the piece labeller's step 1
 // and step 3, whose step 2 is kind 1)
-constexpr int kKindLocal = 0, kKindMerge = 1, kKindWrite = 2, kKindPieceLocal = 3, kKindPieceWrite = 4;
-constexpr int kKernelKinds = 5;
+constexpr int kKindLocal = 0, kKindMerge = 1, kKindWrite = 2, kKindPieceLocal = 3, kKindPieceWrite = 4,
+              kKindPieceCoop = 5;
+constexpr int kKernelKinds = 6;
 // a record of this kind closes the timing of one call
-constexpr bool kind_closes_call(int k) { return k == kKindWrite || k == kKindPieceWrite; }
+constexpr bool kind_closes_call(int k) { return k == kKindWrite || k == kKindPieceWrite || k == kKindPieceCoop; }
 void timing_enable(bool on);
 int timing_read(double *ms, long long *count, int n);
 const char *kernel_kind_name(int k);

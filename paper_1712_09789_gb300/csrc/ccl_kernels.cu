@@ -35,6 +35,7 @@
 #include <mutex>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "ccl_block.cuh"
@@ -654,7 +655,9 @@ struct __align__(16) MergeSmem {  // (16-byte aligned: the edges are staged with
     ItemSlot item;
 };
 
-template <class G, bool kConn8>
+// (kCoherent: the records were written earlier in the same grid, so they are
+// read through L2 rather than the non-coherent read-only path)
+template <class G, bool kConn8, bool kCoherent = false>
 __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsigned gb, const Scratch &s,
                                               MergeSmem<G> &sm, int lcap, int gcap, uint32_t bound) {
     constexpr int T = G::kThreads;
@@ -664,9 +667,11 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
     const int t = threadIdx.x;
     const bool up = by > 0, left = bx > 0;
     const unsigned bu = b - (unsigned)nbx, bl = b - 1u;
-    const int nso = s.nslots[b];
-    const int nsu = up ? s.nslots[bu] : 0;
-    const int nsl = left ? s.nslots[bl] : 0;
+    const auto ld16 = [](const uint4 *p) { return kCoherent ? __ldcg(p) : __ldg(p); };
+    const auto ldn = [&](unsigned blk) { return kCoherent ? __ldcg(s.nslots + blk) : s.nslots[blk]; };
+    const int nso = ldn(b);
+    const int nsu = up ? ldn(bu) : 0;
+    const int nsl = left ? ldn(bl) : 0;
     const uint16_t *Eo = s.edges + (size_t)b * G::kEdge;
     int err = 0;
 
@@ -675,16 +680,16 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
         const uint4 *src_o = reinterpret_cast<const uint4 *>(Eo + G::kEdgeTop);
         const uint4 *src_p = reinterpret_cast<const uint4 *>(s.edges + (size_t)bu * G::kEdge + G::kEdgeBottom);
         for (int i = t; i < G::kBW / 4; i += T) {
-            if (i < G::kBW / 8) reinterpret_cast<uint4 *>(sm.up_o)[i] = __ldg(src_o + i);
-            else reinterpret_cast<uint4 *>(sm.up_p)[i - G::kBW / 8] = __ldg(src_p + (i - G::kBW / 8));
+            if (i < G::kBW / 8) reinterpret_cast<uint4 *>(sm.up_o)[i] = ld16(src_o + i);
+            else reinterpret_cast<uint4 *>(sm.up_p)[i - G::kBW / 8] = ld16(src_p + (i - G::kBW / 8));
         }
     }
     if (left) {
         const uint4 *src_o = reinterpret_cast<const uint4 *>(Eo + G::kEdgeLeft);
         const uint4 *src_p = reinterpret_cast<const uint4 *>(s.edges + (size_t)bl * G::kEdge + G::kEdgeRight);
         for (int i = t; i < G::kBH / 4; i += T) {
-            if (i < G::kBH / 8) reinterpret_cast<uint4 *>(sm.lf_o)[i] = __ldg(src_o + i);
-            else reinterpret_cast<uint4 *>(sm.lf_p)[i - G::kBH / 8] = __ldg(src_p + (i - G::kBH / 8));
+            if (i < G::kBH / 8) reinterpret_cast<uint4 *>(sm.lf_o)[i] = ld16(src_o + i);
+            else reinterpret_cast<uint4 *>(sm.lf_p)[i - G::kBH / 8] = ld16(src_p + (i - G::kBH / 8));
         }
     }
     const int nn = nso + nsu + nsl;
@@ -758,14 +763,16 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
     if (kConn8 && up) {
         if (t == T - 1 && left) {
             const unsigned bd = bu - 1u;
-            const uint16_t a = sm.up_o[0], d = s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom + G::kBW - 1];
-            if (ok(a, nso) && ok(d, s.nslots[bd]))
+            const uint16_t a = sm.up_o[0], d = kCoherent ? __ldcg(s.edges + (size_t)bd * G::kEdge + G::kEdgeBottom + G::kBW - 1)
+                                                         : s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom + G::kBW - 1];
+            if (ok(a, nso) && ok(d, ldn(bd)))
                 union_global(s.P, b * (uint32_t)G::kSlots + a, bd * (uint32_t)G::kSlots + d, gcap, err, bound);
         }
         if (t == T - 2 && bx + 1 < nbx) {
             const unsigned bd = bu + 1u;
-            const uint16_t a = sm.up_o[G::kBW - 1], d = s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom];
-            if (ok(a, nso) && ok(d, s.nslots[bd]))
+            const uint16_t a = sm.up_o[G::kBW - 1], d = kCoherent ? __ldcg(s.edges + (size_t)bd * G::kEdge + G::kEdgeBottom)
+                                                                : s.edges[(size_t)bd * G::kEdge + G::kEdgeBottom];
+            if (ok(a, nso) && ok(d, ldn(bd)))
                 union_global(s.P, b * (uint32_t)G::kSlots + a, bd * (uint32_t)G::kSlots + d, gcap, err, bound);
         }
     }
@@ -1126,7 +1133,7 @@ int timing_read(double *ms, long long *count, int n) {
 
 const char *kernel_kind_name(int k) {
     static const char *names[kKernelKinds] = {"k_block_local", "k_block_merge", "k_block_write", "k_piece_local",
-                                              "k_piece_write"};
+                                              "k_piece_write", "k_piece_coop"};
     return (k >= 0 && k < kKernelKinds) ? names[k] : "";
 }
 
@@ -1269,11 +1276,11 @@ cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, s
 // Per-device set-up of the piece kernels (their shared memory exceeds the 48 KB
 // a launch gets without opting in) and their occupancy.
 template <class PG>
-bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
+bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nullptr) {
     static std::mutex mu;
     struct Ent {
         bool ready = false;
-        int occ_local = 0, occ_write = 0, sms = 0;
+        int occ_local = 0, occ_write = 0, occ_coop = 0, sms = 0;
     };
     static Ent per_dev[64];
     int dev = 0;
@@ -1290,6 +1297,9 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
                 cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_write, k_piece_write<PG>, PG::kThreads, bw) !=
                 cudaSuccess ||
+            cudaFuncSetAttribute(k_piece_coop<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bl) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_coop, k_piece_coop<PG>, PG::kThreads, bl) !=
+                cudaSuccess ||
             cudaDeviceGetAttribute(&e.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return false;
         e.occ_local = std::max(1, e.occ_local);
@@ -1299,6 +1309,7 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms) {
     occ_local = e.occ_local;
     occ_write = e.occ_write;
     sms = e.sms;
+    if (occ_coop) *occ_coop = e.occ_coop;
     return true;
 }
 
@@ -1332,7 +1343,7 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
         // per SM for its latency-bound unions), that of fewer on 256 (a shorter
         // chain per block)
         if (nb >= 1024) {
-            using MG = PGeo<PG::kBW, PG::kBH, 128, PG::kConn8>;
+            using MG = PGeo<PG::kBW, PG::kBH, (PG::kThreads < 128 ? PG::kThreads : 128), PG::kConn8>;
             ok = ok && launch_ex(k_block_merge<MG, PG::kConn8>, grid_merge, MG::kThreads, 0, stream, pdl, jt, ms,
                            local_cap, global_cap, bound) == cudaSuccess;
         } else {
@@ -1353,8 +1364,8 @@ template <class PG>
 int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t *labels, void *ws,
                         cudaStream_t stream, int cap, uint32_t key0 = 0,
                         int phases = kPhaseLocalMerge | kPhaseWrite, bool chain = false) {
-    int occ_l = 0, occ_w = 0, sms = 0;
-    if (!piece_prepare<PG>(occ_l, occ_w, sms)) return -1;
+    int occ_l = 0, occ_w = 0, sms = 0, occ_c = 0;
+    if (!piece_prepare<PG>(occ_l, occ_w, sms, &occ_c)) return -1;
     JobTable jt{};
     jt.single.img = img;
     jt.single.labels = labels;
@@ -1369,8 +1380,28 @@ int launch_piece_single(const uint8_t *img, int H, int W, size_t pitch, int32_t 
                       ((((uintptr_t)labels & 15) == 0 && (W & 3) == 0) ? kJobVecOut : 0u);
     const size_t nb = (size_t)jt.single.nbx * (size_t)jt.single.nby;
     jt.total = (unsigned)nb;
-    return launch_piece_table<PG>(jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, carve_p<PG>(ws, nb), nb, cap,
-                                  stream, phases, chain);
+    const PScratch ps = carve_p<PG>(ws, nb);
+    if (phases == (kPhaseLocalMerge | kPhaseWrite) && nb <= (size_t)occ_c * (size_t)sms) {
+        // every block resident at once: the three steps in one cooperative grid
+        const int local_cap = cap > 0 ? cap : PG::kMaxPieces + 16;
+        const long long slots = (long long)nb * PG::kSlots;
+        int global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
+        uint32_t bound = (uint32_t)slots;
+        Scratch ms{};
+        ms.edges = ps.edges;
+        ms.P = ps.P;
+        ms.nslots = ps.nslots;
+        PScratch psa = ps;
+        int lcap = local_cap;
+        void *args[] = {&jt, &psa, &lcap, &ms, &global_cap, &bound};
+        cudaEvent_t ev = timing_mark(stream, nullptr, -1);
+        const bool ok = cudaLaunchCooperativeKernel((const void *)k_piece_coop<PG>, dim3((unsigned)nb),
+                                                    dim3(PG::kThreads), args, sizeof(PLocalSmem<PG>),
+                                                    stream) == cudaSuccess;
+        timing_mark(stream, ev, kKindPieceCoop);
+        return ok && cudaGetLastError() == cudaSuccess ? 0 : -1;
+    }
+    return launch_piece_table<PG>(jt, (unsigned)nb, (unsigned)nb, (unsigned)nb, ps, nb, cap, stream, phases, chain);
 }
 
 template <class G>

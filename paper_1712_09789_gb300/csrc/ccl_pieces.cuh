@@ -57,7 +57,7 @@ struct PGeo {
     static constexpr int kEdgeRight = 2 * kBW + kBH;
     static constexpr int kEdge = 2 * kBW + 2 * kBH;
     // labels decoded per write-out window (a band always fits)
-    static constexpr int kLabWindow = kConn8 ? 4096 : 8192;
+    static constexpr int kLabWindow = (kConn8 ? 4096 : 8192) < kMaxPieces ? (kConn8 ? 4096 : 8192) : kMaxPieces;
     static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
     static_assert(kMaxPieces <= kBorderRoot, "piece indices must stay below the border-root marker");
     static_assert(kBands <= 32 && kBands % kWarps == 0 && kGroup >= 1, "bands per warp group");
@@ -767,9 +767,14 @@ struct PWriteSmem {
     ItemSlot item;
 };
 
+// The labels of step 3 from the piece index tables of the block (row masks
+// m, starts S, word prefixes pb, band prefix bb) with the buffers slot_label
+// [kSlots] and lab [kLabWindow]; every thread of the CTA takes part.
 template <class PG>
-__device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsigned gb, const PScratch &s,
-                                               PWriteSmem<PG> &sm, int cap, uint32_t bound) {
+__device__ __forceinline__ void pwrite_labels(const Job &job, unsigned lb, unsigned gb, const PScratch &s,
+                                              uint32_t (*m)[PG::kWords], const uint32_t (*S)[PG::kWords],
+                                              uint16_t (*pb)[PG::kWords], const uint16_t *bb, int *slot_label,
+                                              int *lab, int cap, uint32_t bound) {
     constexpr int W = PG::kWords;
     constexpr int T = PG::kThreads;
     constexpr int kChunks = PG::kBW / 4;  // 4-column chunks per row
@@ -781,25 +786,12 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     const uint32_t key0 = job.key0;
     const int x0 = bx * PG::kBW, y0 = by * PG::kBH;
     const int t = threadIdx.x;
-
-    {
-        const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + (size_t)b * PG::kBH * W);
-        uint4 *mo = reinterpret_cast<uint4 *>(&sm.m[0][0]);
-        for (int q = t; q < PG::kBH * W / 4; q += T) mo[q] = mi[q];
-    }
-    // the piece index tables, from step 1's outputs only (step 1 finished
-    // before the merge started)
-    __syncthreads();
-    band_tables<PG, false, false>(sm.m, sm.S, nullptr, nullptr, sm.pb, sm.bandcnt);
-    __syncthreads();
-    band_prefix<PG>(sm.bandcnt, sm.bb);
-    __syncthreads();
     // pb[k][w] becomes the index of the first piece of band k starting in word w or later
 #pragma unroll
     for (int j = 0; j < PG::kBands * W / T; ++j) {
         const int item = t + j * T;
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        sm.pb[k][w] = (uint16_t)(sm.pb[k][w] + sm.bb[k]);
+        pb[k][w] = (uint16_t)(pb[k][w] + bb[k]);
     }
     // the merge (step 2) may still be running when this kernel starts
     // (programmatic dependent launch): wait for it before the first read of
@@ -812,7 +804,7 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     for (int k = t; k < ns; k += T) {
         uint32_t key;
         find_global_ro(s.P, b * (uint32_t)PG::kSlots + (uint32_t)k, key, cap, err, bound);
-        sm.slot_label[k] = (int)key + 1;
+        slot_label[k] = (int)key + 1;
     }
     report(err);
     __syncthreads();
@@ -821,12 +813,12 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     for (int k0 = 0; k0 < PG::kBands;) {
         // a window of whole bands whose piece labels fit in shared memory
         int k1 = k0 + 1;
-        while (k1 < PG::kBands && (int)sm.bb[k1 + 1] - (int)sm.bb[k0] <= PG::kLabWindow) ++k1;
-        const int p0 = sm.bb[k0], np = (int)sm.bb[k1] - p0;
+        while (k1 < PG::kBands && (int)bb[k1 + 1] - (int)bb[k0] <= PG::kLabWindow) ++k1;
+        const int p0 = bb[k0], np = (int)bb[k1] - p0;
         for (int i = t; i < np; i += T) {
             const uint32_t v = vin[p0 + i];
             const uint32_t slot = v & 0x7FFFu;
-            sm.lab[i] = (v & kBorderFlag) ? ((int)slot < ns ? sm.slot_label[slot] : 0)
+            lab[i] = (v & kBorderFlag) ? ((int)slot < ns ? slot_label[slot] : 0)
                                           : (int)(key0 + (uint32_t)(y0 + (int)(v >> PG::kBWLog2)) * (uint32_t)Wd +
                                                   (uint32_t)(x0 + (int)(v & (PG::kBW - 1)))) + 1;
         }
@@ -845,18 +837,18 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
                 for (int k = k0 + t / kChunks; k < k1; k += kStep) {
                     const int y = y0 + 2 * k;
                     if (y >= H) break;
-                    const uint32_t A4 = (sm.m[2 * k][w] >> c0) & 15u, B4 = (sm.m[2 * k + 1][w] >> c0) & 15u;
+                    const uint32_t A4 = (m[2 * k][w] >> c0) & 15u, B4 = (m[2 * k + 1][w] >> c0) & 15u;
                     const uint32_t O4 = A4 | B4;
                     int l0 = 0, l1 = 0, l2 = 0, l3 = 0;
                     if (O4) {
-                        const uint32_t Sw = sm.S[k][w] >> c0;
-                        const int idx = (int)sm.pb[k][w] - p0 - 1 + __popc(sm.S[k][w] & below);
+                        const uint32_t Sw = S[k][w] >> c0;
+                        const int idx = (int)pb[k][w] - p0 - 1 + __popc(S[k][w] & below);
                         const int i0 = idx + (int)(Sw & 1u), i1 = i0 + (int)((Sw >> 1) & 1u);
                         const int i2 = i1 + (int)((Sw >> 2) & 1u), i3 = i2 + (int)((Sw >> 3) & 1u);
-                        if (O4 & 1u) l0 = sm.lab[i0];
-                        if (O4 & 2u) l1 = sm.lab[i1];
-                        if (O4 & 4u) l2 = sm.lab[i2];
-                        if (O4 & 8u) l3 = sm.lab[i3];
+                        if (O4 & 1u) l0 = lab[i0];
+                        if (O4 & 2u) l1 = lab[i1];
+                        if (O4 & 4u) l2 = lab[i2];
+                        if (O4 & 8u) l3 = lab[i3];
                     }
                     int32_t *dst = labels + (size_t)y * Wd + x;
                     const int4 va = make_int4((A4 & 1u) ? l0 : 0, (A4 & 2u) ? l1 : 0, (A4 & 4u) ? l2 : 0,
@@ -883,6 +875,29 @@ __device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsi
     }
 }
 
+
+template <class PG>
+__device__ __forceinline__ void process_pwrite(const Job &job, unsigned lb, unsigned gb, const PScratch &s,
+                                               PWriteSmem<PG> &sm, int cap, uint32_t bound) {
+    constexpr int W = PG::kWords;
+    constexpr int T = PG::kThreads;
+    const unsigned b = gb;
+    const int t = threadIdx.x;
+    {
+        const uint4 *mi = reinterpret_cast<const uint4 *>(s.masks + (size_t)b * PG::kBH * W);
+        uint4 *mo = reinterpret_cast<uint4 *>(&sm.m[0][0]);
+        for (int q = t; q < PG::kBH * W / 4; q += T) mo[q] = mi[q];
+    }
+    // the piece index tables, from step 1's outputs only (step 1 finished
+    // before the merge started)
+    __syncthreads();
+    band_tables<PG, false, false>(sm.m, sm.S, nullptr, nullptr, sm.pb, sm.bandcnt);
+    __syncthreads();
+    band_prefix<PG>(sm.bandcnt, sm.bb);
+    __syncthreads();
+    pwrite_labels<PG>(job, lb, gb, s, sm.m, sm.S, sm.pb, sm.bb, sm.slot_label, sm.lab, cap, bound);
+}
+
 template <class PG>
 __global__ void __launch_bounds__(PG::kThreads, 7) k_piece_write(JobTable jt, PScratch s, int cap, uint32_t bound) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -895,6 +910,33 @@ __global__ void __launch_bounds__(PG::kThreads, 7) k_piece_write(JobTable jt, PS
         process_pwrite<PG>(job, sm.item.lb, sm.item.gb, s, sm, cap, bound);
         __syncthreads();
     }
+}
+
+// The three steps in one cooperative grid, for images whose blocks can all be
+// resident at once (one block per CTA): step 1, a grid-wide barrier, the
+// block's merge, a barrier, then the write-out from the piece index tables
+// step 1 left in shared memory (no reload of the masks, no second table
+// build, no kernel boundaries).  The merge and the write-out buffers overlay
+// step 1's candidate list and equivalence list, which are dead by then.
+template <class PG>
+__global__ void __launch_bounds__(PG::kThreads, 5) k_piece_coop(JobTable jt, PScratch s, int cap, Scratch ms,
+                                                                int gcap, uint32_t bound) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    PLocalSmem<PG> &sm = *reinterpret_cast<PLocalSmem<PG> *>(smem_raw);
+    constexpr size_t kOverlay = offsetof(PLocalSmem<PG>, border) - offsetof(PLocalSmem<PG>, cand);
+    static_assert(sizeof(MergeSmem<PG>) <= kOverlay, "merge overlay");
+    static_assert((PG::kSlots + PG::kLabWindow) * sizeof(int) <= kOverlay, "write-out overlay");
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    claim_item(jt, 0, 0, sm.item);  // block blockIdx.x of the single image
+    const Job &job = sm.item.job;
+    const unsigned lb = sm.item.lb, gb = sm.item.gb;
+    process_plocal<PG>(job, lb, gb, s, sm, cap);
+    grid.sync();
+    MergeSmem<PG> &msm = *reinterpret_cast<MergeSmem<PG> *>(sm.cand);
+    process_merge<PG, PG::kConn8, true>(job, lb, gb, ms, msm, cap, gcap, bound);
+    grid.sync();
+    int *const slot_label = reinterpret_cast<int *>(sm.cand);
+    pwrite_labels<PG>(job, lb, gb, s, sm.m, sm.S, sm.pb, sm.bb, slot_label, slot_label + PG::kSlots, cap, bound);
 }
 
 }  // namespace ccl
