@@ -168,6 +168,16 @@ def test_host_entry_point():
     wide = np.zeros((999, 1300), np.uint8)
     wide[:, :1234] = img
     np.testing.assert_array_equal(ccl.ccl_label_host(wide[:, :1234], 8), oracle.label(img, 8))
+    # page-locked label buffers: the write-out stores into them directly
+    import torch
+
+    for conn in CONNS:
+        for shape in ((999, 1234), (640, 1024)):
+            im = img[: shape[0], : shape[1]].copy()
+            pinned = torch.full(shape, -7, dtype=torch.int32).pin_memory().numpy()
+            out = ccl.ccl_label_host(im, conn, labels=pinned)
+            assert out is pinned
+            np.testing.assert_array_equal(pinned, oracle.label(im, conn))
 
 
 def test_empty_images():
