@@ -1003,6 +1003,9 @@ using P8 = PGeo<512, 64, 256, true>;
 // times the blocks, each a quarter of the work: a shorter chain per block
 // while the grid cannot fill the GPU)
 using P8s = PGeo<256, 32, 128, true>;
+// the same two block shapes under 4-connectivity
+using P4 = PGeo<512, 64, 256, false>;
+using P4s = PGeo<256, 32, 128, false>;
 constexpr size_t kSmallPieceMaxBlocks = 384;  // 512 x 64 blocks (up to about 3500^2 pixels)
 static_assert(P8::kBW == G0::kBW && P8::kBH == G0::kBH, "the piece blocks cover the same blocks as 512x64");
 
@@ -1500,47 +1503,51 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
     }
 }
 
-// A single image under 8-connectivity runs on the piece labeller
-// (ccl_pieces.cuh) on 512x64 blocks: its pieces span the block width, so a
-// block has no inner seams, and the contacts between bands are found for 32
-// columns at a time by bit operations.  Under 4-connectivity a single image
-// runs on the lane-tile kernels above: 32x4 lane tiles at every size measured
-// (32x8 lane tiles hold only 5 CTAs of 128 threads per SM there).
+// A single image runs on the piece labeller (ccl_pieces.cuh) under either
+// connectivity, on 512x64 blocks (256x32 for images of few blocks): its
+// pieces span the block width, so a block has no inner seams, and the
+// contacts between bands are found for 32 columns at a time by bit
+// operations.  The lane-tile kernels above serve batches, the serving loop
+// and the coarse-labelling variants.
 size_t workspace_bytes(int H, int W) {
     const size_t nb = blocks_of<G0>(H, W);
-    const size_t small = blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks ? layout_p<P8s>(blocks_of<P8s>(H, W)).total : 0;
-    return std::max(std::max(layout_p<P8>(nb).total, small),
+    const size_t small = blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks
+                             ? std::max(layout_p<P8s>(blocks_of<P8s>(H, W)).total,
+                                        layout_p<P4s>(blocks_of<P4s>(H, W)).total)
+                             : 0;
+    return std::max(std::max(std::max(layout_p<P8>(nb).total, layout_p<P4>(nb).total), small),
                     std::max(layout_for<G0>(nb).total, layout_for<G3>(nb).total));
 }
 
 int launch_label(const uint8_t *img, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
                  cudaStream_t stream, int cap, bool chain) {
-    if (conn == 8 && blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks)
-        return launch_piece_single<P8s>(img, H, W, pitch, labels, ws, stream, cap, 0,
-                                        kPhaseLocalMerge | kPhaseWrite, chain);
+    const bool small = blocks_of<G0>(H, W) <= kSmallPieceMaxBlocks;
+    constexpr int kAll = kPhaseLocalMerge | kPhaseWrite;
     if (conn == 8)
-        return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, 0,
-                                       kPhaseLocalMerge | kPhaseWrite, chain);
-    return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap);
+        return small ? launch_piece_single<P8s>(img, H, W, pitch, labels, ws, stream, cap, 0, kAll, chain)
+                     : launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, 0, kAll, chain);
+    return small ? launch_piece_single<P4s>(img, H, W, pitch, labels, ws, stream, cap, 0, kAll, chain)
+                 : launch_piece_single<P4>(img, H, W, pitch, labels, ws, stream, cap, 0, kAll, chain);
 }
 
 int launch_label_phases(const uint8_t *img, int H, int W, size_t pitch, int conn, uint32_t key0, int32_t *labels,
                         void *ws, cudaStream_t stream, int cap, int phases) {
     if (conn == 8) return launch_piece_single<P8>(img, H, W, pitch, labels, ws, stream, cap, key0, phases);
-    return launch_single<G0>(img, H, W, pitch, conn, labels, ws, stream, cap, key0, phases);
+    return launch_piece_single<P4>(img, H, W, pitch, labels, ws, stream, cap, key0, phases);
 }
 
 int label_scratch_view(int H, int W, int conn, void *ws, ScratchView *v) {
     const size_t nb = blocks_of<G0>(H, W);
     char *p = static_cast<char *>(ws);
-    const Layout l = conn == 8 ? layout_p<P8>(nb) : layout_for<G0>(nb);
+    const Layout l = conn == 8 ? layout_p<P8>(nb) : layout_p<P4>(nb);
     v->edges = reinterpret_cast<uint16_t *>(p + l.edges);
     v->P = reinterpret_cast<uint64_t *>(p + l.P);
     v->nslots = reinterpret_cast<int32_t *>(p + l.nslots);
     v->nbx = (unsigned)((W + G0::kBW - 1) / G0::kBW);
     v->nby = (unsigned)((H + G0::kBH - 1) / G0::kBH);
-    static_assert(P8::kSlots == G0::kSlots && P8::kEdge == G0::kEdge && P8::kEdgeBottom == G0::kEdgeBottom,
-                  "both block kinds keep the same border records");
+    static_assert(P8::kSlots == G0::kSlots && P8::kEdge == G0::kEdge && P8::kEdgeBottom == G0::kEdgeBottom &&
+                      P4::kSlots == G0::kSlots && P4::kEdge == G0::kEdge && P4::kEdgeBottom == G0::kEdgeBottom,
+                  "the block kinds of strips keep the same border records");
     static_assert(G0::kBW == kStripBW && G0::kBH == kStripBH && G0::kSlots == kStripSlots &&
                       G0::kEdge == kStripEdge && G0::kEdgeBottom == kStripEdgeBottom,
                   "strip constants");

@@ -57,7 +57,7 @@ struct PGeo {
     static constexpr int kEdgeRight = 2 * kBW + kBH;
     static constexpr int kEdge = 2 * kBW + 2 * kBH;
     // labels decoded per write-out window (a band always fits)
-    static constexpr int kLabWindow = (kConn8 ? 4096 : 8192) < kMaxPieces ? (kConn8 ? 4096 : 8192) : kMaxPieces;
+    static constexpr int kLabWindow = 4096 < kMaxPieces / 2 ? 4096 : kMaxPieces / 2;
     static_assert(kBW * kBH <= 32768, "block keys must fit 15 bits");
     static_assert(kMaxPieces <= kBorderRoot, "piece indices must stay below the border-root marker");
     static_assert(kBands <= 32 && kBands % kWarps == 0 && kGroup >= 1, "bands per warp group");
@@ -284,6 +284,33 @@ __device__ __forceinline__ uint32_t lowest_per_run(uint32_t R, uint32_t M, int w
     return M & (row_add<W>(R, M, w) ^ R);
 }
 
+// Segments: the runs of R, each also cut before every bit of Bs (a segment
+// may start inside a run).  Lowest bit of M (a subset of R) in every segment:
+// a seed on a segment's first column is the lowest of its segment; otherwise
+// the lowest seed of the segment's tail (R without the first columns), whose
+// run starts one column later, unless that tail follows a seeded first
+// column.
+template <int W>
+__device__ __forceinline__ uint32_t lowest_per_seg(uint32_t R, uint32_t Bs, uint32_t M, int w) {
+    const uint32_t R2 = R & ~Bs;
+    const uint32_t mb = M & Bs;
+    const uint32_t prev = __shfl_up_sync(kFull, mb, 1, W);
+    const uint32_t after = ((mb << 1) | (w > 0 ? prev >> 31 : 0u)) & R2;
+    const uint32_t T = R2 & ~row_add<W>(R2, after, w);
+    return mb | (lowest_per_run<W>(R2, M & R2, w) & ~T);
+}
+
+// Bits of every segment (as above) from its seed to its last column, for at
+// most one seed M1 per segment.
+template <int W>
+__device__ __forceinline__ uint32_t fill_per_seg(uint32_t R, uint32_t Bs, uint32_t M1, int w) {
+    const uint32_t R2 = R & ~Bs;
+    const uint32_t mb = M1 & Bs;
+    const uint32_t prev = __shfl_up_sync(kFull, mb, 1, W);
+    const uint32_t seeds = (M1 & R2) | (((mb << 1) | (w > 0 ? prev >> 31 : 0u)) & R2);
+    return mb | (R2 & ~row_add<W>(R2, seeds, w));
+}
+
 template <class PG>
 struct PLocalSmem {
     static constexpr int kCandCap = 2048;  // union candidates per pass
@@ -301,6 +328,61 @@ struct PLocalSmem {
     int err;
     ItemSlot item;
 };
+
+// Piece starts (first columns) and piece ends (last columns) of a band under
+// 4-connectivity, from its rows A, B and the bits of the neighbouring words:
+// columns c and c+1 are one piece when they share a row.
+__device__ __forceinline__ uint32_t starts4(uint32_t A, uint32_t B, uint32_t Al, uint32_t Bl) {
+    const uint32_t L = (A & (A >> 1)) | (B & (B >> 1));
+    const uint32_t lin = ((Al >> 31) & A) | ((Bl >> 31) & B);
+    return (A | B) & ~((L << 1) | (lin & 1u));
+}
+__device__ __forceinline__ uint32_t ends4(uint32_t A, uint32_t B, uint32_t Ar, uint32_t Br) {
+    const uint32_t L = (A & (A >> 1)) | (B & (B >> 1));
+    const uint32_t lout = ((A >> 31) & Ar & 1u) | ((B >> 31) & Br & 1u);
+    return (A | B) & ~(L | (lout << 31));
+}
+
+// Contact events of band k with band k-1 under 4-connectivity: a pixel A[c]
+// of the upper row of band k touches the band above only at Bu[c], so the
+// contacts are E = A & Bu.  A piece P of band k and a piece U of band k-1
+// are both intervals of columns, and a run of E lies in one (P, U) pair (two
+// neighbouring columns of A, or of Bu, are one piece); the pairs are the
+// segments of R = OR & ORu cut at the starts of the pieces of either band.
+// D1 keeps the lowest contact of every segment (one event per pair), FE the
+// lowest D1 of every piece, TA the first upper-row pixel of every piece, RE
+// the last column of every piece without events (the outputs of
+// band_events; no L or R events exist).
+template <class PG, int kItems>
+__device__ __forceinline__ void band_events4(const PLocalSmem<PG> &sm, uint32_t (&D1)[kItems],
+                                             uint32_t (&EL)[kItems], uint32_t (&ER)[kItems],
+                                             uint32_t (&FE)[kItems], uint32_t (&TA)[kItems],
+                                             uint32_t (&RE)[kItems]) {
+    constexpr int W = PG::kWords;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const int item = threadIdx.x + j * PG::kThreads;
+        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+        const uint32_t A = sm.m[2 * k][w], B = sm.m[2 * k + 1][w], OR = A | B;
+        const uint32_t Al = w > 0 ? sm.m[2 * k][w - 1] : 0u, Bl = w > 0 ? sm.m[2 * k + 1][w - 1] : 0u;
+        const uint32_t Ar = w + 1 < W ? sm.m[2 * k][w + 1] : 0u, Br = w + 1 < W ? sm.m[2 * k + 1][w + 1] : 0u;
+        const uint32_t Sk = starts4(A, B, Al, Bl);
+        uint32_t Au = 0u, Bu = 0u, Sku = 0u;
+        if (k > 0) {
+            Au = sm.m[2 * k - 2][w];
+            Bu = sm.m[2 * k - 1][w];
+            const uint32_t Aul = w > 0 ? sm.m[2 * k - 2][w - 1] : 0u, Bul = w > 0 ? sm.m[2 * k - 1][w - 1] : 0u;
+            Sku = starts4(Au, Bu, Aul, Bul);
+        }
+        const uint32_t R = OR & (Au | Bu);
+        D1[j] = lowest_per_seg<W>(R, (Sk | Sku) & R, A & Bu, w);
+        EL[j] = 0u;
+        ER[j] = 0u;
+        FE[j] = lowest_per_seg<W>(OR, Sk, D1[j], w);
+        TA[j] = lowest_per_seg<W>(OR, Sk, A, w);
+        RE[j] = ends4(A, B, Ar, Br) & ~fill_per_seg<W>(OR, Sk, FE[j], w);
+    }
+}
 
 // Contact events of band k with band k-1 under 8-connectivity, for the
 // (band, word) items of the calling thread (a warp holds whole bands).  A
@@ -332,47 +414,51 @@ __device__ __forceinline__ void band_events(const PLocalSmem<PG> &sm, uint32_t (
                                             uint32_t (&ER)[kItems], uint32_t (&FE)[kItems], uint32_t (&TA)[kItems],
                                             uint32_t (&RE)[kItems]) {
     constexpr int W = PG::kWords;
+    if constexpr (!PG::kConn8) {
+        band_events4<PG, kItems>(sm, D1, EL, ER, FE, TA, RE);
+    } else {
 #pragma unroll
-    for (int j = 0; j < kItems; ++j) {
-        const int item = threadIdx.x + j * PG::kThreads;
-        const int k = item >> PG::kWordsLog2, w = item & (W - 1);
-        const int ku = k > 0 ? k - 1 : 0;
-        const uint32_t A = sm.m[2 * k][w], B = sm.m[2 * k + 1][w], OR = A | B;
-        const uint32_t Bu = k > 0 ? sm.m[2 * ku + 1][w] : 0u;
-        const uint32_t ORu = k > 0 ? (sm.m[2 * ku][w] | Bu) : 0u;
-        const uint32_t Bul = (k > 0 && w > 0) ? sm.m[2 * ku + 1][w - 1] : 0u;
-        const uint32_t Bur = (k > 0 && w + 1 < W) ? sm.m[2 * ku + 1][w + 1] : 0u;
-        const uint32_t BuL = (Bu << 1) | (Bul >> 31);  // bit c: Bu[c-1]
-        const uint32_t BuR = (Bu >> 1) | (Bur << 31);  // bit c: Bu[c+1]
-        const uint32_t E1 = A & ORu & (Bu | BuL | BuR);
-        // E1 of the neighbouring columns (bits from the neighbouring words)
-        const uint32_t Al = w > 0 ? sm.m[2 * k][w - 1] : 0u, Ar = w + 1 < W ? sm.m[2 * k][w + 1] : 0u;
-        const uint32_t ORur = (k > 0 && w + 1 < W) ? (sm.m[2 * ku][w + 1] | Bur) : 0u;
-        // E1 at column 32w-1 under an L event at 32w (Bu there is set): A there
-        const uint32_t e1l = (Al >> 31) & (Bul >> 31) & 1u;
-        // E1 at column 32w+32 under an R event at 32w+31 (Bu there is set)
-        const uint32_t e1r = Ar & ORur & 1u & (((Bur & 1u) | (Bu >> 31) | ((Bur >> 1) & 1u)) ? 1u : 0u);
-        const uint32_t E1l = (E1 << 1) | e1l;         // bit c: E1[c-1]
-        const uint32_t E1r = (E1 >> 1) | (e1r << 31); // bit c: E1[c+1]
-        const uint32_t el0 = A & ~ORu & BuL & ~E1l;
-        ER[j] = A & ~ORu & BuR & ~E1r;
-        const uint32_t R = OR & ORu;
-        const uint32_t d1 = lowest_per_run<W>(R, E1, w);
-        // runs of R whose first column follows an R event: (a)
-        const uint32_t erp = __shfl_up_sync(kFull, ER[j], 1, W);
-        const uint32_t ers = ((ER[j] << 1) | (w > 0 ? erp >> 31 : 0u)) & R;
-        const uint32_t G = R & ~row_add<W>(R, ers, w);
-        D1[j] = d1 & ~G;
-        // runs of R holding a kept seed, from the seed on: (b)
-        const uint32_t F2 = R & ~row_add<W>(R, D1[j] | ers, w);
-        const uint32_t f2p = __shfl_up_sync(kFull, F2, 1, W);
-        EL[j] = el0 & ~((F2 << 1) | (w > 0 ? f2p >> 31 : 0u));
-        FE[j] = lowest_per_run<W>(OR, D1[j] | EL[j] | ER[j], w);
-        TA[j] = lowest_per_run<W>(OR, A, w);
-        // last columns of the runs without an event
-        const uint32_t orn = __shfl_down_sync(kFull, OR, 1, W);
-        const uint32_t endm = OR & ~((OR >> 1) | ((w + 1 < W ? orn : 0u) << 31));
-        RE[j] = endm & row_add<W>(OR, FE[j], w);
+        for (int j = 0; j < kItems; ++j) {
+            const int item = threadIdx.x + j * PG::kThreads;
+            const int k = item >> PG::kWordsLog2, w = item & (W - 1);
+            const int ku = k > 0 ? k - 1 : 0;
+            const uint32_t A = sm.m[2 * k][w], B = sm.m[2 * k + 1][w], OR = A | B;
+            const uint32_t Bu = k > 0 ? sm.m[2 * ku + 1][w] : 0u;
+            const uint32_t ORu = k > 0 ? (sm.m[2 * ku][w] | Bu) : 0u;
+            const uint32_t Bul = (k > 0 && w > 0) ? sm.m[2 * ku + 1][w - 1] : 0u;
+            const uint32_t Bur = (k > 0 && w + 1 < W) ? sm.m[2 * ku + 1][w + 1] : 0u;
+            const uint32_t BuL = (Bu << 1) | (Bul >> 31);  // bit c: Bu[c-1]
+            const uint32_t BuR = (Bu >> 1) | (Bur << 31);  // bit c: Bu[c+1]
+            const uint32_t E1 = A & ORu & (Bu | BuL | BuR);
+            // E1 of the neighbouring columns (bits from the neighbouring words)
+            const uint32_t Al = w > 0 ? sm.m[2 * k][w - 1] : 0u, Ar = w + 1 < W ? sm.m[2 * k][w + 1] : 0u;
+            const uint32_t ORur = (k > 0 && w + 1 < W) ? (sm.m[2 * ku][w + 1] | Bur) : 0u;
+            // E1 at column 32w-1 under an L event at 32w (Bu there is set): A there
+            const uint32_t e1l = (Al >> 31) & (Bul >> 31) & 1u;
+            // E1 at column 32w+32 under an R event at 32w+31 (Bu there is set)
+            const uint32_t e1r = Ar & ORur & 1u & (((Bur & 1u) | (Bu >> 31) | ((Bur >> 1) & 1u)) ? 1u : 0u);
+            const uint32_t E1l = (E1 << 1) | e1l;         // bit c: E1[c-1]
+            const uint32_t E1r = (E1 >> 1) | (e1r << 31); // bit c: E1[c+1]
+            const uint32_t el0 = A & ~ORu & BuL & ~E1l;
+            ER[j] = A & ~ORu & BuR & ~E1r;
+            const uint32_t R = OR & ORu;
+            const uint32_t d1 = lowest_per_run<W>(R, E1, w);
+            // runs of R whose first column follows an R event: (a)
+            const uint32_t erp = __shfl_up_sync(kFull, ER[j], 1, W);
+            const uint32_t ers = ((ER[j] << 1) | (w > 0 ? erp >> 31 : 0u)) & R;
+            const uint32_t G = R & ~row_add<W>(R, ers, w);
+            D1[j] = d1 & ~G;
+            // runs of R holding a kept seed, from the seed on: (b)
+            const uint32_t F2 = R & ~row_add<W>(R, D1[j] | ers, w);
+            const uint32_t f2p = __shfl_up_sync(kFull, F2, 1, W);
+            EL[j] = el0 & ~((F2 << 1) | (w > 0 ? f2p >> 31 : 0u));
+            FE[j] = lowest_per_run<W>(OR, D1[j] | EL[j] | ER[j], w);
+            TA[j] = lowest_per_run<W>(OR, A, w);
+            // last columns of the runs without an event
+            const uint32_t orn = __shfl_down_sync(kFull, OR, 1, W);
+            const uint32_t endm = OR & ~((OR >> 1) | ((w + 1 < W ? orn : 0u) << 31));
+            RE[j] = endm & row_add<W>(OR, FE[j], w);
+        }
     }
 }
 
