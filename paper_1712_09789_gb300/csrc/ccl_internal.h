@@ -45,11 +45,12 @@ struct JobTable {
     unsigned total;
 };
 
-// Block shapes (lane tiles across x down, lane tile rows): 0 = 16x16 of
-// 32x4 (512x64 pixels, 256 threads), 1 = 8x16 of 32x4 (256x64, 128 threads),
-// 2 = 32x8 of 32x4 (1024x32, 256 threads), 3 = 16x8 of 32x8 (512x64, 128
-// threads).
-constexpr int kNumGeo = 4;
+// Block shapes of a batch.  Lane-tile kernels (lane tiles across x down,
+// lane tile rows): 0 = 16x16 of 32x4 (512x64 pixels, 256 threads), 1 = 8x16
+// of 32x4 (256x64, 128 threads), 2 = 32x8 of 32x4 (1024x32, 256 threads),
+// 3 = 16x8 of 32x8 (512x64, 128 threads).  Piece labeller: 4 = 512x64 (256
+// threads), 5 = 256x32 (128 threads).
+constexpr int kNumGeo = 6;
 const char *geo_name(int geo);
 size_t geo_blocks(int geo, int H, int W);
 size_t geo_workspace_bytes(int geo, size_t blocks);

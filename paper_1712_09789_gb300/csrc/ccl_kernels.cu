@@ -1279,12 +1279,13 @@ cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, s
 // Per-device set-up of the piece kernels (their shared memory exceeds the 48 KB
 // a launch gets without opting in) and their occupancy.
 template <class PG>
-bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nullptr) {
+bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nullptr, int *occ_merge = nullptr) {
     static std::mutex mu;
     struct Ent {
         bool ready = false;
-        int occ_local = 0, occ_write = 0, occ_coop = 0, sms = 0;
+        int occ_local = 0, occ_write = 0, occ_coop = 0, occ_merge = 0, sms = 0;
     };
+    using MG = PGeo<PG::kBW, PG::kBH, (PG::kThreads < 128 ? PG::kThreads : 128), PG::kConn8>;
     static Ent per_dev[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
@@ -1303,6 +1304,8 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nul
             cudaFuncSetAttribute(k_piece_coop<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, bl) != cudaSuccess ||
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_coop, k_piece_coop<PG>, PG::kThreads, bl) !=
                 cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&e.occ_merge, k_block_merge<MG, PG::kConn8>, MG::kThreads,
+                                                          0) != cudaSuccess ||
             cudaDeviceGetAttribute(&e.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return false;
         e.occ_local = std::max(1, e.occ_local);
@@ -1313,6 +1316,7 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nul
     occ_write = e.occ_write;
     sms = e.sms;
     if (occ_coop) *occ_coop = e.occ_coop;
+    if (occ_merge) *occ_merge = std::max(1, e.occ_merge);
     return true;
 }
 
@@ -1321,7 +1325,7 @@ bool piece_prepare(int &occ_local, int &occ_write, int &sms, int *occ_coop = nul
 template <class PG>
 int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_merge, unsigned grid_write,
                        const PScratch &ps, size_t nb, int cap, cudaStream_t stream,
-                       int phases = kPhaseLocalMerge | kPhaseWrite, bool chain = false) {
+                       int phases = kPhaseLocalMerge | kPhaseWrite, bool chain = false, bool allow_pdl = true) {
     const int local_cap = cap > 0 ? cap : PG::kMaxPieces + 16;
     const long long slots = (long long)nb * PG::kSlots;
     const int global_cap = cap > 0 ? cap : (int)(slots + 16 < (1LL << 30) ? slots + 16 : (1LL << 30));
@@ -1334,7 +1338,7 @@ int launch_piece_table(const JobTable &jt, unsigned grid_local, unsigned grid_me
     // per-kernel timing records events between the kernels, which a
     // programmatic (overlapping) launch would blur: off while timing
     // (and only between kernels of one call)
-    const bool pdl = ev == nullptr && phases == (kPhaseLocalMerge | kPhaseWrite);
+    const bool pdl = allow_pdl && ev == nullptr && phases == (kPhaseLocalMerge | kPhaseWrite);
     bool ok = true;
     if (phases & kPhaseLocalMerge) {
         // chained: step 1 may start while the previous call's write-out on
@@ -1425,6 +1429,22 @@ int launch_batch(int conn, JobHeader *hdr, const Job *jobs, void *ws, size_t cap
                            bound, stream);
 }
 
+// A batch on the piece labeller: persistent grids (SMs x occupancy) whose
+// CTAs claim blocks from the job table's counters.  No programmatic overlap
+// between the kernels: a batch is replayed as a captured graph.
+template <class PG>
+int launch_piece_batch(JobHeader *hdr, const Job *jobs, void *ws, size_t capacity, cudaStream_t stream, int cap) {
+    int occ_l = 0, occ_w = 0, sms = 0, occ_m = 0;
+    if (!piece_prepare<PG>(occ_l, occ_w, sms, nullptr, &occ_m)) return -1;
+    JobTable jt{};
+    jt.hdr = hdr;
+    jt.jobs = jobs;
+    jt.total = 0;
+    return launch_piece_table<PG>(jt, (unsigned)(sms * occ_l), (unsigned)(sms * occ_m), (unsigned)(sms * occ_w),
+                                  carve_p<PG>(ws, capacity), capacity, cap, stream,
+                                  kPhaseLocalMerge | kPhaseWrite, false, false);
+}
+
 // One image through a coarse-labelling variant of step 1 (with its
 // counters), on 512x64 blocks; steps 2 and 3 as in the method.
 template <bool kConn8, int kMode>
@@ -1472,7 +1492,7 @@ int launch_variant_c(int mode, const uint8_t *img, int H, int W, size_t pitch, i
 }  // namespace
 
 const char *geo_name(int geo) {
-    static const char *names[kNumGeo] = {"512x64", "256x64", "1024x32", "512x64x8"};
+    static const char *names[kNumGeo] = {"512x64", "256x64", "1024x32", "512x64x8", "512x64p", "256x32p"};
     return (geo >= 0 && geo < kNumGeo) ? names[geo] : "";
 }
 
@@ -1481,6 +1501,8 @@ void geo_block_shape(int geo, int *bw, int *bh) {
         case 1: *bw = G1::kBW; *bh = G1::kBH; break;
         case 2: *bw = G2::kBW; *bh = G2::kBH; break;
         case 3: *bw = G3::kBW; *bh = G3::kBH; break;
+        case 4: *bw = P8::kBW; *bh = P8::kBH; break;
+        case 5: *bw = P8s::kBW; *bh = P8s::kBH; break;
         default: *bw = G0::kBW; *bh = G0::kBH; break;
     }
 }
@@ -1490,6 +1512,8 @@ size_t geo_blocks(int geo, int H, int W) {
         case 1: return blocks_of<G1>(H, W);
         case 2: return blocks_of<G2>(H, W);
         case 3: return blocks_of<G3>(H, W);
+        case 4: return blocks_of<P8>(H, W);
+        case 5: return blocks_of<P8s>(H, W);
         default: return blocks_of<G0>(H, W);
     }
 }
@@ -1499,6 +1523,8 @@ size_t geo_workspace_bytes(int geo, size_t blocks) {
         case 1: return layout_for<G1>(blocks).total;
         case 2: return layout_for<G2>(blocks).total;
         case 3: return layout_for<G3>(blocks).total;
+        case 4: return std::max(layout_p<P8>(blocks).total, layout_p<P4>(blocks).total);
+        case 5: return std::max(layout_p<P8s>(blocks).total, layout_p<P4s>(blocks).total);
         default: return layout_for<G0>(blocks).total;
     }
 }
@@ -1556,10 +1582,13 @@ int label_scratch_view(int H, int W, int conn, void *ws, ScratchView *v) {
 
 int prepare_geo(int geo) {
     GeoLaunch gl;
+    int a, b, c;
     switch (geo) {
         case 1: return geo_launch<G1>(gl) ? 0 : -1;
         case 2: return geo_launch<G2>(gl) ? 0 : -1;
         case 3: return geo_launch<G3>(gl) ? 0 : -1;
+        case 4: return piece_prepare<P8>(a, b, c) && piece_prepare<P4>(a, b, c) ? 0 : -1;
+        case 5: return piece_prepare<P8s>(a, b, c) && piece_prepare<P4s>(a, b, c) ? 0 : -1;
         default: return geo_launch<G0>(gl) ? 0 : -1;
     }
 }
@@ -1570,6 +1599,10 @@ int launch_jobs(int geo, int conn, JobHeader *hdr, const Job *jobs, void *ws, si
         case 1: return launch_batch<G1>(conn, hdr, jobs, ws, capacity, stream, cap);
         case 2: return launch_batch<G2>(conn, hdr, jobs, ws, capacity, stream, cap);
         case 3: return launch_batch<G3>(conn, hdr, jobs, ws, capacity, stream, cap);
+        case 4: return conn == 8 ? launch_piece_batch<P8>(hdr, jobs, ws, capacity, stream, cap)
+                                 : launch_piece_batch<P4>(hdr, jobs, ws, capacity, stream, cap);
+        case 5: return conn == 8 ? launch_piece_batch<P8s>(hdr, jobs, ws, capacity, stream, cap)
+                                 : launch_piece_batch<P4s>(hdr, jobs, ws, capacity, stream, cap);
         default: return launch_batch<G0>(conn, hdr, jobs, ws, capacity, stream, cap);
     }
 }

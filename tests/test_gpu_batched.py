@@ -64,12 +64,12 @@ def test_batched_argument_checks_without_gpu():
     assert lib.ccl_label_batched(arr, 1, 6, None) == ccl.CCL_ERR_INVALID_ARG
     assert lib.ccl_label_batched(None, 0, 8, None) == ccl.CCL_OK
     assert lib.ccl_label_batched_tile(arr, 1, 8, 99, None) == ccl.CCL_ERR_INVALID_ARG
-    assert ccl.ccl_tile_names() == ["512x64", "256x64", "1024x32", "512x64x8"]
+    assert ccl.ccl_tile_names() == ["512x64", "256x64", "1024x32", "512x64x8", "512x64p", "256x32p"]
 
 
 @pytest.mark.gpu
 @pytest.mark.parametrize("conn", (4, 8))
-@pytest.mark.parametrize("tile", (0, 1, 2, 3))
+@pytest.mark.parametrize("tile", (0, 1, 2, 3, 4, 5))
 def test_uneven_batch_every_tile(conn, tile):
     imgs = uneven_batch(24, seed=tile * 10 + conn)
     imgs += [np.zeros((0, 7), np.uint8), np.ones((1, 1), np.uint8), synth.spiral(301),
@@ -118,7 +118,7 @@ def test_autotune_and_cache(tmp_path, monkeypatch):
     pairs = [(torch.from_numpy(im).cuda(), torch.empty(im.shape, dtype=torch.int32, device="cuda"))
              for im in imgs]
     tile = ccl.ccl_autotune_batched(pairs, 8)
-    assert 0 <= tile < 3
+    assert 0 <= tile < len(ccl.ccl_tile_names())
     assert ccl.ccl_batched_tile(pairs, 8) == tile
     check_all(imgs, [lab.cpu().numpy() for _, lab in pairs], 8, "autotuned")
     assert (tmp_path / "tune.txt").read_text().strip().endswith(str(tile))
@@ -137,5 +137,6 @@ def test_uneven_256_batch_full_size():
     """The 256-image batch (H, W uniform in [64, 2048], density uniform in
     [0.2, 0.8], half Bernoulli, half smoothed noise), 8-connectivity."""
     imgs = synth.batch_uneven(256, seed=0)
-    outs = run_batched(imgs, 8, tile=0)
-    check_all(imgs, outs, 8, "batch256")
+    for tile in (0, 4, 5):
+        outs = run_batched(imgs, 8, tile=tile)
+        check_all(imgs, outs, 8, f"batch256 tile={tile}")
