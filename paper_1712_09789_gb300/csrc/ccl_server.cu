@@ -299,7 +299,8 @@ int tile_for(ccl_server *s, const Request &r) {
     int &tile = s->tile[r.conn == 8 ? 1 : 0];
     if (tile < 0) {
         const ccl_image im{r.host_img, r.host_labels, r.H, r.W, r.pitch};
-        if (ccl_batched_tile(&im, 1, r.conn, &tile) != CCL_OK || tile < 0 || tile >= ccl::kNumGeo) tile = 0;
+        // untuned: the piece labeller's 512x64 blocks
+        if (ccl_batched_tile(&im, 1, r.conn, &tile) != CCL_OK || tile < 0 || tile >= ccl::kNumGeo) tile = 4;
     }
     return tile;
 }
