@@ -6,10 +6,15 @@
 // Canonical labels make the components easy to index: a pixel is its
 // component's root when its label equals its own raster position plus one,
 // and the roots in raster order are the components in label order.
-//   k_stats_count       roots per chunk of 8192 consecutive pixels
+//   k_stats_count       a bit per pixel (1 = root), and roots per chunk of
+//                       8192 consecutive pixels
 //   k_stats_scan        exclusive prefix over the chunk counts (one CTA)
-//   k_stats_index       dense index of every root (rootmap[p]), component
-//                       records initialised in label order
+//   k_stats_index       per 32-pixel word, the roots in the chunk's earlier
+//                       words; component records initialised in label
+//                       order.  The dense index of root p is then
+//                       chunk prefix + word prefix + popcount below p (the
+//                       bitmap and the prefixes are 3/16 B per pixel and
+//                       stay in L2, where a 4 B/pixel index map did not)
 //   k_stats_accumulate  tiles of 32 x 256 pixels: each pixel's component is
 //                       looked up and its statistics folded into a shared-
 //                       memory hash table, one global update per component
@@ -36,13 +41,29 @@ __device__ __forceinline__ bool is_root(const int32_t *labels, long long p) {
     return labels[p] == (int32_t)(p + 1);
 }
 
-__global__ void __launch_bounds__(kStatThreads) k_stats_count(const int32_t *labels, long long n, uint32_t *counts) {
+// Word j of chunk c holds pixels c * kChunk + 32 * j .. + 31 (a warp's step).
+__global__ void __launch_bounds__(kStatThreads) k_stats_count(const int32_t *labels, long long n, uint32_t *bits,
+                                                               uint32_t *counts) {
     __shared__ uint32_t warp_sum[kStatThreads / 32];
     const long long base = (long long)blockIdx.x * kChunk;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t c = 0;
-    for (int i = 0; i < kChunk / kStatThreads; ++i) {
-        const long long p = base + i * kStatThreads + threadIdx.x;
-        if (p < n && is_root(labels, p)) ++c;
+    // all of a thread's loads first (independent, in flight together), then
+    // the ballots
+    constexpr int kSteps = kChunk / kStatThreads;
+    int32_t v[kSteps];
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+        const long long p = base + (long long)(i * kStatThreads) + 32 * w + lane;
+        v[i] = __ldg(labels + (p < n ? p : n - 1));  // unconditional: no branch between the loads
+    }
+#pragma unroll
+    for (int i = 0; i < kSteps; ++i) {
+        const long long q = base + (long long)(i * kStatThreads) + 32 * w;  // first pixel of the warp's word
+        const long long p = q + lane;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, p < n && v[i] == (int32_t)(p + 1));
+        if (lane == 0 && q < n) bits[q >> 5] = m;
+        c += (uint32_t)(lane == 0 ? __popc(m) : 0);
     }
     c = __reduce_add_sync(0xFFFFFFFFu, c);
     if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = c;
@@ -82,44 +103,52 @@ __global__ void __launch_bounds__(1024) k_stats_scan(uint32_t *counts, int nchun
     if (threadIdx.x == 0) counts[nchunks] = carry;
 }
 
-__global__ void __launch_bounds__(kStatThreads) k_stats_index(const int32_t *labels, long long n,
-                                                               const uint32_t *base, uint32_t *rootmap,
+__global__ void __launch_bounds__(kStatThreads) k_stats_index(const uint32_t *bits, long long n,
+                                                               const uint32_t *base, uint16_t *wpre,
                                                                ccl_component *out, int capacity) {
-    __shared__ uint32_t warp_cnt[kStatThreads / 32];
-    const long long start = (long long)blockIdx.x * kChunk;
+    __shared__ uint32_t warp_sum[kStatThreads / 32];
+    static_assert(kChunk / 32 == kStatThreads, "one word of the chunk per thread");
+    const long long word = (long long)blockIdx.x * (kChunk / 32) + threadIdx.x;
+    const long long nwords = (n + 31) >> 5;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    uint32_t next = base[blockIdx.x];  // dense index of the chunk's next root (same in every thread)
-    for (int i = 0; i < kChunk / kStatThreads; ++i) {
-        const long long p = start + i * kStatThreads + threadIdx.x;
-        const bool r = p < n && is_root(labels, p);
-        const unsigned m = __ballot_sync(0xFFFFFFFFu, r);
-        if (lane == 0) warp_cnt[w] = __popc(m);
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-        for (int k = 0; k < kStatThreads / 32; ++k) {
-            const uint32_t c = warp_cnt[k];
-            if (k < w) before += c;
-            total += c;
-        }
-        if (r) {
-            const uint32_t idx = next + before + __popc(m & ((1u << lane) - 1u));
-            rootmap[p] = idx;
-            if ((int)idx < capacity) {
-                ccl_component c;
-                c.label = (int32_t)(p + 1);
-                c.area = 0;
-                c.x0 = INT_MAX;
-                c.y0 = INT_MAX;
-                c.x1 = -1;
-                c.y1 = -1;
-                c.sum_x = 0;
-                c.sum_y = 0;
-                out[idx] = c;
-            }
-        }
-        next += total;
-        __syncthreads();
+    const uint32_t m = word < nwords ? bits[word] : 0u;
+    const uint32_t c = __popc(m);
+    uint32_t incl = c;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += v;
     }
+    if (lane == 31) warp_sum[w] = incl;
+    __syncthreads();
+    uint32_t before = incl - c;
+    for (int k = 0; k < w; ++k) before += warp_sum[k];
+    if (word < nwords) wpre[word] = (uint16_t)before;
+    uint32_t idx = base[blockIdx.x] + before;
+    for (uint32_t r = m; r; r &= r - 1, ++idx) {
+        const long long p = word * 32 + (__ffs(r) - 1);
+        if ((int)idx < capacity) {
+            ccl_component cc;
+            cc.label = (int32_t)(p + 1);
+            cc.area = 0;
+            cc.x0 = INT_MAX;
+            cc.y0 = INT_MAX;
+            cc.x1 = -1;
+            cc.y1 = -1;
+            cc.sum_x = 0;
+            cc.sum_y = 0;
+            out[idx] = cc;
+        }
+    }
+}
+
+// Dense index of pixel p when it is a root, else kEmpty.
+__device__ __forceinline__ uint32_t root_index(const uint32_t *bits, const uint16_t *wpre, const uint32_t *base,
+                                               long long p) {
+    const uint32_t m = bits[p >> 5];
+    const uint32_t b = 1u << (p & 31);
+    if (!(m & b)) return kEmpty;
+    return base[p / kChunk] + wpre[p >> 5] + __popc(m & (b - 1u));
 }
 
 // Per-tile statistics in tile coordinates (x - tx0, y - ty0): every field
@@ -146,9 +175,9 @@ __device__ __forceinline__ void fold_global(ccl_component *out, uint32_t k, int 
 }
 
 __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t *labels, int H, int W,
-                                                                    const uint32_t *rootmap, const uint32_t *counts,
-                                                                    int nchunks, ccl_component *out, int capacity,
-                                                                    int *bad) {
+                                                                    const uint32_t *bits, const uint16_t *wpre,
+                                                                    const uint32_t *counts, int nchunks,
+                                                                    ccl_component *out, int capacity, int *bad) {
     __shared__ StatSmem sm;
     for (int i = threadIdx.x; i < kHash; i += kStatThreads) {
         sm.key[i] = kEmpty;
@@ -179,11 +208,11 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t
             if (l != 0) {
                 // a label must name a root of the image (canonical labels);
                 // anything else is counted and skipped
-                if (l < 0 || (long long)l > n || !is_root(labels, (long long)l - 1)) {
+                const uint32_t r = (l < 0 || (long long)l > n) ? kEmpty : root_index(bits, wpre, counts, (long long)l - 1);
+                if (r == kEmpty) {
                     ++nbad;
                 } else {
-                    k = rootmap[l - 1];
-                    if (k >= lim) k = kEmpty;
+                    k = r < lim ? r : kEmpty;
                 }
             }
         }
@@ -243,23 +272,40 @@ __global__ void __launch_bounds__(kStatThreads) k_stats_accumulate(const int32_t
 
 }  // namespace
 
-size_t stats_workspace_bytes(int H, int W) {
-    const long long n = (long long)H * W;
-    const long long nchunks = (n + kChunk - 1) / kChunk;
-    return (size_t)((n * 4 + 255) & ~255LL) + (size_t)((nchunks + 1 + 1) * 4 + 255);
+// Scratch: the root bitmap (n / 8 bytes), the word prefixes (n / 16 bytes),
+// the chunk counts.
+namespace {
+struct StatsLayout {
+    size_t bits, wpre, counts, total;
+};
+StatsLayout stats_layout(long long n) {
+    const long long nwords = (n + 31) / 32, nchunks = (n + kChunk - 1) / kChunk;
+    StatsLayout l;
+    size_t off = 0;
+    l.bits = off;   off += ((size_t)nwords * 4 + 255) & ~(size_t)255;
+    l.wpre = off;   off += ((size_t)nwords * 2 + 255) & ~(size_t)255;
+    l.counts = off; off += ((size_t)(nchunks + 2) * 4 + 255) & ~(size_t)255;
+    l.total = off;
+    return l;
 }
+}  // namespace
+
+size_t stats_workspace_bytes(int H, int W) { return stats_layout((long long)H * W).total; }
 
 int launch_stats(const int32_t *labels, int H, int W, ccl_component *out, int capacity, void *ws,
                  uint32_t *count_dev, int *bad_dev, cudaStream_t stream) {
     const long long n = (long long)H * W;
     const int nchunks = (int)((n + kChunk - 1) / kChunk);
-    uint32_t *rootmap = static_cast<uint32_t *>(ws);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(static_cast<char *>(ws) + ((n * 4 + 255) & ~255LL));
-    k_stats_count<<<nchunks, kStatThreads, 0, stream>>>(labels, n, counts);
+    const StatsLayout lay = stats_layout(n);
+    char *w8 = static_cast<char *>(ws);
+    uint32_t *bits = reinterpret_cast<uint32_t *>(w8 + lay.bits);
+    uint16_t *wpre = reinterpret_cast<uint16_t *>(w8 + lay.wpre);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(w8 + lay.counts);
+    k_stats_count<<<nchunks, kStatThreads, 0, stream>>>(labels, n, bits, counts);
     k_stats_scan<<<1, 1024, 0, stream>>>(counts, nchunks);
-    k_stats_index<<<nchunks, kStatThreads, 0, stream>>>(labels, n, counts, rootmap, out, capacity);
+    k_stats_index<<<nchunks, kStatThreads, 0, stream>>>(bits, n, counts, wpre, out, capacity);
     const dim3 grid((W + kTileW - 1) / kTileW, (H + kTileH - 1) / kTileH);
-    k_stats_accumulate<<<grid, kStatThreads, 0, stream>>>(labels, H, W, rootmap, counts, nchunks, out, capacity,
+    k_stats_accumulate<<<grid, kStatThreads, 0, stream>>>(labels, H, W, bits, wpre, counts, nchunks, out, capacity,
                                                          bad_dev);
     if (cudaMemcpyAsync(count_dev, counts + nchunks, sizeof(uint32_t), cudaMemcpyDeviceToDevice, stream) !=
         cudaSuccess)
