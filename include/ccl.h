@@ -371,9 +371,12 @@ ccl_status ccl_label_variant(const uint8_t *img, int H, int W, size_t pitch, int
  *                background, else 1 + the smallest raster position
  *                x + y*W + z*W*H of the voxel's component.
  *   stream       cudaStream_t; the call is stream-ordered and asynchronous.
- * Uses a library-owned scratch buffer per (device, stream) of about 2 bytes
- * per voxel (each voxel's block-local root), grown on demand (a cudaMalloc;
- * call once outside stream capture before capturing).  Returns CCL_ERR_INVALID_ARG for NULL pointers, negative sizes,
+ * Uses a library-owned scratch buffer per (device, stream) of about 4.3
+ * bytes per voxel, grown on demand (a cudaMalloc; call once outside stream
+ * capture before capturing).  Per block of 32 x 16 x 16 voxels it holds the
+ * row masks, one 16-bit value per run or piece, the border-slot record of
+ * every face voxel and the global union-find entries of the border slots,
+ * each sized for the worst case; a call touches only the used part.  Returns CCL_ERR_INVALID_ARG for NULL pointers, negative sizes,
  * pitch < W, connectivity not in {6,26} or overlapping img/labels;
  * CCL_ERR_UNSUPPORTED when D*H*W > 2^31 - 2; CCL_ERR_OUT_OF_MEMORY when the
  * scratch cannot grow; CCL_ERR_CUDA when a launch fails.  Iteration caps are

@@ -27,7 +27,7 @@ std::map<std::pair<int, cudaStream_t>, DevBuf> g_scratch;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_img;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_host_lab;
 std::map<std::pair<int, cudaStream_t>, DevBuf> g_stats;  // component statistics scratch
-std::map<std::pair<int, cudaStream_t>, DevBuf> g_volume; // face records of the 3D labelling
+std::map<std::pair<int, cudaStream_t>, DevBuf> g_volume; // workspace of the 3D labelling
 
 // ccl_label() alternates between two halves of its scratch per (device,
 // stream), so that a labelling's step 1 may start (chained) while the

@@ -15,22 +15,23 @@
 //                the larger block position to the smaller, so a root is its
 //                component's first voxel in raster order.  Roots of
 //                components that touch a neighbouring block's foreground get
-//                a forest entry in `labels` (own position + 1), and every
-//                voxel's local root goes to a root record (2 bytes per
-//                voxel).
-//   k_vol_merge  step 2 (Sec. 3.2): every voxel pair across a block face is
-//                joined in the global forest (lock-free atomicMin union, the
-//                pairs of roots deduplicated per CTA); a pair that crosses
-//                several faces is taken by the z face, else the y face, else
-//                the x face, so each pair is seen once.
-//   k_vol_write  step 3 (Sec. 3.3): each block root's final label is found
-//                (border roots by a walk of the global forest) and every voxel
-//                of the block is written once from its root record, as whole
-//                128-byte rows.
+//                a border slot and an entry of the global union-find over
+//                slots, keyed by their global position (ID conversion, Sec.
+//                3.1.4).  Outputs: the row masks, one 16-bit value per element
+//                (border slot or block position of its root) and, for every
+//                voxel of the six block faces, the slot of its root.
+//   k_vol_merge  step 2 (Sec. 3.2): every voxel pair across a block face
+//                joins its two slots in the global union-find (lock-free
+//                atomicMin union, the pairs deduplicated per CTA); a pair
+//                that crosses several faces is taken by the z face, else the
+//                y face, else the x face, so each pair is seen once.
+//   k_vol_write  step 3 (Sec. 3.3): the element index of every voxel is
+//                rebuilt from the row masks, each element's value becomes its
+//                final label (border slots by a root-find in the merged
+//                union-find) and every voxel of the block is written once, as
+//                whole 128-byte rows.
 // Labels: 1 + min raster position x + y*W + z*W*H of the component, 0 for
-// background.  The forest lives in `labels` at border-root positions only;
-// the write-out overwrites such an entry with its final value, which is still
-// a pointer to the same tree's root, so concurrent walks stay valid.
+// background.  Nothing but the final labels is written to `labels`.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -45,30 +46,50 @@ constexpr int kVX = 32, kVY = 16, kVZ = 16;  // block: voxels along x, y, z
 constexpr int kVRows = kVY * kVZ;            // rows of 32 voxels per block
 constexpr int kVThreads = kVRows;            // one thread per row
 constexpr int kVIds = kVRows * kVX;          // ids: row * 32 + x (row = z * kVY + y)
-constexpr uint16_t kNoRoot = 0xFFFF;         // face record of a background voxel
-constexpr int kPairHash = 2048;              // root pairs remembered per CTA in the merge
+constexpr int kPairHash = 2048;              // slot pairs remembered per CTA in the merge
 constexpr unsigned long long kNoPair = ~0ull;
-// Root records: per block, one u16 per voxel slot (row * 32 + x), block
-// after block: the local root id of the voxel, with kBorderBit set when that
-// root's component reaches a block face; kNoRoot for background.
-constexpr uint16_t kBorderBit = 0x8000;
-constexpr uint16_t kIdMask = 0x7FFF;
-static_assert(kVIds <= kIdMask, "ids must fit the root records");
-static_assert((kVIds * 2) % 16 == 0, "root records stay 16-byte aligned per block");
+// Element values (one u16 per element, in element order): the block
+// position (id) of the element's root, or kSlotFlag | border slot of that
+// root when its component touches a neighbouring block.
+constexpr uint16_t kSlotFlag = 0x8000;
+// Elements per block at most: 16 runs in each row (6-connectivity), 16
+// pieces in each of the 64 bundles (26-connectivity).
+constexpr int kVMaxElems = kVRows * kVX / 2;
+// Border slots per block at most: a border root's component holds a
+// foreground voxel of a block face, so there are no more of them than face
+// voxels.
+constexpr int kVFaceVoxels = 2 * (kVY * kVX + kVZ * kVX + kVZ * kVY);
+constexpr int kVSlots = kVFaceVoxels;
+// Face records: for every voxel of the six faces, the border slot of its
+// root, kNoSlot for background (and for a root without a slot, whose
+// component meets no foreground across the face).  Per block:
+//   [kFaceZ0 + y*32 + x]   slice z = 0       [kFaceZ1 + y*32 + x]  slice z = 15
+//   [kFaceY0 + z*32 + x]   rows y = 0        [kFaceY1 + z*32 + x]  rows y = 15
+//   [kFaceX0 + z*16 + y]   voxels x = 0      [kFaceX1 + z*16 + y]  voxels x = 31
+constexpr uint16_t kNoSlot = 0xFFFF;
+constexpr int kFaceZ0 = 0, kFaceZ1 = kVY * kVX, kFaceY0 = 2 * kVY * kVX, kFaceY1 = kFaceY0 + kVZ * kVX;
+constexpr int kFaceX0 = kFaceY1 + kVZ * kVX, kFaceX1 = kFaceX0 + kVRows;
+static_assert(kFaceX1 + kVRows == kVFaceVoxels, "face record layout");
+static_assert(kVIds < kSlotFlag && kVSlots < kSlotFlag, "ids and slots must fit the element values");
+static_assert(kVMaxElems < 65536 && kVSlots < 65536, "the step-1 scan packs both counts in 16 bits");
 
 __device__ int g_volume_error = 0;
 
 struct VolArgs {
     const uint8_t *img;
     int32_t *labels;
-    uint16_t *roots;  // root records, kVIds per block
-    uint16_t *xface;  // the root records of x = 0 and x = 31, [block][2][row]
+    uint32_t *mask;   // row masks, kVRows per block
+    uint16_t *vals;   // element values, kVMaxElems per block (the first ones used)
+    uint16_t *face;   // face records, kVFaceVoxels per block
+    uint64_t *P;      // global union-find over border slots, kVSlots per block
+    uint32_t *ns;     // border slots per block
     unsigned long long pitch;
     int D, H, W;
     int n;  // voxels, D * H * W
     int nbx, nby, nbz;
     int vec_in;
     int local_cap, global_cap;
+    uint32_t bound;  // slots in all: blocks * kVSlots
 };
 
 struct VolSmem {
@@ -136,51 +157,29 @@ __device__ void v_union(uint32_t *par, int a, int b, int cap, int &err) {
     err |= kErrLocalCap;
 }
 
-// Global forest in `labels`: the entry of a border root holds parent + 1.
-// A parent outside the volume can only come from an entry that a capped run
-// left unset; the walk then stops with the cap error instead of reading it.
-__device__ int vg_find(int32_t *lab, int n, int g, int cap, int &err) {
-    for (int i = 0; i < cap; ++i) {
-        const int p = __ldcg(lab + g) - 1;
-        if (p == g) return g;
-        if ((unsigned)p >= (unsigned)n) break;
-        const int q = __ldcg(lab + p) - 1;
-        if (q == p) return p;
-        if ((unsigned)q >= (unsigned)n) break;
-        __stcg(lab + g, q + 1);
-        g = q;
+// Exclusive prefix sum of v over the CTA's kVThreads threads, in thread
+// order; `total` gets the sum over all threads.  wtot holds kVThreads / 32
+// words; the call ends with the barrier after which they may be reused.
+__device__ __forceinline__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t *wtot, uint32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t s = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, s, d);
+        if (lane >= d) s += u;
     }
-    err |= kErrGlobalCap;
-    return g;
-}
-
-__device__ void vg_union(int32_t *lab, int n, int a, int b, int cap, int &err) {
-    for (int i = 0; i < cap; ++i) {
-        a = vg_find(lab, n, a, cap, err);
-        b = vg_find(lab, n, b, cap, err);
-        if (a == b || err) return;
-        if (a < b) {
-            const int t = a;
-            a = b;
-            b = t;
-        }
-        const int old = atomicMin(lab + a, b + 1) - 1;
-        if (old == a) return;
-        if ((unsigned)old >= (unsigned)n) break;
-        a = old;
+    if (lane == 31) wtot[warp] = s;
+    __syncthreads();
+    uint32_t base = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kVThreads / 32; ++w) {
+        const uint32_t x = wtot[w];
+        if (w < warp) base += x;
+        tot += x;
     }
-    err |= kErrGlobalCap;
-}
-
-__device__ int vg_find_ro(const int32_t *lab, int n, int g, int cap, int &err) {
-    for (int i = 0; i < cap; ++i) {
-        const int p = __ldcg(lab + g) - 1;
-        if (p == g) return g;
-        if ((unsigned)p >= (unsigned)n) break;
-        g = p;
-    }
-    err |= kErrGlobalCap;
-    return g;
+    total = tot;
+    __syncthreads();
+    return base + s - v;
 }
 
 // Contacts of the runs of row r (mask m, run starts st) with the runs of the
@@ -462,45 +461,107 @@ __device__ __forceinline__ void block_coords(const VolArgs &a, int &bx, int &by,
     bz = b / (a.nbx * a.nby);
 }
 
+// Element starts of thread t: the run starts of its row (6-connectivity),
+// the piece starts of bundle t (26-connectivity, threads 0..63).  Elements
+// are numbered thread after thread, start after start; *o gets the mask the
+// starts belong to (the row, or the bundle's OR).
 template <bool k26>
-__global__ void __launch_bounds__(kVThreads) k_vol_local(VolArgs a) {
+__device__ __forceinline__ uint32_t element_starts(const uint32_t *mask, int t, uint32_t &o, int &r0) {
+    if (k26) {
+        constexpr int kBY = kVY / 2, kBZ = kVZ / 2;
+        r0 = 2 * (t / kBY) * kVY + 2 * (t % kBY);
+        o = t < kBY * kBZ ? (mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1]) : 0u;
+    } else {
+        r0 = t;
+        o = mask[t];
+    }
+    return o & ~(o << 1);
+}
+
+// Index of the element that holds voxel x of row r (x must be foreground),
+// from the row masks and the per-thread element offsets eoff.
+template <bool k26>
+__device__ __forceinline__ int element_at(const uint32_t *mask, const uint16_t *eoff, int r, int x) {
+    if (k26) {
+        const int r0 = (r / kVY & ~1) * kVY + (r % kVY & ~1);
+        const uint32_t o = mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1];
+        const int t = (r / kVY / 2) * (kVY / 2) + (r % kVY) / 2;
+        return (int)eoff[t] + __popc(o & ~(o << 1) & upto(x)) - 1;
+    }
+    const uint32_t m = mask[r];
+    return (int)eoff[r] + __popc(m & ~(m << 1) & upto(x)) - 1;
+}
+
+template <bool k26>
+__global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     __shared__ VolSmem sm;
+    __shared__ uint16_t sbase[kVRows];  // border slot of the first marked root of each row
+    __shared__ uint32_t wtot[kVThreads / 32];
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     int err = 0;
     const uint32_t m = vol_local<k26>(sm, a, bx, by, bz, err);
     const int r = threadIdx.x, y = r % kVY, z = r / kVY;
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
+    const size_t b = blockIdx.x;
 
-    // forest entries of the border roots on the own row
-    for (uint32_t t = sm.border[r]; t; t &= t - 1) {
-        const long long g = vpos(a, gx0 + lobit(t), gy0 + y, gz0 + z);
-        a.labels[g] = (int32_t)(g + 1);
-    }
+    // border slots of the marked roots and element numbers, by one scan of
+    // both counts (16 bits each)
+    uint32_t o;
+    int r0;
+    const uint32_t est = element_starts<k26>(sm.mask, r, o, r0);
+    const uint32_t bd = sm.border[r];
+    uint32_t tot;
+    const uint32_t pre = cta_exclusive_scan((uint32_t)__popc(est) | ((uint32_t)__popc(bd) << 16), wtot, tot);
+    sbase[r] = (uint16_t)(pre >> 16);
+    if (r == 0) a.ns[b] = tot >> 16;
+    a.mask[b * kVRows + r] = m;
+    __syncthreads();
+    const auto marked = [&](int root) { return ((sm.border[root >> 5] >> (root & 31)) & 1u) != 0u; };
+    const auto border_slot = [&](int root) {
+        return (int)sbase[root >> 5] + __popc(sm.border[root >> 5] & ((1u << (root & 31)) - 1u));
+    };
 
-    // root records of the block, one warp per row (64-byte stores)
-    uint16_t *rec = a.roots + (size_t)blockIdx.x * kVIds;
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
-    for (int row = warp; row < kVRows; row += kVThreads / 32) {
-        const uint32_t mr = sm.mask[row];
-        uint16_t v = kNoRoot;
-        if ((mr >> lane) & 1u) {
-            const int root = voxel_root<k26>(sm, row, lane);
-            v = (uint16_t)(root | (((sm.border[root / kVX] >> (root % kVX)) & 1u) ? kBorderBit : 0));
+    // global union-find entries of the own row's border roots, keyed by the
+    // root's global position (its component's first voxel in the block)
+    {
+        const uint32_t s0 = (uint32_t)(b * kVSlots) + (pre >> 16);
+        uint32_t k = 0;
+        for (uint32_t t = bd; t; t &= t - 1, ++k) {
+            const uint32_t key = (uint32_t)vpos(a, gx0 + lobit(t), gy0 + y, gz0 + z);
+            a.P[s0 + k] = pack_slot(key, s0 + k);
         }
-        rec[row * kVX + lane] = v;
-        // the x faces once more, packed: the merge reads them per row
-        uint16_t *xf = a.xface + (size_t)blockIdx.x * 2 * kVRows;
-        if (lane == 0) xf[row] = v;
-        if (lane == kVX - 1) xf[kVRows + row] = v;
     }
+    // element values
+    {
+        uint16_t *V = a.vals + b * kVMaxElems + (pre & 0xFFFFu);
+        const Bundle bu = (k26 && est) ? load_bundle(sm, r0) : Bundle{0u, 0u, 0u, 0u, 0};
+        for (uint32_t t = est; t; t &= t - 1, ++V) {
+            const int s = lobit(t);
+            const int key = k26 ? piece_key(bu, s, run_end(o, s)) : r * kVX + s;
+            const int root = (int)sm.par[slot(key)];
+            *V = marked(root) ? (uint16_t)(kSlotFlag | border_slot(root)) : (uint16_t)root;
+        }
+    }
+    // face records: the slices z = 0 and 15 and the rows y = 0 and 15 one
+    // warp per row (lane = x), the voxels x = 0 and 31 of the own row
+    uint16_t *F = a.face + b * kVFaceVoxels;
+    const auto face_slot = [&](int row, int x) -> uint16_t {
+        if (!((sm.mask[row] >> x) & 1u)) return kNoSlot;
+        const int root = voxel_root<k26>(sm, row, x);
+        return marked(root) ? (uint16_t)border_slot(root) : kNoSlot;
+    };
+    {
+        const int lane = r & 31, warp = r >> 5;
+        for (int j = warp; j < 4 * 16; j += kVThreads / 32) {
+            const int f = j >> 4, i = j & 15;
+            const int row = f == 0 ? i : f == 1 ? (kVZ - 1) * kVY + i : f == 2 ? i * kVY : i * kVY + kVY - 1;
+            F[f * (kVY * kVX) + i * kVX + lane] = face_slot(row, lane);
+        }
+    }
+    F[kFaceX0 + r] = face_slot(r, 0);
+    F[kFaceX1 + r] = face_slot(r, kVX - 1);
     if (err) atomicOr(&g_volume_error, err);
-}
-
-// Position of local id `id` of block (bx, by, bz).
-__device__ __forceinline__ int id_pos(const VolArgs &a, int bx, int by, int bz, int id) {
-    const int row = id / kVX;
-    return (int)vpos(a, bx * kVX + id % kVX, by * kVY + row % kVY, bz * kVZ + row / kVY);
 }
 
 template <bool k26>
@@ -508,20 +569,21 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
-    const uint16_t *own = a.roots + (size_t)blockIdx.x * kVIds;
+    const uint32_t b = blockIdx.x;
+    const uint16_t *own = a.face + (size_t)b * kVFaceVoxels;
     constexpr int kR = k26 ? 1 : 0;
-    // pairs of roots already joined by this CTA: most face voxels of a
-    // component repeat the pair of their neighbours
+    // slot pairs already joined by this CTA: most face voxels of a component
+    // repeat the pair of their neighbours
     __shared__ unsigned long long seen[kPairHash];
     for (int i = threadIdx.x; i < kPairHash; i += kVThreads) seen[i] = kNoPair;
     __syncthreads();
     int err = 0;
-    int last_q = -1, last_p = -1;
-    auto join = [&](int q, int p) {
+    uint32_t last_q = ~0u, last_p = ~0u;
+    auto join = [&](uint32_t q, uint32_t p) {
         if (q == last_q && p == last_p) return;
         last_q = q;
         last_p = p;
-        const unsigned long long key = ((unsigned long long)(unsigned)q << 32) | (unsigned)p;
+        const unsigned long long key = ((unsigned long long)q << 32) | p;
         unsigned h = (unsigned)((key * 0x9E3779B97F4A7C15ull) >> 40) & (kPairHash - 1);
         for (int i = 0; i < 16; ++i, h = (h + 1) & (kPairHash - 1)) {
             unsigned long long cur = ((volatile unsigned long long *)seen)[h];
@@ -529,67 +591,62 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
             if (cur == key) return;      // joined by another thread of the CTA
             if (cur == kNoPair) break;   // claimed: this thread joins it
         }
-        vg_union(a.labels, a.n, q, p, a.global_cap, err);
+        union_global(a.P, q, p, a.global_cap, err, a.bound);
     };
+    const auto gslot = [](uint32_t blk, int k) { return blk * (uint32_t)kVSlots + (uint32_t)k; };
     // z face: own slice 0 against the last slice of the blocks below
     if (bz > 0) {
         for (int e = threadIdx.x; e < kVY * kVX; e += kVThreads) {
-            const int q = own[e] & kIdMask;  // slice 0: row = y, e = y * 32 + x
-            if (q == kIdMask) continue;
+            const int q = own[kFaceZ0 + e];  // e = y * 32 + x
+            if (q == kNoSlot) continue;
             const int gx = gx0 + e % kVX, gy = gy0 + e / kVX;
-            const int qg = id_pos(a, bx, by, bz, q);
             for (int dy = -kR; dy <= kR; ++dy) {
                 for (int dx = -kR; dx <= kR; ++dx) {
                     const int nx = gx + dx, ny = gy + dy;
                     if (nx < 0 || ny < 0 || nx >= a.W || ny >= a.H) continue;
-                    const int nbx = nx / kVX, nby = ny / kVY;
-                    const uint16_t *nr = a.roots + (size_t)(((bz - 1) * a.nby + nby) * a.nbx + nbx) * kVIds;
-                    const int p = nr[((kVZ - 1) * kVY + ny % kVY) * kVX + nx % kVX] & kIdMask;
-                    if (p != kIdMask) join(qg, id_pos(a, nbx, nby, bz - 1, p));
+                    const uint32_t nb = (uint32_t)(((bz - 1) * a.nby + ny / kVY) * a.nbx + nx / kVX);
+                    const int p = a.face[(size_t)nb * kVFaceVoxels + kFaceZ1 + (ny % kVY) * kVX + nx % kVX];
+                    if (p != kNoSlot) join(gslot(b, q), gslot(nb, p));
                 }
             }
         }
     }
-    // y face: own row y = 0 against row y = last of the blocks in front, in
-    // the same z block
+    // y face: own rows y = 0 against the rows y = 15 of the blocks in front,
+    // in the same z block
     if (by > 0) {
         for (int e = threadIdx.x; e < kVZ * kVX; e += kVThreads) {
+            const int q = own[kFaceY0 + e];  // e = z * 32 + x
+            if (q == kNoSlot) continue;
             const int z = e / kVX, gx = gx0 + e % kVX;
-            const int q = own[z * kVY * kVX + e % kVX] & kIdMask;  // row y = 0 of slice z
-            if (q == kIdMask) continue;
-            const int qg = id_pos(a, bx, by, bz, q);
             for (int dz = -kR; dz <= kR; ++dz) {
                 const int zz = z + dz;
                 if (zz < 0 || zz >= kVZ || gz0 + zz >= a.D) continue;
                 for (int dx = -kR; dx <= kR; ++dx) {
                     const int nx = gx + dx;
                     if (nx < 0 || nx >= a.W) continue;
-                    const int nbx = nx / kVX;
-                    const uint16_t *nr = a.roots + (size_t)((bz * a.nby + by - 1) * a.nbx + nbx) * kVIds;
-                    const int p = nr[(zz * kVY + kVY - 1) * kVX + nx % kVX] & kIdMask;
-                    if (p != kIdMask) join(qg, id_pos(a, nbx, by - 1, bz, p));
+                    const uint32_t nb = (uint32_t)((bz * a.nby + by - 1) * a.nbx + nx / kVX);
+                    const int p = a.face[(size_t)nb * kVFaceVoxels + kFaceY1 + zz * kVX + nx % kVX];
+                    if (p != kNoSlot) join(gslot(b, q), gslot(nb, p));
                 }
             }
         }
     }
-    // x face: own first voxels against the last voxels of the block to the
+    // x face: own voxels x = 0 against the voxels x = 31 of the block to the
     // left, in the same y and z block
     if (bx > 0) {
-        const uint16_t *ox = a.xface + (size_t)blockIdx.x * 2 * kVRows;
-        const uint16_t *nx = a.xface + (size_t)(blockIdx.x - 1) * 2 * kVRows;
+        const uint16_t *nf = a.face + (size_t)(b - 1) * kVFaceVoxels;
         for (int r = threadIdx.x; r < kVRows; r += kVThreads) {
-            const int q = ox[r] & kIdMask;  // voxel x = 0 of row r
-            if (q == kIdMask) continue;
+            const int q = own[kFaceX0 + r];
+            if (q == kNoSlot) continue;
             const int y = r % kVY, z = r / kVY;
-            const int qg = id_pos(a, bx, by, bz, q);
             for (int dz = -kR; dz <= kR; ++dz) {
                 const int zz = z + dz;
                 if (zz < 0 || zz >= kVZ || gz0 + zz >= a.D) continue;
                 for (int dy = -kR; dy <= kR; ++dy) {
                     const int yy = y + dy;
                     if (yy < 0 || yy >= kVY || gy0 + yy >= a.H) continue;
-                    const int p = nx[kVRows + zz * kVY + yy] & kIdMask;  // voxel x = 31
-                    if (p != kIdMask) join(qg, id_pos(a, bx - 1, by, bz, p));
+                    const int p = nf[kFaceX1 + zz * kVY + yy];
+                    if (p != kNoSlot) join(gslot(b, q), gslot(b - 1, p));
                 }
             }
         }
@@ -597,70 +654,55 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     if (err) atomicOr(&g_volume_error, err);
 }
 
-// Step 3 from the root records: every block root that is a voxel of the
-// own row gets its final label (border roots by a walk of the global
-// forest), then every voxel of the block is written once.
+// Step 3: the element index of every voxel from the row masks, the final
+// label of every element (border slots through a root-find in the merged
+// union-find), then every voxel of the block written once.
+template <bool k26>
 __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
-    constexpr int kWalks = 1024;      // marked roots walked by the whole CTA
-    __shared__ uint32_t fin[kVIds];   // final label by root id
-    __shared__ uint16_t walk[kWalks]; // marked roots of the block
-    __shared__ int nwalk;
+    __shared__ uint32_t mask[kVRows];
+    __shared__ uint16_t eoff[kVThreads];  // first element of each thread's row or bundle
+    __shared__ uint32_t wtot[kVThreads / 32];
+    __shared__ int fin[kVSlots];          // final label by border slot
+    __shared__ int lab[kVMaxElems];       // final label by element
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     const int gx0 = bx * kVX, gy0 = by * kVY, gz0 = bz * kVZ;
-    const uint16_t *rec = a.roots + (size_t)blockIdx.x * kVIds;
-    int err = 0;
-    if (threadIdx.x == 0) nwalk = 0;
+    const size_t b = blockIdx.x;
+    const int t = threadIdx.x;
+    mask[t] = a.mask[b * kVRows + t];
     __syncthreads();
-    // roots of the own row: unmarked ones are final at once, marked ones are
-    // listed so that the forest walks (chains of dependent loads) spread
-    // over all threads; a full list leaves the rest to the thread that found
-    // them
-    {
-        const int r = threadIdx.x, gy = gy0 + r % kVY, gz = gz0 + r / kVY;
-        if (gy < a.H && gz < a.D) {
-            const uint4 *row = reinterpret_cast<const uint4 *>(rec + r * kVX);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint4 w = __ldg(row + c);  // read again below: keep it in L2
-                const uint32_t h[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int x = c * 8 + k;
-                    const int v = (int)((h[k / 2] >> (16 * (k % 2))) & 0xFFFFu);
-                    if (v == kNoRoot || (v & kIdMask) != r * kVX + x) continue;
-                    const int g = (int)vpos(a, gx0 + x, gy, gz);
-                    if (!(v & kBorderBit)) {
-                        fin[v & kIdMask] = (uint32_t)(g + 1);
-                        continue;
-                    }
-                    const int i = atomicAdd(&nwalk, 1);
-                    if (i < kWalks) walk[i] = (uint16_t)(v & kIdMask);
-                    else fin[v & kIdMask] = (uint32_t)(vg_find_ro(a.labels, a.n, g, a.global_cap, err) + 1);
-                }
-            }
-        }
+    uint32_t o, tot;
+    int r0;
+    const uint32_t est = element_starts<k26>(mask, t, o, r0);
+    eoff[t] = (uint16_t)cta_exclusive_scan((uint32_t)__popc(est), wtot, tot);
+    const int ns = (int)a.ns[b];
+    int err = 0;
+    for (int k = t; k < ns; k += kVThreads) {
+        uint32_t key;
+        find_global_ro(a.P, (uint32_t)(b * kVSlots) + (uint32_t)k, key, a.global_cap, err, a.bound);
+        fin[k] = (int)key + 1;
     }
     __syncthreads();
-    {
-        const int n = nwalk < kWalks ? nwalk : kWalks;
-        for (int i = threadIdx.x; i < n; i += kVThreads) {
-            const int id = walk[i];
-            const int g = id_pos(a, bx, by, bz, id);
-            fin[id] = (uint32_t)(vg_find_ro(a.labels, a.n, g, a.global_cap, err) + 1);
+    const uint16_t *V = a.vals + b * kVMaxElems;
+    for (int e = t; e < (int)tot; e += kVThreads) {
+        const int v = V[e];
+        if (v & kSlotFlag) {
+            lab[e] = (v & ~kSlotFlag) < ns ? fin[v & ~kSlotFlag] : 0;
+        } else {
+            const int row = v / kVX;
+            lab[e] = (int)vpos(a, gx0 + v % kVX, gy0 + row % kVY, gz0 + row / kVY) + 1;
         }
     }
     __syncthreads();
 
     // whole rows, one warp per row, lane = x
-    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    const int lane = t % 32, warp = t / 32;
     const int gx = gx0 + lane;
     for (int row = warp; row < kVRows; row += kVThreads / 32) {
         const int gy = gy0 + row % kVY, gz = gz0 + row / kVY;
-        if (gy >= a.H || gz >= a.D) continue;
-        if (gx >= a.W) continue;
-        const int v = rec[row * kVX + lane];
-        __stcs(a.labels + vpos(a, gx, gy, gz), v == kNoRoot ? 0 : (int32_t)fin[v & kIdMask]);
+        if (gy >= a.H || gz >= a.D || gx >= a.W) continue;
+        const int v = ((mask[row] >> lane) & 1u) ? lab[element_at<k26>(mask, eoff, row, lane)] : 0;
+        __stcs(a.labels + vpos(a, gx, gy, gz), (int32_t)v);
     }
     if (err) atomicOr(&g_volume_error, err);
 }
@@ -673,11 +715,33 @@ void volume_grid(int D, int H, int W, int &nbx, int &nby, int &nbz) {
 
 }  // namespace
 
+namespace {
+
+// Workspace layout, array after array, each 256-byte aligned: row masks,
+// element values, face records, global union-find entries, slot counts.
+struct VolLayout {
+    size_t mask, vals, face, P, ns, bytes;
+};
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+VolLayout volume_layout(size_t blocks) {
+    VolLayout l;
+    l.mask = 0;
+    l.vals = align256(l.mask + blocks * kVRows * sizeof(uint32_t));
+    l.face = align256(l.vals + blocks * kVMaxElems * sizeof(uint16_t));
+    l.P = align256(l.face + blocks * kVFaceVoxels * sizeof(uint16_t));
+    l.ns = align256(l.P + blocks * kVSlots * sizeof(uint64_t));
+    l.bytes = align256(l.ns + blocks * sizeof(uint32_t));
+    return l;
+}
+
+}  // namespace
+
 size_t volume_workspace_bytes(int D, int H, int W) {
     int nbx, nby, nbz;
     volume_grid(D, H, W, nbx, nby, nbz);
-    const size_t bytes = (size_t)nbx * nby * nbz * (kVIds + 2 * kVRows) * sizeof(uint16_t);
-    return (bytes + 255) & ~(size_t)255;
+    return volume_layout((size_t)nbx * nby * nbz).bytes;
 }
 
 int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int conn, int32_t *labels, void *ws,
@@ -685,29 +749,37 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     VolArgs a;
     a.img = img;
     a.labels = labels;
-    a.roots = static_cast<uint16_t *>(ws);
     a.pitch = pitch;
     a.D = D;
     a.H = H;
     a.W = W;
     a.n = (int)((long long)D * H * W);
     volume_grid(D, H, W, a.nbx, a.nby, a.nbz);
-    a.xface = a.roots + (size_t)a.nbx * a.nby * a.nbz * kVIds;
+    const size_t nblocks = (size_t)a.nbx * a.nby * a.nbz;
+    if (nblocks * kVSlots >= 0xFFFFFFFFull) return -1;  // slot numbers are 32-bit
+    const VolLayout l = volume_layout(nblocks);
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    a.mask = reinterpret_cast<uint32_t *>(w + l.mask);
+    a.vals = reinterpret_cast<uint16_t *>(w + l.vals);
+    a.face = reinterpret_cast<uint16_t *>(w + l.face);
+    a.P = reinterpret_cast<uint64_t *>(w + l.P);
+    a.ns = reinterpret_cast<uint32_t *>(w + l.ns);
+    a.bound = (uint32_t)(nblocks * kVSlots);
     a.vec_in = (pitch % 16 == 0) && (reinterpret_cast<uintptr_t>(img) % 16 == 0);
     // a find walks a strictly decreasing chain and a union retry strictly
     // lowers its node, so neither can take more steps than there are nodes
     const long long n = (long long)D * H * W;
     a.local_cap = cap > 0 ? cap : kVIds + 16;
     a.global_cap = cap > 0 ? cap : (int)(n + 16 < (1LL << 30) ? n + 16 : (1LL << 30));
-    const unsigned blocks = (unsigned)((long long)a.nbx * a.nby * a.nbz);
+    const unsigned blocks = (unsigned)nblocks;
     if (conn == 26) {
         k_vol_local<true><<<blocks, kVThreads, 0, stream>>>(a);
         k_vol_merge<true><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<true><<<blocks, kVThreads, 0, stream>>>(a);
     } else {
         k_vol_local<false><<<blocks, kVThreads, 0, stream>>>(a);
         k_vol_merge<false><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<<<blocks, kVThreads, 0, stream>>>(a);
+        k_vol_write<false><<<blocks, kVThreads, 0, stream>>>(a);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
