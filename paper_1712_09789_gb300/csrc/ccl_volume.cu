@@ -88,14 +88,20 @@ struct VolArgs {
     int n;  // voxels, D * H * W
     int nbx, nby, nbz;
     int vec_in;
+    int vec_out;  // labels rows start 16-byte aligned (W % 4 == 0, aligned base)
     int local_cap, global_cap;
     uint32_t bound;  // slots in all: blocks * kVSlots
 };
 
+constexpr int kCand = 2048;  // refinement pairs listed per pass (more are joined at once)
+
 struct VolSmem {
     uint32_t mask[kVRows];    // row masks (bit x = voxel x of the row)
     uint32_t border[kVRows];  // bit x of row r: id r*32+x is the root of a component on a block face
-    uint32_t par[kVIds];      // union-find entries, by slot(id); used at run starts only
+    uint32_t par[kVIds];      // union-find entries, by slot(id); used at element ids only
+    uint32_t cand[kCand];     // refinement pairs (a << 16 | b)
+    uint32_t wtot[kVThreads / 32];
+    unsigned ncand;
 };
 
 // Storage slot of an id: rows keep their 32 entries, rotated by the row so
@@ -182,64 +188,65 @@ __device__ __forceinline__ uint32_t cta_exclusive_scan(uint32_t v, uint32_t *wto
     return base + s - v;
 }
 
-// Contacts of the runs of row r (mask m, run starts st) with the runs of the
-// earlier row n (x widened by one voxel under 26-connectivity), visited per
-// run in increasing x.  Coarse labelling: the first contact of a run (over
-// the neighbour rows in a fixed order) became its parent before any union,
-// so it is skipped here (bit s of `first` marks run s as past it); every
-// later contact is joined by a union.
-template <bool k26>
-__device__ __forceinline__ void link_rows(VolSmem &sm, int r, uint32_t m, uint32_t st, int n, uint32_t &first,
-                                          int cap, int &err) {
-    const uint32_t mn = sm.mask[n];
-    if (!(m & touch_range<k26>(mn))) return;
-    const uint32_t sn = mn & ~(mn << 1);
-    for (uint32_t t = st; t; t &= t - 1) {
-        const int s = lobit(t);
-        uint32_t c = mn & touch_range<k26>(run_bits(s, run_end(m, s)));
-        while (c) {
-            const int b = lobit(c);
-            if (first & (1u << s)) v_union(sm.par, r * kVX + s, n * kVX + hibit(sn & upto(b)), cap, err);
-            first |= 1u << s;
-            const int ne = run_end(mn, b);
-            c = ne == 31 ? 0u : c & (~0u << (ne + 1));
+// Two steps up from x: x itself for a root, else its parent's parent (its
+// parent when that is a root).  Equal results mean one set.
+__device__ __forceinline__ int v_root2(const volatile uint32_t *par, int x) {
+    return (int)par[slot((int)par[slot(x)])];
+}
+
+// Joins the sets of a and b, by all 32 lanes of a warp together (lanes with
+// valid == false keep step), with the links of v_union.
+__device__ __forceinline__ void v_union_sync(uint32_t *par, bool valid, int a, int b, int cap, int &err) {
+    volatile uint32_t *vp = par;
+    bool pend = valid;
+    for (int i = 0; __any_sync(0xFFFFFFFFu, pend); ++i) {
+        if (pend) {
+            a = v_find(vp, a, cap, err);
+            b = v_find(vp, b, cap, err);
+            if (a == b || err) {
+                pend = false;
+            } else {
+                if (a < b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                const int old = (int)atomicMin(par + slot(a), (uint32_t)b);
+                if (old == a) pend = false;
+                else a = old;  // a gained a parent meanwhile: join that one instead
+            }
+        }
+        if (i >= cap) {
+            if (pend) err |= kErrLocalCap;
+            break;
         }
     }
 }
 
-// The earlier rows a run can touch, in the order they are visited: the row
-// above, the row in the slice before, and under 26-connectivity the two
-// diagonal rows of the slice before.  Bit k of the returned mask says that
-// neighbour k exists inside the block.
-__device__ __forceinline__ constexpr int nb_off(int k) {
-    return k == 0 ? -1 : k == 1 ? -kVY : k == 2 ? -kVY - 1 : -kVY + 1;
-}
-template <bool k26>
-__device__ __forceinline__ uint32_t earlier_rows(int y, int z) {
-    uint32_t v = 0;
-    if (y > 0) v |= 1u;
-    if (z > 0) {
-        v |= 2u;
-        if (k26 && y > 0) v |= 4u;
-        if (k26 && y < kVY - 1) v |= 8u;
-    }
-    return v;
+// A refinement pair (two element ids): listed for join_candidates, or
+// joined at once when the list is full.
+__device__ __forceinline__ void emit_pair(VolSmem &sm, int a, int b, int cap, int &err) {
+    const unsigned i = atomicAdd(&sm.ncand, 1u);
+    if (i < (unsigned)kCand) sm.cand[i] = ((uint32_t)a << 16) | (uint32_t)b;
+    else v_union(sm.par, a, b, cap, err);
 }
 
-// First contact of run s of row r among the earlier rows, in the order
-// link_rows visits them; -1 when the run touches none.
-template <bool k26>
-__device__ __forceinline__ int first_contact(const VolSmem &sm, int r, uint32_t m, int s, uint32_t nbv) {
-    const uint32_t w = touch_range<k26>(run_bits(s, run_end(m, s)));
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (!(nbv & (1u << k))) continue;
-        const int n = r + nb_off(k);
-        const uint32_t mn = sm.mask[n];
-        const uint32_t c = mn & w;
-        if (c) return n * kVX + hibit(mn & ~(mn << 1) & upto(lobit(c)));
+// After the barrier that follows the last emit_pair: every lane takes one
+// listed pair per step and joins it where the two-step roots differ.
+__device__ __forceinline__ void join_candidates(VolSmem &sm, int cap, int &err) {
+    const unsigned nc = sm.ncand < (unsigned)kCand ? sm.ncand : (unsigned)kCand;
+    for (unsigned j0 = 0; j0 < nc; j0 += kVThreads) {
+        const unsigned j = j0 + threadIdx.x;
+        int a = 0, b = 0;
+        bool need = false;
+        if (j < nc) {
+            const uint32_t e = sm.cand[j];
+            a = (int)(e >> 16);
+            b = (int)(e & 0xFFFFu);
+            need = v_root2(sm.par, a) != v_root2(sm.par, b);
+        }
+        v_union_sync(sm.par, need, a, b, cap, err);
     }
-    return -1;
 }
 
 // Row (y, z) of the volume over the block's 32 columns from gx0, as a bit
@@ -351,23 +358,39 @@ __device__ void bundle_labelling(VolSmem &sm, const VolArgs &a, int &err) {
         sm.par[slot(key)] = (uint32_t)parent;
     }
     __syncthreads();
-    for (uint32_t q = starts; q; q &= q - 1) {
-        const int s = lobit(q), e = run_end(o, s);
-        const int key = piece_key(b, s, e);
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (!(nbv & (1u << k))) continue;
-            const Bundle n = load_bundle(sm, r0 + bundle_nb_off(k));
-            const uint32_t no = bundle_or(n);
-            uint32_t c = touch_range<true>(bundle_own_face(b, k) & run_bits(s, e)) & bundle_nb_face(n, k);
-            while (c) {
-                const int bit = lobit(c);
-                v_union(sm.par, key, piece_key_at(n, bit), a.local_cap, err);
-                const int ne = run_end(no, bit);
-                c = ne == 31 ? 0u : c & (~0u << (ne + 1));
+    // refinement: thread t takes bundle t % 64 against its earlier bundle
+    // t / 64; every contact of one of its pieces with a piece there is a
+    // pair to join (the contact that made a parent link is dropped by the
+    // root filter of join_candidates)
+    static_assert(kBY * kBZ * 4 == kVThreads, "one thread per bundle and earlier bundle");
+    {
+        const int bt = t % (kBY * kBZ), k = t / (kBY * kBZ);
+        const int Yb = bt % kBY, Zb = bt / kBY;
+        const bool on = k == 0 ? Yb > 0 : k == 1 ? Zb > 0 : k == 2 ? (Yb > 0 && Zb > 0) : (Yb < kBY - 1 && Zb > 0);
+        if (on) {
+            const int rb = 2 * Zb * kVY + 2 * Yb;
+            const Bundle bb = load_bundle(sm, rb);
+            const Bundle n = load_bundle(sm, rb + bundle_nb_off(k));
+            const uint32_t ob = bundle_or(bb), no = bundle_or(n);
+            const uint32_t fo = bundle_own_face(bb, k), fn = bundle_nb_face(n, k);
+            if (touch_range<true>(fo) & fn) {
+                for (uint32_t q = ob & ~(ob << 1); q; q &= q - 1) {
+                    const int s = lobit(q), e = run_end(ob, s);
+                    uint32_t c = touch_range<true>(fo & run_bits(s, e)) & fn;
+                    if (!c) continue;
+                    const int key = piece_key(bb, s, e);
+                    while (c) {
+                        const int bit = lobit(c);
+                        emit_pair(sm, key, piece_key_at(n, bit), a.local_cap, err);
+                        const int ne = run_end(no, bit);
+                        c = ne == 31 ? 0u : c & (~0u << (ne + 1));
+                    }
+                }
             }
         }
     }
+    __syncthreads();
+    join_candidates(sm, a.local_cap, err);
     __syncthreads();
     for (uint32_t q = starts; q; q &= q - 1) {
         const int s = lobit(q);
@@ -408,30 +431,51 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
     }
     sm.mask[r] = m;
     sm.border[r] = 0;
+    if (r == 0) sm.ncand = 0;
     __syncthreads();
 
     if (k26) {
         bundle_labelling(sm, a, err);
     } else {
         const uint32_t st = m & ~(m << 1);
-        const uint32_t nbv = earlier_rows<k26>(y, z);
-        // coarse labelling: each run takes its first contact (a run of an
-        // earlier row, hence a smaller id) as parent, or itself; only the
-        // own entries are written, so no atomics are needed
+        // contact events with the row above (u) and the row of the slice
+        // before (v): a run of m & m_u lies inside one (run, run) pair, so
+        // its first column is one event per pair
+        const uint32_t mu = y > 0 ? sm.mask[r - 1] : 0u, mv = z > 0 ? sm.mask[r - kVY] : 0u;
+        const uint32_t cu = m & mu, cv = m & mv;
+        const uint32_t eu = cu & ~(cu << 1), ev = cv & ~(cv << 1);
+        // coarse labelling: the lowest event of each run (the one with the
+        // row above where both rows have one in that column) makes the run it
+        // meets, of an earlier row and so of a smaller id, the run's parent;
+        // a run without events is a root.  Only the own entries are written.
+        const uint32_t e = eu | ev;
+        const uint32_t fe = ((m + e) ^ m) & e;  // lowest event of every run
         for (uint32_t t = st; t; t &= t - 1) {
             const int s = lobit(t), id = r * kVX + s;
-            const int f = first_contact<k26>(sm, r, m, s, nbv);
-            sm.par[slot(id)] = (uint32_t)(f >= 0 ? f : id);
+            const uint32_t f = fe & run_bits(s, run_end(m, s));
+            int parent = id;
+            if (f) {
+                const int c = lobit(f);
+                const bool up = (eu >> c) & 1u;
+                const uint32_t mn = up ? mu : mv;
+                parent = (r - (up ? 1 : kVY)) * kVX + hibit(mn & ~(mn << 1) & upto(c));
+            }
+            sm.par[slot(id)] = (uint32_t)parent;
         }
         __syncthreads();
 
-        // refinement: the remaining contacts by union
-        if (m) {
-            uint32_t first = 0;
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (nbv & (1u << k)) link_rows<k26>(sm, r, m, st, r + nb_off(k), first, a.local_cap, err);
+        // refinement: every other event joins its two runs
+        const uint32_t su = mu & ~(mu << 1), sv = mv & ~(mv << 1);
+        for (uint32_t t = eu & ~fe; t; t &= t - 1) {
+            const int c = lobit(t);
+            emit_pair(sm, r * kVX + hibit(st & upto(c)), (r - 1) * kVX + hibit(su & upto(c)), a.local_cap, err);
         }
+        for (uint32_t t = ev & ~(fe & ~eu); t; t &= t - 1) {
+            const int c = lobit(t);
+            emit_pair(sm, r * kVX + hibit(st & upto(c)), (r - kVY) * kVX + hibit(sv & upto(c)), a.local_cap, err);
+        }
+        __syncthreads();
+        join_candidates(sm, a.local_cap, err);
         __syncthreads();
 
         for (uint32_t t = st; t; t &= t - 1) {
@@ -478,25 +522,10 @@ __device__ __forceinline__ uint32_t element_starts(const uint32_t *mask, int t, 
     return o & ~(o << 1);
 }
 
-// Index of the element that holds voxel x of row r (x must be foreground),
-// from the row masks and the per-thread element offsets eoff.
-template <bool k26>
-__device__ __forceinline__ int element_at(const uint32_t *mask, const uint16_t *eoff, int r, int x) {
-    if (k26) {
-        const int r0 = (r / kVY & ~1) * kVY + (r % kVY & ~1);
-        const uint32_t o = mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1];
-        const int t = (r / kVY / 2) * (kVY / 2) + (r % kVY) / 2;
-        return (int)eoff[t] + __popc(o & ~(o << 1) & upto(x)) - 1;
-    }
-    const uint32_t m = mask[r];
-    return (int)eoff[r] + __popc(m & ~(m << 1) & upto(x)) - 1;
-}
-
 template <bool k26>
 __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     __shared__ VolSmem sm;
     __shared__ uint16_t sbase[kVRows];  // border slot of the first marked root of each row
-    __shared__ uint32_t wtot[kVThreads / 32];
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     int err = 0;
@@ -512,7 +541,7 @@ __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     const uint32_t est = element_starts<k26>(sm.mask, r, o, r0);
     const uint32_t bd = sm.border[r];
     uint32_t tot;
-    const uint32_t pre = cta_exclusive_scan((uint32_t)__popc(est) | ((uint32_t)__popc(bd) << 16), wtot, tot);
+    const uint32_t pre = cta_exclusive_scan((uint32_t)__popc(est) | ((uint32_t)__popc(bd) << 16), sm.wtot, tot);
     sbase[r] = (uint16_t)(pre >> 16);
     if (r == 0) a.ns[b] = tot >> 16;
     a.mask[b * kVRows + r] = m;
@@ -695,14 +724,44 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
     }
     __syncthreads();
 
-    // whole rows, one warp per row, lane = x
+    // whole rows: a lane takes 4 voxels (one 16-byte store), a warp 4 rows
+    // per step
     const int lane = t % 32, warp = t / 32;
-    const int gx = gx0 + lane;
-    for (int row = warp; row < kVRows; row += kVThreads / 32) {
+    const int c0 = 4 * (lane & 7);
+    const int gx = gx0 + c0;
+    for (int row = 4 * warp + (lane >> 3); row < kVRows; row += 4 * (kVThreads / 32)) {
         const int gy = gy0 + row % kVY, gz = gz0 + row / kVY;
         if (gy >= a.H || gz >= a.D || gx >= a.W) continue;
-        const int v = ((mask[row] >> lane) & 1u) ? lab[element_at<k26>(mask, eoff, row, lane)] : 0;
-        __stcs(a.labels + vpos(a, gx, gy, gz), (int32_t)v);
+        const uint32_t m = mask[row];
+        int v[4] = {0, 0, 0, 0};
+        if ((m >> c0) & 15u) {
+            uint32_t st;
+            int e;
+            if (k26) {
+                const int r0 = (row / kVY & ~1) * kVY + (row % kVY & ~1);
+                const uint32_t o = mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1];
+                st = o & ~(o << 1);
+                e = (int)eoff[(row / kVY / 2) * (kVY / 2) + (row % kVY) / 2];
+            } else {
+                st = m & ~(m << 1);
+                e = (int)eoff[row];
+            }
+            e += __popc(st & ((1u << c0) - 1u)) - 1;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                e += (int)((st >> (c0 + j)) & 1u);
+                if ((m >> (c0 + j)) & 1u) v[j] = lab[e];
+            }
+        }
+        int32_t *dst = a.labels + vpos(a, gx, gy, gz);
+        if (a.vec_out && gx + 4 <= a.W) {
+            __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
+        } else {
+            const int n = a.W - gx < 4 ? a.W - gx : 4;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (j < n) __stcs(dst + j, v[j]);
+        }
     }
     if (err) atomicOr(&g_volume_error, err);
 }
@@ -766,6 +825,7 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     a.ns = reinterpret_cast<uint32_t *>(w + l.ns);
     a.bound = (uint32_t)(nblocks * kVSlots);
     a.vec_in = (pitch % 16 == 0) && (reinterpret_cast<uintptr_t>(img) % 16 == 0);
+    a.vec_out = (W % 4 == 0) && (reinterpret_cast<uintptr_t>(labels) % 16 == 0);
     // a find walks a strictly decreasing chain and a union retry strictly
     // lowers its node, so neither can take more steps than there are nodes
     const long long n = (long long)D * H * W;
