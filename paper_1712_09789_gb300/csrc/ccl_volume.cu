@@ -323,79 +323,82 @@ __device__ __forceinline__ int voxel_root(const VolSmem &sm, int r, int x) {
     return (int)sm.par[slot(r * kVX + hibit(mr & ~(mr << 1) & upto(x)))];
 }
 
-// Step 1 for 26-connectivity on the block's 64 bundles (threads 0..63):
-// coarse labelling (each piece takes its first contact in an earlier bundle
-// as parent when that piece has the smaller name), refinement (every contact
-// joined by union) and compression.  Ends with a barrier.
+// Step 1 for 26-connectivity on the block's 64 bundles.  Thread t works on
+// bundle t % 64: in the contact pass against the earlier bundle k = t / 64,
+// in the per-piece passes on every fourth piece of the bundle from k on.
+// Column connection: each contact of a piece with a piece of a smaller name
+// lowers the piece's entry to that name (atomicMin: the entry ends at the
+// smallest such neighbour, so the links go to smaller names and form a
+// forest).  Refinement: every contact is also listed as a pair (those that
+// made a link are dropped by the root filter of join_candidates).
+// Compression follows.  Ends with a barrier.
 __device__ void bundle_labelling(VolSmem &sm, const VolArgs &a, int &err) {
     constexpr int kBY = kVY / 2, kBZ = kVZ / 2;
+    static_assert(kBY * kBZ * 4 == kVThreads, "one thread per bundle and earlier bundle");
     const int t = threadIdx.x;
-    const bool mine = t < kBY * kBZ;
-    const int Y = t % kBY, Z = t / kBY;
-    const int r0 = 2 * Z * kVY + 2 * Y;
-    Bundle b = {0u, 0u, 0u, 0u, 0};
-    uint32_t o = 0, starts = 0, nbv = 0;
-    if (mine) {
-        b = load_bundle(sm, r0);
-        o = bundle_or(b);
-        starts = o & ~(o << 1);
-        nbv = (Y > 0 ? 1u : 0u) | (Z > 0 ? 2u : 0u) | (Y > 0 && Z > 0 ? 4u : 0u) | (Y < kBY - 1 && Z > 0 ? 8u : 0u);
-    }
-    for (uint32_t q = starts; q; q &= q - 1) {
-        const int s = lobit(q), e = run_end(o, s);
-        const int key = piece_key(b, s, e);
-        int parent = key;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (parent != key || !(nbv & (1u << k))) continue;
-            const Bundle n = load_bundle(sm, r0 + bundle_nb_off(k));
-            const uint32_t c = touch_range<true>(bundle_own_face(b, k) & run_bits(s, e)) & bundle_nb_face(n, k);
-            if (c) {
-                const int nk = piece_key_at(n, lobit(c));
-                if (nk < key) parent = nk;
-            }
+    const int bt = t % (kBY * kBZ), k = t / (kBY * kBZ);
+    const int Yb = bt % kBY, Zb = bt / kBY;
+    const int rb = 2 * Zb * kVY + 2 * Yb;
+    const Bundle bb = load_bundle(sm, rb);
+    const uint32_t ob = bundle_or(bb), starts = ob & ~(ob << 1);
+    {
+        int j = 0;
+        for (uint32_t q = starts; q; q &= q - 1, ++j) {
+            if ((j & 3) != k) continue;
+            const int s = lobit(q);
+            const int key = piece_key(bb, s, run_end(ob, s));
+            sm.par[slot(key)] = (uint32_t)key;
         }
-        sm.par[slot(key)] = (uint32_t)parent;
     }
     __syncthreads();
-    // refinement: thread t takes bundle t % 64 against its earlier bundle
-    // t / 64; every contact of one of its pieces with a piece there is a
-    // pair to join (the contact that made a parent link is dropped by the
-    // root filter of join_candidates)
-    static_assert(kBY * kBZ * 4 == kVThreads, "one thread per bundle and earlier bundle");
-    {
-        const int bt = t % (kBY * kBZ), k = t / (kBY * kBZ);
-        const int Yb = bt % kBY, Zb = bt / kBY;
-        const bool on = k == 0 ? Yb > 0 : k == 1 ? Zb > 0 : k == 2 ? (Yb > 0 && Zb > 0) : (Yb < kBY - 1 && Zb > 0);
-        if (on) {
-            const int rb = 2 * Zb * kVY + 2 * Yb;
-            const Bundle bb = load_bundle(sm, rb);
-            const Bundle n = load_bundle(sm, rb + bundle_nb_off(k));
-            const uint32_t ob = bundle_or(bb), no = bundle_or(n);
-            const uint32_t fo = bundle_own_face(bb, k), fn = bundle_nb_face(n, k);
-            if (touch_range<true>(fo) & fn) {
-                for (uint32_t q = ob & ~(ob << 1); q; q &= q - 1) {
-                    const int s = lobit(q), e = run_end(ob, s);
-                    uint32_t c = touch_range<true>(fo & run_bits(s, e)) & fn;
-                    if (!c) continue;
-                    const int key = piece_key(bb, s, e);
-                    while (c) {
-                        const int bit = lobit(c);
-                        emit_pair(sm, key, piece_key_at(n, bit), a.local_cap, err);
-                        const int ne = run_end(no, bit);
-                        c = ne == 31 ? 0u : c & (~0u << (ne + 1));
-                    }
-                }
+    const bool on = k == 0 ? Yb > 0 : k == 1 ? Zb > 0 : k == 2 ? (Yb > 0 && Zb > 0) : (Yb < kBY - 1 && Zb > 0);
+    Bundle n = {0u, 0u, 0u, 0u, 0};
+    uint32_t no = 0, fo = 0, fn = 0;
+    if (on) {
+        n = load_bundle(sm, rb + bundle_nb_off(k));
+        no = bundle_or(n);
+        fo = bundle_own_face(bb, k);
+        fn = bundle_nb_face(n, k);
+        if (!(touch_range<true>(fo) & fn)) fo = 0;
+    }
+    // the contacts of the own pieces with the pieces of bundle n: one per
+    // (piece, piece) pair
+    const auto contacts = [&](auto &&visit) {
+        if (!fo) return;
+        for (uint32_t q = starts; q; q &= q - 1) {
+            const int s = lobit(q), e = run_end(ob, s);
+            uint32_t c = touch_range<true>(fo & run_bits(s, e)) & fn;
+            if (!c) continue;
+            const int key = piece_key(bb, s, e);
+            while (c) {
+                const int bit = lobit(c);
+                visit(key, piece_key_at(n, bit));
+                const int ne = run_end(no, bit);
+                c = ne == 31 ? 0u : c & (~0u << (ne + 1));
             }
         }
-    }
+    };
+    contacts([&](int key, int nk) {
+        if (nk < key) atomicMin(&sm.par[slot(key)], (uint32_t)nk);
+        const unsigned i = atomicAdd(&sm.ncand, 1u);
+        if (i < (unsigned)kCand) sm.cand[i] = ((uint32_t)key << 16) | (uint32_t)nk;
+    });
     __syncthreads();
     join_candidates(sm, a.local_cap, err);
+    if (sm.ncand > (unsigned)kCand) {
+        // the list overflowed: every contact is joined once more, one by one
+        __syncthreads();
+        contacts([&](int key, int nk) { v_union(sm.par, key, nk, a.local_cap, err); });
+    }
     __syncthreads();
-    for (uint32_t q = starts; q; q &= q - 1) {
-        const int s = lobit(q);
-        const int key = piece_key(b, s, run_end(o, s));
-        sm.par[slot(key)] = (uint32_t)v_find_ro(sm.par, key, a.local_cap, err);
+    {
+        int j = 0;
+        for (uint32_t q = starts; q; q &= q - 1, ++j) {
+            if ((j & 3) != k) continue;
+            const int s = lobit(q);
+            const int key = piece_key(bb, s, run_end(ob, s));
+            sm.par[slot(key)] = (uint32_t)v_find_ro(sm.par, key, a.local_cap, err);
+        }
     }
     __syncthreads();
 }
@@ -525,7 +528,8 @@ __device__ __forceinline__ uint32_t element_starts(const uint32_t *mask, int t, 
 template <bool k26>
 __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     __shared__ VolSmem sm;
-    __shared__ uint16_t sbase[kVRows];  // border slot of the first marked root of each row
+    __shared__ uint16_t sbase[kVRows];      // border slot of the first marked root of each row
+    __shared__ uint16_t eoff[kVThreads];    // first element of each thread's row (bundle)
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     int err = 0;
@@ -543,12 +547,15 @@ __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     uint32_t tot;
     const uint32_t pre = cta_exclusive_scan((uint32_t)__popc(est) | ((uint32_t)__popc(bd) << 16), sm.wtot, tot);
     sbase[r] = (uint16_t)(pre >> 16);
+    eoff[r] = (uint16_t)(pre & 0xFFFFu);
     if (r == 0) a.ns[b] = tot >> 16;
     a.mask[b * kVRows + r] = m;
     __syncthreads();
-    const auto marked = [&](int root) { return ((sm.border[root >> 5] >> (root & 31)) & 1u) != 0u; };
-    const auto border_slot = [&](int root) {
-        return (int)sbase[root >> 5] + __popc(sm.border[root >> 5] & ((1u << (root & 31)) - 1u));
+    const auto value_of = [&](int root) -> uint16_t {
+        const int rr = root >> 5;
+        const uint32_t bw = sm.border[rr];
+        if (!((bw >> (root & 31)) & 1u)) return (uint16_t)root;
+        return (uint16_t)(kSlotFlag | (sbase[rr] + __popc(bw & ((1u << (root & 31)) - 1u))));
     };
 
     // global union-find entries of the own row's border roots, keyed by the
@@ -561,24 +568,52 @@ __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
             a.P[s0 + k] = pack_slot(key, s0 + k);
         }
     }
-    // element values
-    {
-        uint16_t *V = a.vals + b * kVMaxElems + (pre & 0xFFFFu);
-        const Bundle bu = (k26 && est) ? load_bundle(sm, r0) : Bundle{0u, 0u, 0u, 0u, 0};
-        for (uint32_t t = est; t; t &= t - 1, ++V) {
+    // element values, staged in shared memory (the candidate list is free
+    // now): the runs of the own row, or every fourth piece of bundle t % 64
+    static_assert(sizeof(sm.cand) == kVMaxElems * sizeof(uint16_t), "the value stage fills the candidate list");
+    uint16_t *const stage = reinterpret_cast<uint16_t *>(sm.cand);
+    if (k26) {
+        constexpr int kB = (kVY / 2) * (kVZ / 2);
+        const int bt = r % kB, k = r / kB;
+        const int rb = 2 * (bt / (kVY / 2)) * kVY + 2 * (bt % (kVY / 2));
+        const Bundle bu = load_bundle(sm, rb);
+        const uint32_t ob = bundle_or(bu);
+        int j = 0;
+        for (uint32_t t = ob & ~(ob << 1); t; t &= t - 1, ++j) {
+            if ((j & 3) != k) continue;
             const int s = lobit(t);
-            const int key = k26 ? piece_key(bu, s, run_end(o, s)) : r * kVX + s;
-            const int root = (int)sm.par[slot(key)];
-            *V = marked(root) ? (uint16_t)(kSlotFlag | border_slot(root)) : (uint16_t)root;
+            stage[eoff[bt] + j] = value_of((int)sm.par[slot(piece_key(bu, s, run_end(ob, s)))]);
         }
+    } else {
+        int e = eoff[r];
+        for (uint32_t t = est; t; t &= t - 1, ++e) stage[e] = value_of((int)sm.par[slot(r * kVX + lobit(t))]);
     }
-    // face records: the slices z = 0 and 15 and the rows y = 0 and 15 one
-    // warp per row (lane = x), the voxels x = 0 and 31 of the own row
+    __syncthreads();
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(stage);
+        uint4 *dst = reinterpret_cast<uint4 *>(a.vals + b * kVMaxElems);
+        for (int i = r; i < (int)((tot & 0xFFFFu) + 7) / 8; i += kVThreads) dst[i] = src[i];
+    }
+    // face records from the staged values: the slices z = 0 and 15 and the
+    // rows y = 0 and 15 one warp per row (lane = x), the voxels x = 0 and 31
+    // of the own row
     uint16_t *F = a.face + b * kVFaceVoxels;
     const auto face_slot = [&](int row, int x) -> uint16_t {
         if (!((sm.mask[row] >> x) & 1u)) return kNoSlot;
-        const int root = voxel_root<k26>(sm, row, x);
-        return marked(root) ? (uint16_t)border_slot(root) : kNoSlot;
+        uint32_t st;
+        int e0;
+        if (k26) {
+            const int rb = (row / kVY & ~1) * kVY + (row % kVY & ~1);
+            const uint32_t ob = sm.mask[rb] | sm.mask[rb + 1] | sm.mask[rb + kVY] | sm.mask[rb + kVY + 1];
+            st = ob & ~(ob << 1);
+            e0 = eoff[(row / kVY / 2) * (kVY / 2) + (row % kVY) / 2];
+        } else {
+            const uint32_t mr = sm.mask[row];
+            st = mr & ~(mr << 1);
+            e0 = eoff[row];
+        }
+        const uint16_t v = stage[e0 + __popc(st & upto(x)) - 1];
+        return (v & kSlotFlag) ? (uint16_t)(v & ~kSlotFlag) : kNoSlot;
     };
     {
         const int lane = r & 31, warp = r >> 5;
