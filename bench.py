@@ -85,12 +85,12 @@ def load_peaks():
 KERNEL_SOURCES = ("ccl_block.cuh", "ccl_internal.h", "ccl_kernels.cu", "ccl_pieces.cuh")
 
 
-def csrc_digest():
-    """Digest of the labelling kernels' sources; a recorded ncu figure is
-    used only while it matches."""
+def csrc_digest(sources=KERNEL_SOURCES):
+    """Digest of the kernels' sources; a recorded ncu figure is used only
+    while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1712_09789_gb300", "csrc")
-    for name in KERNEL_SOURCES:
+    for name in sources:
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
@@ -108,6 +108,19 @@ def recorded_traffic(kernel: str):
     if not m_sha or not m_b or m_sha.group(1) != csrc_digest():
         return None
     return float(m_b.group(1))
+
+
+def recorded_figures(profile: str, sources):
+    """The `name: number` lines of a committed ncu summary under profiles/,
+    or None when it is missing or its csrc_digest does not match `sources`."""
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"^csrc_digest:\s*([0-9a-f]+)", text, re.M)
+    if not m_sha or m_sha.group(1) != csrc_digest(sources):
+        return None
+    return {k: float(v) for k, v in re.findall(r"^(dram_bytes_per_[a-z0-9_.]+):\s*([0-9.eE+]+)\s*$", text, re.M)}
 
 
 class ClockSampler:
@@ -698,6 +711,9 @@ def bench_stats(torch, ccl):
     lib = ccl.load()
     img = torch.from_numpy(synth.bernoulli(8192, 8192, 0.5, 0)).cuda()
     res = {"workload": "8192x8192 Bernoulli p=0.5 seed 0 labels"}
+    # DRAM bytes per pixel of a call (ncu) from
+    # profiles/k_stats_8192_bernoulli.md while the sources match
+    rec = recorded_figures("k_stats_8192_bernoulli.md", ("ccl_block.cuh", "ccl_internal.h", "ccl_stats.cu")) or {}
     for conn in (8, 4):
         lab = ccl.ccl_label(img, conn)
         n = ctypes.c_int(0)
@@ -715,7 +731,8 @@ def bench_stats(torch, ccl):
             if i >= 2:
                 ts.append((t1 - t0) * 1e3)
         ms = sorted(ts)[2]
-        res[f"conn{conn}"] = {"components": n.value, "ms": ms, "gpixel_s": 8192 * 8192 / (ms / 1e3) / 1e9}
+        res[f"conn{conn}"] = {"components": n.value, "ms": ms, "gpixel_s": 8192 * 8192 / (ms / 1e3) / 1e9,
+                              "ncu_dram_bytes_per_pixel": rec.get(f"dram_bytes_per_pixel_conn{conn}")}
     return res
 
 
@@ -789,6 +806,9 @@ def bench_volume(torch, ccl, hbm_gbs):
     from paper_1712_09789_gb300 import synth
 
     res = {"workload": "512x512x512 Bernoulli volumes, seed 0", "bytes_per_voxel": BYTES_PER_PIXEL, "runs": {}}
+    # DRAM bytes per voxel of the three kernels (ncu, 384^3 of the same
+    # recipe) from profiles/k_vol_512_bernoulli.md while the sources match
+    rec = recorded_figures("k_vol_512_bernoulli.md", ("ccl_block.cuh", "ccl_internal.h", "ccl_volume.cu"))
     n = 512 ** 3
     for p in (0.3, 0.5):
         d = torch.from_numpy(synth.bernoulli3d(512, 512, 512, p, 0)).cuda()
@@ -811,7 +831,8 @@ def bench_volume(torch, ccl, hbm_gbs):
             res["runs"][f"p{p}_conn{conn}"] = {
                 "ms": ms, "min_ms": min(ts), "gvoxel_s": gvx,
                 "hbm_roofline_frac": gvx * 1e9 * BYTES_PER_PIXEL / (hbm_gbs * 1e9),
-                "components": int(torch.unique(out).numel() - 1) if p == 0.3 else None}
+                "components": int(torch.unique(out).numel() - 1) if p == 0.3 else None,
+                "ncu_dram_bytes_per_voxel_384": (rec or {}).get(f"dram_bytes_per_voxel_p{p}_conn{conn}")}
         del d, out
         torch.cuda.empty_cache()
     return res
