@@ -747,55 +747,65 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
         fin[k] = (int)key + 1;
     }
     __syncthreads();
+    // positions in 32 bits: every voxel of the volume lies below 2^31
+    const uint32_t W = (uint32_t)a.W, WH = W * (uint32_t)a.H;
+    const uint32_t base = (uint32_t)gz0 * WH + (uint32_t)gy0 * W + (uint32_t)gx0;
     const uint16_t *V = a.vals + b * kVMaxElems;
     for (int e = t; e < (int)tot; e += kVThreads) {
         const int v = V[e];
         if (v & kSlotFlag) {
             lab[e] = (v & ~kSlotFlag) < ns ? fin[v & ~kSlotFlag] : 0;
         } else {
-            const int row = v / kVX;
-            lab[e] = (int)vpos(a, gx0 + v % kVX, gy0 + row % kVY, gz0 + row / kVY) + 1;
+            const uint32_t row = (uint32_t)v / kVX;
+            lab[e] = (int)(base + (row / kVY) * WH + (row % kVY) * W + (uint32_t)v % kVX) + 1;
         }
     }
     __syncthreads();
 
     // whole rows: a lane takes 4 voxels (one 16-byte store), a warp 4 rows
-    // per step
+    // per step; a lane keeps its y and steps two slices at a time
     const int lane = t % 32, warp = t / 32;
     const int c0 = 4 * (lane & 7);
     const int gx = gx0 + c0;
-    for (int row = 4 * warp + (lane >> 3); row < kVRows; row += 4 * (kVThreads / 32)) {
-        const int gy = gy0 + row % kVY, gz = gz0 + row / kVY;
-        if (gy >= a.H || gz >= a.D || gx >= a.W) continue;
-        const uint32_t m = mask[row];
-        int v[4] = {0, 0, 0, 0};
-        if ((m >> c0) & 15u) {
-            uint32_t st;
-            int e;
-            if (k26) {
-                const int r0 = (row / kVY & ~1) * kVY + (row % kVY & ~1);
-                const uint32_t o = mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1];
-                st = o & ~(o << 1);
-                e = (int)eoff[(row / kVY / 2) * (kVY / 2) + (row % kVY) / 2];
+    const int row0 = 4 * warp + (lane >> 3);
+    constexpr int kRowStep = 4 * (kVThreads / 32);
+    static_assert(kRowStep % kVY == 0, "a lane's rows share their y");
+    const int yl = row0 % kVY, gy = gy0 + yl;
+    if (gy < a.H && gx < a.W) {
+        const bool vec = a.vec_out && gx + 4 <= a.W;
+        const int nx = a.W - gx < 4 ? a.W - gx : 4;
+        const uint32_t pstep = (uint32_t)(kRowStep / kVY) * WH;
+        uint32_t pos = base + (uint32_t)(row0 / kVY) * WH + (uint32_t)yl * W + (uint32_t)c0;
+        for (int row = row0; row < kVRows && gz0 + row / kVY < a.D; row += kRowStep, pos += pstep) {
+            const uint32_t m = mask[row];
+            int v[4] = {0, 0, 0, 0};
+            if ((m >> c0) & 15u) {
+                uint32_t st;
+                int e;
+                if (k26) {
+                    const int r0 = (row / kVY & ~1) * kVY + (yl & ~1);
+                    const uint32_t o = mask[r0] | mask[r0 + 1] | mask[r0 + kVY] | mask[r0 + kVY + 1];
+                    st = o & ~(o << 1);
+                    e = (int)eoff[(row / kVY / 2) * (kVY / 2) + yl / 2];
+                } else {
+                    st = m & ~(m << 1);
+                    e = (int)eoff[row];
+                }
+                e += __popc(st & ((1u << c0) - 1u)) - 1;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    e += (int)((st >> (c0 + j)) & 1u);
+                    if ((m >> (c0 + j)) & 1u) v[j] = lab[e];
+                }
+            }
+            int32_t *dst = a.labels + pos;
+            if (vec) {
+                __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
             } else {
-                st = m & ~(m << 1);
-                e = (int)eoff[row];
-            }
-            e += __popc(st & ((1u << c0) - 1u)) - 1;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                e += (int)((st >> (c0 + j)) & 1u);
-                if ((m >> (c0 + j)) & 1u) v[j] = lab[e];
+                for (int j = 0; j < 4; ++j)
+                    if (j < nx) __stcs(dst + j, v[j]);
             }
-        }
-        int32_t *dst = a.labels + vpos(a, gx, gy, gz);
-        if (a.vec_out && gx + 4 <= a.W) {
-            __stcs(reinterpret_cast<int4 *>(dst), make_int4(v[0], v[1], v[2], v[3]));
-        } else {
-            const int n = a.W - gx < 4 ? a.W - gx : 4;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j < n) __stcs(dst + j, v[j]);
         }
     }
     if (err) atomicOr(&g_volume_error, err);
