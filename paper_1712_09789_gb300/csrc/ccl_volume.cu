@@ -131,14 +131,18 @@ __device__ __forceinline__ int v_find(volatile uint32_t *par, int x, int cap, in
     return x;
 }
 
-// Root of x without writing: used once the unions are done, while other
-// threads store roots into their own entries (a halving store here could put
-// a non-root ancestor back over such a root).
-__device__ __forceinline__ int v_find_ro(const volatile uint32_t *par, int x, int cap, int &err) {
+// Root of x with path halving by CAS: a halving store lands only while the
+// entry still holds the parent the walk read, so it never overwrites the root
+// that the entry's own thread stores meanwhile (the compression pass).
+__device__ __forceinline__ int v_find_cas(uint32_t *par, int x, int cap, int &err) {
+    volatile uint32_t *vp = par;
     for (int i = 0; i < cap; ++i) {
-        const int p = (int)par[slot(x)];
+        const int p = (int)vp[slot(x)];
         if (p == x) return x;
-        x = p;
+        const int g = (int)vp[slot(p)];
+        if (g == p) return p;
+        atomicCAS(par + slot(x), (uint32_t)p, (uint32_t)g);
+        x = g;
     }
     err |= kErrLocalCap;
     return x;
@@ -397,7 +401,8 @@ __device__ void bundle_labelling(VolSmem &sm, const VolArgs &a, int &err) {
             if ((j & 3) != k) continue;
             const int s = lobit(q);
             const int key = piece_key(bb, s, run_end(ob, s));
-            sm.par[slot(key)] = (uint32_t)v_find_ro(sm.par, key, a.local_cap, err);
+            const int root = v_find_cas(sm.par, key, a.local_cap, err);
+            if (root != key) sm.par[slot(key)] = (uint32_t)root;
         }
     }
     __syncthreads();
@@ -466,6 +471,15 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
             sm.par[slot(id)] = (uint32_t)parent;
         }
         __syncthreads();
+        // one round of pointer jumping: every link to its grandparent (an
+        // ancestor either way when another thread's store races with the
+        // read), halving the chains of coarse links up the rows
+        for (uint32_t t = st; t; t &= t - 1) {
+            const int id = r * kVX + lobit(t);
+            const uint32_t p = sm.par[slot(id)];
+            if (p != (uint32_t)id) sm.par[slot(id)] = sm.par[slot((int)p)];
+        }
+        __syncthreads();
 
         // refinement: every other event joins its two runs
         const uint32_t su = mu & ~(mu << 1), sv = mv & ~(mv << 1);
@@ -483,7 +497,8 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
 
         for (uint32_t t = st; t; t &= t - 1) {
             const int id = r * kVX + lobit(t);
-            sm.par[slot(id)] = (uint32_t)v_find_ro(sm.par, id, a.local_cap, err);
+            const int root = v_find_cas(sm.par, id, a.local_cap, err);
+            if (root != id) sm.par[slot(id)] = (uint32_t)root;
         }
         __syncthreads();
     }
