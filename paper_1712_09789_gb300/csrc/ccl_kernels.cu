@@ -133,6 +133,35 @@ __device__ __forceinline__ bool local_union(uint16_t *lp, int a, int b, int cap,
     return false;
 }
 
+// local_union by all 32 lanes of a warp together (lanes with valid == false
+// keep step); true in the lanes whose CAS linked two different sets, so the
+// pairs of those lanes form a spanning forest of all the pairs.
+__device__ __forceinline__ bool local_union_sync(uint16_t *lp, bool valid, int a, int b, int cap, int &err) {
+    volatile uint16_t *vp = lp;
+    bool pend = valid, joined = false;
+    for (int i = 0; __any_sync(0xFFFFFFFFu, pend); ++i) {
+        if (pend) {
+            a = local_find(vp, a, cap, err);
+            b = local_find(vp, b, cap, err);
+            if (a == b || err) {
+                pend = false;
+            } else {
+                if (a < b) { const int t = a; a = b; b = t; }
+                if (atomicCAS(reinterpret_cast<unsigned short *>(lp + a), (unsigned short)a, (unsigned short)b) ==
+                    (unsigned short)a) {
+                    pend = false;
+                    joined = true;
+                }
+            }
+        }
+        if (i >= cap) {
+            if (pend) err |= kErrGlobalCap;
+            break;
+        }
+    }
+    return joined;
+}
+
 // ---------------------------------------------------------------------------
 template <class G, int kCap_>
 struct LocalSmem {
@@ -643,15 +672,15 @@ __global__ void __launch_bounds__(G::kThreads,
 // blocks.  A pair that repeats the pair of the neighbouring pixel, or the
 // pair the thread linked last, is skipped.  The slots of the block and of the
 // blocks above and to the left are joined first in a shared-memory
-// union-find; only the pairs that join two of its sets reach the global
-// union-find, all in one round.
+// union-find (the pairs listed, then joined by whole warps); only the pairs
+// that join two of its sets reach the global union-find, all in one round.
 template <class G>
 struct __align__(16) MergeSmem {  // (16-byte aligned: the edges are staged with 16-byte stores)
     uint16_t up_o[G::kBW], up_p[G::kBW];  // top row of the block, bottom row of the block above
     uint16_t lf_o[G::kBH], lf_p[G::kBH];  // left column of the block, right column of the block to the left
     uint16_t lp[3 * G::kSlots];           // local nodes: own slots, then those above, then those to the left
-    uint32_t edge[3 * G::kSlots];         // joining pairs of local nodes: (a << 16) | b
-    int nedge;
+    uint32_t edge[3 * G::kSlots];         // pairs of local nodes (a << 16) | b: listed, then the joining ones
+    int nedge, njoin;
     ItemSlot item;
 };
 
@@ -694,18 +723,22 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
     }
     const int nn = nso + nsu + nsl;
     for (int i = t; i < nn; i += T) sm.lp[i] = (uint16_t)i;
-    if (t == 0) sm.nedge = 0;
+    if (t == 0) {
+        sm.nedge = 0;
+        sm.njoin = 0;
+    }
     __syncthreads();
 
+    // at most 3 pairs per top-edge column and per left-edge row
+    static_assert(3 * G::kSlots >= 3 * (G::kBW + G::kBH), "the pair list holds every pair of a block");
+    static_assert(T % 32 == 0, "the pairs are joined by whole warps");
     uint32_t last = 0xFFFFFFFFu;
     const auto link = [&](int na, int nb) {
         const uint32_t q = ((uint32_t)na << 16) | (uint32_t)nb;
         if (q == last) return;
         last = q;
-        if (local_union(sm.lp, na, nb, lcap, err)) {
-            const int k = atomicAdd(&sm.nedge, 1);
-            if (k < 3 * G::kSlots) sm.edge[k] = q;
-        }
+        const int k = atomicAdd(&sm.nedge, 1);
+        if (k < 3 * G::kSlots) sm.edge[k] = q;
     };
     const auto ok = [](uint16_t v, int ns) { return v != kBg && (int)v < ns; };
     if (up) {
@@ -748,6 +781,24 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
         }
     }
     __syncthreads();
+    // the listed pairs through the shared-memory union-find, a warp-wide step
+    // per pair per lane, where the two-step roots of a pair differ; the pairs
+    // that join two sets are written back to the front of the list (every
+    // index written is below the pairs already read)
+    {
+        const int nc = sm.nedge < 3 * G::kSlots ? sm.nedge : 3 * G::kSlots;
+        volatile uint16_t *vp = sm.lp;
+        for (int j0 = 0; j0 < nc; j0 += T) {
+            const int j = j0 + t;
+            uint32_t q = 0;
+            if (j < nc) q = sm.edge[j];
+            __syncthreads();
+            const int na = (int)(q >> 16), nb = (int)(q & 0xFFFFu);
+            const bool need = j < nc && vp[vp[na]] != vp[vp[nb]];
+            if (local_union_sync(sm.lp, need, na, nb, lcap, err)) sm.edge[atomicAdd(&sm.njoin, 1)] = q;
+            __syncthreads();
+        }
+    }
 
     // the joining pairs, then the two corner pairs (8-connectivity)
     const auto slot_of = [&](int node) -> uint32_t {
@@ -755,7 +806,7 @@ __device__ __forceinline__ void process_merge(const Job &job, unsigned lb, unsig
         if (node < nso + nsu) return bu * (uint32_t)G::kSlots + (uint32_t)(node - nso);
         return bl * (uint32_t)G::kSlots + (uint32_t)(node - nso - nsu);
     };
-    const int ne = sm.nedge < 3 * G::kSlots ? sm.nedge : 3 * G::kSlots;
+    const int ne = sm.njoin;
     for (int i = t; i < ne; i += T) {
         const uint32_t e = sm.edge[i];
         union_global(s.P, slot_of((int)(e >> 16)), slot_of((int)(e & 0xFFFFu)), gcap, err, bound);

@@ -152,3 +152,90 @@ def test_iteration_cap_reports_timeout_without_hanging():
         ccl.ccl_debug_set_iteration_cap(0)
     assert ccl.ccl_get_device_status() == ccl.CCL_OK
     np.testing.assert_array_equal(ccl.ccl_label_3d(dev, 6).cpu().numpy(), oracle.label3d(vol, 6))
+
+
+def _row_mask(vol, y, z):
+    """Bits x = 0..31 of row (y, z) of the first block."""
+    return sum(1 << x for x in range(32) if vol[z, y, x])
+
+
+def _runs(m):
+    """(first, last) column of every run of the bit mask m, in order."""
+    out, x = [], 0
+    while x < 32:
+        if (m >> x) & 1:
+            s = x
+            while x < 32 and (m >> x) & 1:
+                x += 1
+            out.append((s, x - 1))
+        else:
+            x += 1
+    return out
+
+
+def _pairs6(vol):
+    """Refinement pairs of the first 32x16x16 block under 6-connectivity:
+    every (run, run) contact with the row above or the row of the slice
+    before, less one per run that has any (its parent link)."""
+    n = 0
+    for z in range(16):
+        for y in range(16):
+            m = _row_mask(vol, y, z)
+            nbs = [_row_mask(vol, y - 1, z) if y else 0, _row_mask(vol, y, z - 1) if z else 0]
+            for s, e in _runs(m):
+                run = ((2 << e) - 1) ^ ((1 << s) - 1)
+                ev = sum(len(_runs(run & mn)) for mn in nbs)
+                n += max(ev - 1, 0)
+    return n
+
+
+def _pairs26(vol):
+    """Refinement pairs of the first block under 26-connectivity: contacts of
+    every piece of a 2x2 row bundle with the pieces of its four earlier
+    bundles (one per pair of pieces)."""
+    def rows(Y, Z):
+        return [_row_mask(vol, 2 * Y + dy, 2 * Z + dz) for dz in (0, 1) for dy in (0, 1)]  # r0, r0+1, r0+16, r0+17
+
+    n = 0
+    for Z in range(8):
+        for Y in range(8):
+            b = rows(Y, Z)
+            ob = b[0] | b[1] | b[2] | b[3]
+            for k, (dY, dZ, own, nbf) in enumerate(((-1, 0, (0, 2), (1, 3)), (0, -1, (0, 1), (2, 3)),
+                                                     (-1, -1, (0,), (3,)), (1, -1, (1,), (2,)))):
+                if not (0 <= Y + dY < 8 and 0 <= Z + dZ < 8):
+                    continue
+                nb = rows(Y + dY, Z + dZ)
+                on = nb[0] | nb[1] | nb[2] | nb[3]
+                fo = 0
+                for i in own:
+                    fo |= b[i]
+                fn = 0
+                for i in nbf:
+                    fn |= nb[i]
+                for s, e in _runs(ob):
+                    run = ((2 << e) - 1) ^ ((1 << s) - 1)
+                    t = fo & run
+                    c = (t | (t << 1) | (t >> 1)) & fn & 0xFFFFFFFF
+                    n += sum(1 for ps, pe in _runs(on) if c & (((2 << pe) - 1) ^ ((1 << ps) - 1)))
+    return n
+
+
+@pytest.mark.parametrize("conn", CONNS3)
+def test_refinement_list_overflow(conn):
+    """Blocks with more refinement pairs than the shared candidate list holds
+    (2048 per 32x16x16 block): the surplus is joined directly (6-connectivity)
+    or by a second pass over the contacts (26-connectivity)."""
+    D, H, W = 40, 40, 70
+    z, y, x = np.indices((D, H, W))
+    if conn == 6:
+        # full rows beside rows of every other voxel, alternating in y and z:
+        # a full row meets 16 runs above it and 16 in the slice before
+        vol = np.where((y + z) % 2 == 0, 1, x % 2 == 0).astype(np.uint8)
+        assert _pairs6(vol) > 2048
+    else:
+        # every other x: each bundle holds 16 one-voxel-wide pieces, each
+        # touching the piece of its column in every earlier bundle
+        vol = (x % 2 == 0).astype(np.uint8)
+        assert _pairs26(vol) > 2048
+    assert_parity(vol, conn, "list overflow")
