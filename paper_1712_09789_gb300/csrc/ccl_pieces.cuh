@@ -879,6 +879,18 @@ __device__ __forceinline__ void pwrite_labels(const Job &job, unsigned lb, unsig
         const int k = item >> PG::kWordsLog2, w = item & (W - 1);
         pb[k][w] = (uint16_t)(pb[k][w] + bb[k]);
     }
+    // a window of whole bands from band k0 whose piece labels fit in shared
+    // memory: bands k0 .. k1 - 1
+    const auto window_end = [&](int k0) {
+        int k1 = k0 + 1;
+        while (k1 < PG::kBands && (int)bb[k1 + 1] - (int)bb[k0] <= PG::kLabWindow) ++k1;
+        return k1;
+    };
+    const uint16_t *const vin = s.values + (size_t)b * PG::kMaxPieces;
+    // the values of the first window come from step 1 alone: they are read
+    // before the wait below
+    const int np_first = (int)bb[window_end(0)];
+    for (int i = t; i < np_first; i += T) lab[i] = vin[i];
     // the merge (step 2) may still be running when this kernel starts
     // (programmatic dependent launch): wait for it before the first read of
     // the merged union-find
@@ -895,14 +907,12 @@ __device__ __forceinline__ void pwrite_labels(const Job &job, unsigned lb, unsig
     report(err);
     __syncthreads();
 
-    const uint16_t *const vin = s.values + (size_t)b * PG::kMaxPieces;
     for (int k0 = 0; k0 < PG::kBands;) {
-        // a window of whole bands whose piece labels fit in shared memory
-        int k1 = k0 + 1;
-        while (k1 < PG::kBands && (int)bb[k1 + 1] - (int)bb[k0] <= PG::kLabWindow) ++k1;
+        const int k1 = window_end(k0);
         const int p0 = bb[k0], np = (int)bb[k1] - p0;
         for (int i = t; i < np; i += T) {
-            const uint32_t v = vin[p0 + i];
+            // (the first window's values were loaded into lab by this thread)
+            const uint32_t v = k0 == 0 ? (uint32_t)lab[i] : (uint32_t)vin[p0 + i];
             const uint32_t slot = v & 0x7FFFu;
             lab[i] = (v & kBorderFlag) ? ((int)slot < ns ? slot_label[slot] : 0)
                                           : (int)(key0 + (uint32_t)(y0 + (int)(v >> PG::kBWLog2)) * (uint32_t)Wd +
