@@ -417,24 +417,27 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
     const int gx0 = bx * kVX, gy = by * kVY + y, gz = bz * kVZ + z;
     const uint32_t m = row_mask(a, gx0, gy, gz);
 
-    // Voxels of this row that touch a foreground voxel of a neighbouring
-    // block across a y or z face: the rows across the face (under
-    // 26-connectivity the three rows at dz or dy in -1..1, widened by one
-    // voxel, with the voxels beyond the block's x range taken as
-    // foreground).  Only their components need a forest entry.  The x faces
-    // are taken as touching wherever the edge voxel is foreground.
+    // Voxels of this row that may touch a foreground voxel of a neighbouring
+    // block: only their components need a border slot.  Under
+    // 6-connectivity a voxel of a y or z face counts when the voxel across
+    // it is foreground (the row across is read); under 26-connectivity every
+    // voxel of a face row counts.  The x faces count wherever the edge
+    // voxel is foreground.
     uint32_t across = 0;
     {
-        constexpr int kR = k26 ? 1 : 0;
-        const auto widen = [](uint32_t h) { return k26 ? (h | (h << 1) | (h >> 1) | 0x80000001u) : h; };
-        if (m && y == 0 && by > 0)
-            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy - 1, gz + d));
-        if (m && y == kVY - 1 && by < a.nby - 1)
-            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + 1, gz + d));
-        if (m && z == 0 && bz > 0)
-            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + d, gz - 1));
-        if (m && z == kVZ - 1 && bz < a.nbz - 1)
-            for (int d = -kR; d <= kR; ++d) across |= widen(row_mask(a, gx0, gy + d, gz + 1));
+        const bool fy0 = y == 0 && by > 0, fy1 = y == kVY - 1 && by < a.nby - 1;
+        const bool fz0 = z == 0 && bz > 0, fz1 = z == kVZ - 1 && bz < a.nbz - 1;
+        if (k26) {
+            // a voxel of a y or z face meets nine voxels across it, and one
+            // of them is nearly always foreground: every voxel of such a row
+            // counts (no reads across the face)
+            if (fy0 || fy1 || fz0 || fz1) across = ~0u;
+        } else {
+            if (m && fy0) across |= row_mask(a, gx0, gy - 1, gz);
+            if (m && fy1) across |= row_mask(a, gx0, gy + 1, gz);
+            if (m && fz0) across |= row_mask(a, gx0, gy, gz - 1);
+            if (m && fz1) across |= row_mask(a, gx0, gy, gz + 1);
+        }
         across |= (bx > 0 ? 1u : 0u) | (bx < a.nbx - 1 ? 0x80000000u : 0u);
     }
     sm.mask[r] = m;
