@@ -433,10 +433,11 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
             // counts (no reads across the face)
             if (fy0 || fy1 || fz0 || fz1) across = ~0u;
         } else {
-            if (m && fy0) across |= row_mask(a, gx0, gy - 1, gz);
-            if (m && fy1) across |= row_mask(a, gx0, gy + 1, gz);
-            if (m && fz0) across |= row_mask(a, gx0, gy, gz - 1);
-            if (m && fz1) across |= row_mask(a, gx0, gy, gz + 1);
+            // (the loads go out together with the own row's)
+            if (fy0) across |= row_mask(a, gx0, gy - 1, gz);
+            if (fy1) across |= row_mask(a, gx0, gy + 1, gz);
+            if (fz0) across |= row_mask(a, gx0, gy, gz - 1);
+            if (fz1) across |= row_mask(a, gx0, gy, gz + 1);
         }
         across |= (bx > 0 ? 1u : 0u) | (bx < a.nbx - 1 ? 0x80000000u : 0u);
     }
