@@ -549,6 +549,9 @@ __global__ void __launch_bounds__(kVThreads, 5) k_vol_local(VolArgs a) {
     __shared__ VolSmem sm;
     __shared__ uint16_t sbase[kVRows];      // border slot of the first marked root of each row
     __shared__ uint16_t eoff[kVThreads];    // first element of each thread's row (bundle)
+    // the merge may be launched once every CTA of this grid has started (it
+    // waits for this grid's completion before reading anything)
+    grid_launch_dependents();
     int bx, by, bz;
     block_coords(a, bx, by, bz);
     int err = 0;
@@ -659,6 +662,10 @@ __global__ void __launch_bounds__(kVThreads) k_vol_merge(VolArgs a) {
     // repeat the pair of their neighbours
     __shared__ unsigned long long seen[kPairHash];
     for (int i = threadIdx.x; i < kPairHash; i += kVThreads) seen[i] = kNoPair;
+    // launched behind step 1 (programmatic dependent launch): wait for it,
+    // then let the write-out start its prologue
+    grid_dependency_wait();
+    grid_launch_dependents();
     __syncthreads();
     int err = 0;
     uint32_t last_q = ~0u, last_p = ~0u;
@@ -759,13 +766,9 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
     const uint32_t est = element_starts<k26>(mask, t, o, r0);
     eoff[t] = (uint16_t)cta_exclusive_scan((uint32_t)__popc(est), wtot, tot);
     const int ns = (int)a.ns[b];
-    int err = 0;
-    for (int k = t; k < ns; k += kVThreads) {
-        uint32_t key;
-        find_global_ro(a.P, (uint32_t)(b * kVSlots) + (uint32_t)k, key, a.global_cap, err, a.bound);
-        fin[k] = (int)key + 1;
-    }
-    __syncthreads();
+    // step 1's outputs are complete when this grid starts (the merge it runs
+    // behind waited for step 1): the labels of the elements whose root has
+    // no border slot are final now; a border slot s is held as -(s + 1)
     // positions in 32 bits: every voxel of the volume lies below 2^31
     const uint32_t W = (uint32_t)a.W, WH = W * (uint32_t)a.H;
     const uint32_t base = (uint32_t)gz0 * WH + (uint32_t)gy0 * W + (uint32_t)gx0;
@@ -773,11 +776,25 @@ __global__ void __launch_bounds__(kVThreads) k_vol_write(VolArgs a) {
     for (int e = t; e < (int)tot; e += kVThreads) {
         const int v = V[e];
         if (v & kSlotFlag) {
-            lab[e] = (v & ~kSlotFlag) < ns ? fin[v & ~kSlotFlag] : 0;
+            lab[e] = -((v & ~kSlotFlag) + 1);
         } else {
             const uint32_t row = (uint32_t)v / kVX;
             lab[e] = (int)(base + (row / kVY) * WH + (row % kVY) * W + (uint32_t)v % kVX) + 1;
         }
+    }
+    // the merge (step 2) may still be running: wait for it before the first
+    // read of the merged union-find
+    grid_dependency_wait();
+    int err = 0;
+    for (int k = t; k < ns; k += kVThreads) {
+        uint32_t key;
+        find_global_ro(a.P, (uint32_t)(b * kVSlots) + (uint32_t)k, key, a.global_cap, err, a.bound);
+        fin[k] = (int)key + 1;
+    }
+    __syncthreads();
+    for (int e = t; e < (int)tot; e += kVThreads) {
+        const int l = lab[e];
+        if (l < 0) lab[e] = -l - 1 < ns ? fin[-l - 1] : 0;
     }
     __syncthreads();
 
@@ -896,16 +913,31 @@ int launch_volume(const uint8_t *img, int D, int H, int W, size_t pitch, int con
     a.local_cap = cap > 0 ? cap : kVIds + 16;
     a.global_cap = cap > 0 ? cap : (int)(n + 16 < (1LL << 30) ? n + 16 : (1LL << 30));
     const unsigned blocks = (unsigned)nblocks;
+    // step 1 is a plain launch: it overwrites the scratch that the previous
+    // call's write-out reads.  The merge and the write-out may start while
+    // the kernel before them drains (programmatic dependent launch); each
+    // waits for it before reading what it wrote.
+    const auto pdl = [&](void (*kernel)(VolArgs)) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(kVThreads);
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, a) == cudaSuccess;
+    };
+    bool ok;
     if (conn == 26) {
         k_vol_local<true><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_merge<true><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<true><<<blocks, kVThreads, 0, stream>>>(a);
+        ok = cudaGetLastError() == cudaSuccess && pdl(k_vol_merge<true>) && pdl(k_vol_write<true>);
     } else {
         k_vol_local<false><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_merge<false><<<blocks, kVThreads, 0, stream>>>(a);
-        k_vol_write<false><<<blocks, kVThreads, 0, stream>>>(a);
+        ok = cudaGetLastError() == cudaSuccess && pdl(k_vol_merge<false>) && pdl(k_vol_write<false>);
     }
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+    return ok ? 0 : -1;
 }
 
 int read_and_clear_volume_error(int *value) {
