@@ -116,26 +116,11 @@ __device__ __forceinline__ int local_find(volatile uint16_t *lp, int x, int cap,
     return x;
 }
 
-// Joins the sets of nodes a and b; true when this call linked two different
-// sets (the larger root hung under the smaller).
-__device__ __forceinline__ bool local_union(uint16_t *lp, int a, int b, int cap, int &err) {
-    volatile uint16_t *vp = lp;
-    for (int i = 0; i < cap; ++i) {
-        a = local_find(vp, a, cap, err);
-        b = local_find(vp, b, cap, err);
-        if (a == b || err) return false;
-        if (a < b) { const int t = a; a = b; b = t; }
-        if (atomicCAS(reinterpret_cast<unsigned short *>(lp + a), (unsigned short)a, (unsigned short)b) ==
-            (unsigned short)a)
-            return true;
-    }
-    err |= kErrGlobalCap;
-    return false;
-}
-
-// local_union by all 32 lanes of a warp together (lanes with valid == false
-// keep step); true in the lanes whose CAS linked two different sets, so the
-// pairs of those lanes form a spanning forest of all the pairs.
+// Joins the sets of local nodes a and b, by all 32 lanes of a warp together
+// (lanes with valid == false keep step): the larger root is hung under the
+// smaller by CAS, and a lane whose CAS failed retries with the new roots.
+// True in the lanes whose CAS linked two different sets, so the pairs of
+// those lanes form a spanning forest of all the pairs.
 __device__ __forceinline__ bool local_union_sync(uint16_t *lp, bool valid, int a, int b, int cap, int &err) {
     volatile uint16_t *vp = lp;
     bool pend = valid, joined = false;
