@@ -97,7 +97,7 @@ constexpr int kCand = 2048;  // refinement pairs listed per pass (more are joine
 
 struct VolSmem {
     uint32_t mask[kVRows];    // row masks (bit x = voxel x of the row)
-    uint32_t border[kVRows];  // bit x of row r: id r*32+x is the root of a component on a block face
+    uint32_t border[kVRows];  // bit x of row r: id r*32+x is a marked root (border slot owner)
     uint32_t par[kVIds];      // union-find entries, by slot(id); used at element ids only
     uint32_t cand[kCand];     // refinement pairs (a << 16 | b)
     uint32_t wtot[kVThreads / 32];
@@ -507,7 +507,7 @@ __device__ uint32_t vol_local(VolSmem &sm, const VolArgs &a, int bx, int by, int
         __syncthreads();
     }
 
-    // roots of the components with a voxel that touches a neighbouring block
+    // roots of the components with a voxel that may touch a neighbouring block
     uint32_t fm = m & across;
     while (fm) {
         const int b = lobit(fm);
